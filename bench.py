@@ -1,0 +1,345 @@
+"""Throughput of the two-step Brillouin-zone propagation on GB300.
+
+Workload (one "step" = one full time step of every sub-simulation): the
+two-step linear-response run of 64 shifted 4^3 Monkhorst-Pack subgrids of
+the 8-atom cubic Si-like cell (a = 10.26 bohr, 16^3 grid, 16 doubly
+occupied bands, 32 KB projectors), i.e. 4096 k-points and 65 536 orbitals,
+kick 0.005 along x, dt = 0.08, 4th-order Taylor, self-consistent v_Hxc.
+Inputs are synthetic (plane-wave start orbitals) and larger than L2.
+
+metric: orbital-steps/s = (k, band, dt) units advanced per second.
+  value : FP32/tensor-path throughput, device-resident inputs, CUDA events
+  e2e   : the same through the C ABI with host buffers (ground-state upload,
+          propagation, current download inside the timed region)
+  fp64  : the plain FP64 GPU path on the same workload (context)
+
+--impl reference times the CPU oracle (the reference of this build) on
+host cores, one bounded sample of the workload per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+# The oracle's worker processes re-import this module: one BLAS thread each.
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+os.environ.setdefault("OMP_NUM_THREADS", "1")
+
+import numpy as np  # noqa: E402
+
+METRIC = "orbital-steps/s (k·band·Δt), FP32/TC batched vs FP64 GPU; ε(ω) rel err vs oracle"
+UNIT = "orbital-steps/s"
+WORKLOAD = "two-step 64x4^3 shifted MP, Si-like 8-atom cubic cell, 16^3 grid, 16 bands (config 2 step)"
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle timing (reference arm and cpu_baseline)
+# ----------------------------------------------------------------------------
+def _oracle_job(args):
+    m, n_steps = args
+    import workloads as W
+    from oracle import dynamics
+    run = W.config2(n_steps=n_steps)
+    sub = run.subsims[m]
+    cell = sub.cell
+    psi = W.plane_wave_orbitals(cell.a, cell.n, W.plane_wave_set(cell.n_bands), sub.mp[0] * sub.mp[1] * sub.mp[2])
+    t0 = time.perf_counter()
+    dynamics._run_one((sub, psi, "scf", None))
+    return time.perf_counter() - t0, psi.shape[0] * psi.shape[1] * n_steps
+
+
+def oracle_sample(workers: int, n_steps: int = 1):
+    """Each worker propagates one sub-simulation (64 k x 16 bands) for n_steps
+    with the oracle; returns (orbital-steps, wall seconds)."""
+    import multiprocessing as mp
+    jobs = [(m % 64, n_steps) for m in range(workers)]
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(workers) as pool:
+        res = pool.map(_oracle_job, jobs)
+    wall = time.perf_counter() - t0
+    return sum(r[1] for r in res), wall
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+# ----------------------------------------------------------------------------
+# Clocks
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int = 0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 6:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[2:6]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+def build_propagator(precision, n_steps_cap, psi_host=None, device=0):
+    import workloads as W
+    from paper_2112_00920_gb300 import Propagator, shifted_kpoints
+    run = W.config2(n_steps=n_steps_cap)
+    cell = run.subsims[0].cell
+    P = Propagator(precision, device=device)
+    cid = P.add_cell_spec(cell)
+    sids = [P.add_subsim(cid, shifted_kpoints(cell.a, s.mp, s.shift), s.dt, n_steps_cap) for s in run.subsims]
+    return P, sids, run
+
+
+def stage_bytes_per_launch(elem: int, n_orb: int, npts: int) -> float:
+    """Algorithmic DRAM bytes of the Taylor stage kernel, averaged over its
+    four launches per step: m=1 reads t0 and writes t1 (2 arrays), m=2 and
+    m=3 read t, read and write psi and write t (4 arrays), m=4 reads t and
+    reads and writes psi (3 arrays): 13 arrays / 4 launches."""
+    return 13.0 / 4.0 * elem * n_orb * npts
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        run_reference(args)
+        return
+
+    # CPU baseline first (before any CUDA context exists in this process)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        workers = max(1, min(host_cores(), 16))
+        units, wall = oracle_sample(workers, 1)
+        cpu = {"value": units / wall, "unit": UNIT, "cores": workers, "kind": "oracle",
+               "sample": f"{workers} sub-simulations x 1 step (64 k x 16 bands each, numpy complex128, "
+                         f"one process per core, BLAS 1 thread), {wall:.1f} s wall, {cpu_model()}"}
+
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    import workloads as W
+    from paper_2112_00920_gb300 import build_library
+    build_library()
+
+    cap = args.warmup + args.steps
+    P, sids, run = build_propagator(args.precision, cap, device=local_rank)
+    cell = run.subsims[0].cell
+    n_orb = run.n_orbitals
+    gints = W.plane_wave_set(cell.n_bands)
+    psi_host = W.plane_wave_orbitals(cell.a, cell.n, gints, 64)
+    psi_dev = torch.from_numpy(psi_host).to(f"cuda:{local_rank}")
+    for sid in sids:
+        P.load_ground_state(sid, psi_dev)
+    P.set_kick(-1, 0.005, (1.0, 0.0, 0.0))
+    P.propagate(args.warmup)
+    stream = torch.cuda.current_stream()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    P.set_profiling(True)
+    l0 = P.launches()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        start.record(stream)
+        P.propagate(args.steps)
+        end.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = start.elapsed_time(end)
+    launches = P.launches() - l0
+    fam = P.timings()
+    P.set_profiling(False)
+    J_avg, _ = P.current(-1)
+    ms_t = torch.tensor([ms], device=f"cuda:{local_rank}")
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = n_orb * args.steps * world / (ms_max / 1e3)
+
+    # roofline of the dominant kernel family (the Taylor stage kernel)
+    import json as _json
+    peaks = {}
+    try:
+        peaks = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    elem = 8 if args.precision == "fp32" else 16
+    n_stage = 4 * args.steps
+    stage_ms = fam["stage"] / n_stage
+    bytes_launch = stage_bytes_per_launch(elem, n_orb, cell.n_pts)
+    achieved = bytes_launch / (stage_ms / 1e3) / 1e9
+    roof = {"kernel": "k_stage (stencil + ket + Taylor accumulate)", "bound": "hbm", "achieved": achieved,
+            "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)" if peaks else "fallback 6.8 TB/s",
+            "family_ms_per_step": {k: v / args.steps for k, v in fam.items()}}
+
+    # end-to-end through the C ABI with host buffers
+    P.close()
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter()
+    P2, sids2, _ = build_propagator(args.precision, args.steps, device=local_rank)
+    for sid in sids2:
+        P2.load_ground_state(sid, psi_host)
+    P2.set_kick(-1, 0.005, (1.0, 0.0, 0.0))
+    P2.propagate(args.steps)
+    J_e2e, _ = P2.current(-1)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t_e2e
+    P2.close()
+    e2e = {"value": n_orb * args.steps * world / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(psi_host.nbytes * 64 / args.steps),
+           "d2h_bytes_per_step": int(J_e2e.nbytes * 64 / max(args.steps, 1)),
+           "includes": "context set-up, 64 ground-state uploads (complex128 host), kick, propagation, "
+                       "two-step current download"}
+
+    # plain FP64 GPU path on the same workload (comparison)
+    fp64 = None
+    if args.precision == "fp32" and args.fp64_steps > 0:
+        P3, sids3, _ = build_propagator("fp64", args.fp64_steps + 1, device=local_rank)
+        for sid in sids3:
+            P3.load_ground_state(sid, psi_dev)
+        P3.set_kick(-1, 0.005, (1.0, 0.0, 0.0))
+        P3.propagate(1)
+        torch.cuda.synchronize()
+        s3, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s3.record(stream)
+        P3.propagate(args.fp64_steps)
+        e3.record(stream)
+        torch.cuda.synchronize()
+        fp64_ms = s3.elapsed_time(e3)
+        P3.close()
+        fp64 = {"value": n_orb * args.fp64_steps / (fp64_ms / 1e3), "unit": UNIT, "steps": args.fp64_steps,
+                "ms_per_step": fp64_ms / args.fp64_steps}
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+               "data": "synthetic (seeded Si-like model, plane-wave start orbitals)",
+               "config": {"workload": WORKLOAD, "n_subsims": len(run.subsims), "k_points": 4096,
+                          "orbitals_per_gpu": n_orb, "grid": "16^3", "bands": 16, "dt": 0.08,
+                          "precision": args.precision, "l2": "inputs (psi 2 GiB fp32) larger than L2",
+                          "parallelism": f"replica x{world} (independent shifts per GPU)"},
+               "roofline": roof, "e2e": e2e, "gpu_launches": launches,
+               "clocks": clk.summary(),
+               "fp64_gpu": fp64,
+               "fp32_over_fp64": (value / world / fp64["value"]) if fp64 else None,
+               "two_step_dJx_last": float(J_avg[-1, 0])}
+        if cpu is not None:
+            out["cpu_baseline"] = cpu
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    workers = max(1, min(host_cores(), 16))
+    for _ in range(args.warmup):
+        oracle_sample(workers, 1)
+    units = 0
+    wall = 0.0
+    for _ in range(args.steps):
+        u, w = oracle_sample(workers, 1)
+        units += u
+        wall += w
+    value = units / wall
+    sample = (f"per step: {workers} sub-simulations x 1 time step (64 k x 16 bands each) with the numpy "
+              f"complex128 oracle, one process per core; {cpu_model()}")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded Si-like model, plane-wave start orbitals)",
+           "config": {"workload": WORKLOAD, "precision": "fp64 (oracle)"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

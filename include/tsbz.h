@@ -1,0 +1,193 @@
+/*
+ * tsbz -- two-step Brillouin-zone sampling for real-time TDDFT on one GPU.
+ *
+ * C ABI of the propagation library.  The library advances many independent
+ * sub-simulations (one shifted k-subgrid each, Sec. II.B steps 1-4 and
+ * Eqs. 9-10) of the time-dependent Kohn-Sham equation (Eq. 1) with the
+ * Hamiltonian of Eq. 2, and returns the density (Eq. 3) and the macroscopic
+ * current (Eqs. 5-6) of each, plus their two-step average (Eq. 9).
+ *
+ * Conventions (all entry points):
+ *  - Hartree atomic units; k and A are Cartesian (bohr^-1).
+ *  - Grid arrays are [n3][n2][n1] with x (n1) fastest; orbital arrays of a
+ *    sub-simulation are [n_k][n_bands][n3][n2][n1], interleaved complex
+ *    (re, im) doubles; the k order is the caller's.
+ *  - Every function returns a status: TSBZ_OK (0) or a negative TSBZ_E*
+ *    code; tsbz_last_error() gives the text.  No C++ exception crosses the
+ *    ABI.  A failed call leaves the context usable unless it returns
+ *    TSBZ_ECUDA, after which only tsbz_last_error and tsbz_destroy are valid.
+ *  - Input arrays are owned by the caller and are copied (host arrays) or
+ *    read (device arrays) before the call returns; outputs go to caller
+ *    buffers whose capacity (in doubles) is passed and checked.
+ *  - The context owns its device memory.  It is obtained from the optional
+ *    caller allocator (tsbz_alloc) or else from cudaMalloc, and released by
+ *    tsbz_destroy.  Work is issued on the caller's stream (or the legacy
+ *    default stream); calls that return host data synchronise that stream.
+ *  - A context is not thread-safe; distinct contexts may be used from
+ *    distinct threads.
+ */
+#ifndef TSBZ_H
+#define TSBZ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TSBZ_OK 0
+#define TSBZ_EINVAL (-1)     /* bad argument, size or capacity            */
+#define TSBZ_ENOMEM (-2)     /* device or host allocation failed          */
+#define TSBZ_ECUDA (-3)      /* a CUDA call failed                         */
+#define TSBZ_ETIMEOUT (-4)   /* a bounded device wait gave up              */
+#define TSBZ_ENONFINITE (-5) /* a non-finite current was produced          */
+#define TSBZ_ESTATE (-6)     /* call out of order (e.g. no ground state)   */
+
+/* Arithmetic of the propagation (a2-a5).  Density, current, Hartree and
+ * the time integration of the observables are FP64 in every mode. */
+#define TSBZ_FP64 0          /* everything in double                          */
+#define TSBZ_FP32 1          /* stencil, Taylor and projectors in float       */
+#define TSBZ_FP32_TC 2       /* as FP32, projector contractions on tensor cores
+                                (split-BF16, three products, FP32 accumulate) */
+
+#define TSBZ_HXC_SCF 0       /* v_Hxc[rho(t)] updated every step (Eq. 2)      */
+#define TSBZ_HXC_FROZEN 1    /* v_Hxc kept at its loaded value                */
+
+typedef struct tsbz_ctx tsbz_ctx;
+
+/* Optional device allocator: alloc returns device memory of `bytes` bytes
+ * aligned to at least 256 bytes, or NULL; free releases it. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* user);
+  void (*free)(void* ptr, void* user);
+  void* user;
+} tsbz_alloc;
+
+/* A cell and its synthetic norm-conserving pseudopotential (Eq. 2, Sec. III).
+ *  - orthorhombic edges a[3] (bohr), grid n[3] (each 2*fd_nd+1 .. 1024);
+ *  - atoms at fractional positions atom_frac[3*n_atoms];
+ *  - local part per atom: -z_ion erf(r/r_erf)/r + c_core exp(-r^2/(2 sigma_core^2)),
+ *    defined through its Fourier series with the G = 0 Coulomb term removed;
+ *  - projectors (if use_projectors): per atom one s and three p functions
+ *    beta = N exp(-|d|^2/(2 r_proj^2)) * {1, d_x, d_y, d_z}, d the minimum-image
+ *    displacement, zero unless every |d_ax|/h_ax < proj_half, each normalised
+ *    to dV sum beta^2 = 1, energies e_kb_s and e_kb_p;
+ *  - n_bands occupied bands with occupation occ each;
+ *  - fd_nd: stencil half-width (1..6); hxc_mode: TSBZ_HXC_*;
+ *  - xc: 0 none, 1 LDA Perdew-Zunger 81; hartree: 0/1. */
+typedef struct {
+  double a[3];
+  int n[3];
+  int n_atoms;
+  const double* atom_frac;
+  double z_ion, r_erf, c_core, sigma_core;
+  double r_proj, proj_half, e_kb_s, e_kb_p;
+  int use_projectors;
+  int n_bands;
+  double occ;
+  int fd_nd;
+  int hxc_mode;
+  int xc;
+  int hartree;
+} tsbz_cell_desc;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int tsbz_version(void);
+
+/* Create a context on CUDA device `device` computing in `precision`
+ * (TSBZ_FP64 / TSBZ_FP32 / TSBZ_FP32_TC).  `cuda_stream` is a cudaStream_t
+ * or NULL; `alloc` may be NULL.  *out receives the context. */
+int tsbz_create(tsbz_ctx** out, int device, int precision, void* cuda_stream, const tsbz_alloc* alloc);
+
+/* Register a cell (Eq. 2's v_ion and grid); builds v_loc, the projector
+ * tables and the FD weights on the host and copies them to the device. */
+int tsbz_init_cell(tsbz_ctx* ctx, const tsbz_cell_desc* desc, int* cell_id);
+
+/* Add one sub-simulation (Sec. II.B step 3): n_k k-points k_cart[n_k][3]
+ * of cell `cell_id`, time step dt, capacity for max_steps steps of history.
+ * Sub-simulations can only be added before the first load_ground_state. */
+int tsbz_add_subsim(tsbz_ctx* ctx, int cell_id, int n_k, const double* k_cart, double dt, int max_steps,
+                    int* subsim_id);
+
+/* Load the initial orbitals of a sub-simulation: psi is complex128
+ * [n_k][n_bands][n3][n2][n1] (n_elems complex values), on the host
+ * (psi_on_device = 0) or the device (1).  v_hxc_frozen ([n3][n2][n1] host
+ * doubles) is required in TSBZ_HXC_FROZEN mode and ignored otherwise.
+ * Computes rho(0), v_Hxc[rho(0)] and J(0-) (A = 0), and resets the step count. */
+int tsbz_load_ground_state(tsbz_ctx* ctx, int subsim_id, const double* psi, size_t n_elems, int psi_on_device,
+                           const double* v_hxc_frozen);
+
+/* Impulsive field of Eq. 11, read as A(t) = -k0 dir theta(t) (A = 0 before
+ * the kick, -k0 dir from t = 0+ on).  subsim_id = -1 applies to all. */
+int tsbz_set_kick(tsbz_ctx* ctx, int subsim_id, double k0, const double dir[3]);
+
+/* General field: samples A(j dt/2), j = 0..2*n_steps, as [2 n_steps + 1][3]
+ * (j = 0 is t = 0+); n_steps <= the sub-simulation's max_steps. */
+int tsbz_set_field(tsbz_ctx* ctx, int subsim_id, int n_steps, const double* a_samples);
+
+/* Advance every sub-simulation by n_steps 4th-order Taylor steps (Eq. 1 with
+ * the step defined in the header of the CUDA sources): h uses
+ * q = k + A(t_n + dt/2) and v_Hxc[rho(t_n)]; after the step rho, v_Hxc and
+ * J(t_{n+1}) (q = k + A(t_{n+1})) are updated.  Returns when the work is
+ * complete; TSBZ_ENONFINITE names the first failing sub-simulation. */
+int tsbz_propagate(tsbz_ctx* ctx, int n_steps);
+
+/* Current history J(t_j), j = first .. first+count-1 (j = 0 is t = 0+), as
+ * [count][3], and J(0-) (nullable).  subsim_id = -1 returns the two-step
+ * average (1/N_H) sum_m (J_m(t_j) - J_m(0-)) (Eq. 9, Sec. II.B step 4) and
+ * J0_minus = 0; all sub-simulations then need the same dt. */
+int tsbz_get_current(tsbz_ctx* ctx, int subsim_id, int first, int count, double* J, double* J0_minus);
+
+/* Density rho(r) = (1/N_k) sum_k sum_b occ |u_bk(r)|^2 (Eq. 3) of a
+ * sub-simulation at its current step, [n3][n2][n1] doubles (cap >= n_pts). */
+int tsbz_get_density(tsbz_ctx* ctx, int subsim_id, double* rho, size_t cap);
+
+/* Orbital norms dV sum_r |u_bk(r)|^2 at the current step, [n_k][n_bands]. */
+int tsbz_get_norms(tsbz_ctx* ctx, int subsim_id, double* norms, size_t cap);
+
+/* Steps done by a sub-simulation. */
+int tsbz_get_step(tsbz_ctx* ctx, int subsim_id, int* step);
+
+/* Checkpoint: copy the orbitals out as complex128 (cap in complex values)
+ * together with the step count; tsbz_load_state restores orbitals, step
+ * count and recomputes rho and v_Hxc from them. */
+int tsbz_get_state(tsbz_ctx* ctx, int subsim_id, double* psi, size_t cap, int* step);
+int tsbz_load_state(tsbz_ctx* ctx, int subsim_id, const double* psi, size_t n_elems, int step);
+
+/* The local potential and the projector normalisations of a cell as built
+ * by tsbz_init_cell: vloc [n3][n2][n1] (cap >= n_pts), norms [4 n_atoms]. */
+int tsbz_get_cell_tables(tsbz_ctx* ctx, int cell_id, double* vloc, size_t cap, double* proj_norms, size_t ncap);
+
+/* Kernel launches issued by this context so far (for accounting). */
+int tsbz_get_launch_count(tsbz_ctx* ctx, long long* launches);
+
+/* Device time of the most recent tsbz_propagate (CUDA events on the
+ * context stream) split by kernel family: times_ms[0..5] =
+ * {bra, stage, observe, finalize, hxc, field}; bytes are not measured. */
+int tsbz_get_timings(tsbz_ctx* ctx, double* times_ms, int n);
+int tsbz_set_profiling(tsbz_ctx* ctx, int on);
+
+const char* tsbz_last_error(tsbz_ctx* ctx);
+void tsbz_destroy(tsbz_ctx* ctx);
+
+/* ---- Host-side method helpers (no context, no GPU) ------------------------
+ * k-points of the shifted Monkhorst-Pack grid of Eq. 10 (shift = 0 gives
+ * Eq. 8): k = sum_j (2 n_j - N_j - 1 + 2 s_j)/(2 N_j) b_j with
+ * b_j = (2 pi / a_j) e_j, each fractional coordinate wrapped into
+ * [-1/2, 1/2); order n_1 fastest.  k_out has 3 * mp[0]*mp[1]*mp[2] doubles. */
+int tsbz_shifted_kpoints(const double a[3], const int mp[3], const double shift[3], double* k_out, size_t cap);
+
+/* First n points of the Halton sequence in bases 2, 3, 5 (index m = 1..n),
+ * the quasi-random shifts of Sec. II.B; out has 3 n doubles. */
+int tsbz_halton(int n, double* out, size_t cap);
+
+/* Samples A(j dt/2), j = 0..2 n_steps, of the laser pulse of Eq. 15, read as
+ * A(t) = -(e0/w0) dir sin^4(pi t/T) sin(w0 (t - T/2)) on (0, T), else 0. */
+int tsbz_pulse_samples(double e0, double w0, double t_pulse, const double dir[3], double dt, int n_steps,
+                       double* out, size_t cap);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TSBZ_H */

@@ -1,0 +1,856 @@
+// Host runtime of the propagation library: context, device layout, the
+// launch sequence of one time step, and the C ABI declared in tsbz.h.
+//
+// Time step n -> n+1 (all sub-simulations advance together):
+//   field(STEP)                          q = k + A(t_n + dt/2), q_obs = k + A(t_{n+1})
+//   for m = 1..4: bra(t_{m-1}) ; stage m  Taylor recurrence, psi accumulates
+//   bra_J(psi) ; observe(psi)            projections and sums at t_{n+1}
+//   finalize(STEP)                       rho, norms, J(t_{n+1}); step += 1
+//   hxc                                  v_Hxc[rho(t_{n+1})], v_eff
+// Term buffers: stage 1 psi -> tA, stage 2 tA -> tB (psi += t1 + t2),
+// stage 3 tB -> tA (psi += t3), stage 4 tA -> (psi += t4).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "tsbz.h"
+#include "tsbz_host.h"
+#include "tsbz_internal.h"
+
+namespace {
+
+struct HostCell {
+  tsbz_cell_desc desc;
+  std::vector<double> atoms;
+  CellDev dev;
+  std::vector<double> vloc, pnorm;
+  double2* tw[3] = {nullptr, nullptr, nullptr};
+  std::vector<int> unit_ids;
+  int* d_unit_ids = nullptr;
+  std::vector<int> hxc_subs;   // non-frozen sub-simulations of this cell
+  int* d_hxc_subs = nullptr;
+};
+
+struct HostSub {
+  int cell = 0;
+  int n_k = 0;
+  std::vector<double> k;
+  double dt = 0.0;
+  int max_steps = 0;
+  int unit0 = 0;
+  std::vector<double> A;   // (2 max_steps + 1) * 3
+  bool field_dirty = true;
+  bool loaded = false;
+  bool need_init = false;
+  bool need_j0plus = false;
+  int steps = 0;
+  double* A_d = nullptr;
+  double* J = nullptr;
+  double* J0m = nullptr;
+  double* rho = nullptr;
+  double* vhxc = nullptr;
+  double* norms = nullptr;
+  void* veff = nullptr;
+};
+
+}  // namespace
+
+struct tsbz_ctx {
+  int device = 0;
+  int precision = TSBZ_FP64;
+  cudaStream_t stream = nullptr;
+  bool has_alloc = false;
+  tsbz_alloc alloc{};
+  std::string err;
+  std::vector<HostCell> cells;
+  std::vector<HostSub> subs;
+  bool laid_out = false;
+  std::vector<void*> owned;
+  void* psi = nullptr;
+  void* tA = nullptr;
+  void* tB = nullptr;
+  void* P = nullptr;
+  void* Pa = nullptr;
+  void* ph_half = nullptr;
+  void* ph_obs = nullptr;
+  long long ph_stride = 1;
+  double* rho_part = nullptr;
+  double* jk_part = nullptr;
+  double* nrm_part = nullptr;
+  double* q_half = nullptr;
+  double* q_obs = nullptr;
+  double* kcart = nullptr;
+  UnitDev* d_units = nullptr;
+  SubDev* d_subs = nullptr;
+  CellDev* d_cells = nullptr;
+  int* d_steps = nullptr;
+  int* d_status = nullptr;
+  int* d_mask = nullptr;
+  double2* work_a = nullptr;
+  double2* work_b = nullptr;
+  double2* staging = nullptr;
+  long long staging_elems = 0;
+  long long n_units = 0;
+  std::vector<long long> unit_psi_off;
+  long long launches = 0;
+  bool prof = false;
+  double times[6] = {0, 0, 0, 0, 0, 0};
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, int>> ev_marks;   // (family, event index of start)
+  size_t ev_next = 0;
+  size_t elem_size() const { return precision == TSBZ_FP64 ? sizeof(double2) : sizeof(float2); }
+};
+
+namespace {
+
+enum { FAM_BRA = 0, FAM_STAGE = 1, FAM_OBS = 2, FAM_FIN = 3, FAM_HXC = 4, FAM_FIELD = 5 };
+
+int set_err(tsbz_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+#define CK(call)                                                                               \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess)                                                                     \
+      return set_err(ctx, TSBZ_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));     \
+  } while (0)
+
+int dalloc(tsbz_ctx* ctx, size_t bytes, void** out) {
+  bytes = bytes ? bytes : 256;
+  void* p = nullptr;
+  if (ctx->has_alloc) {
+    p = ctx->alloc.alloc(bytes, ctx->alloc.user);
+    if (!p) return set_err(ctx, TSBZ_ENOMEM, "caller allocator returned NULL for " + std::to_string(bytes) + " bytes");
+  } else {
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return set_err(ctx, TSBZ_ENOMEM, "cudaMalloc(" + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+    }
+  }
+  ctx->owned.push_back(p);
+  *out = p;
+  return TSBZ_OK;
+}
+
+template <typename P> int dalloc_t(tsbz_ctx* ctx, size_t count, P** out) {
+  void* p = nullptr;
+  int rc = dalloc(ctx, count * sizeof(P), &p);
+  *out = static_cast<P*>(p);
+  return rc;
+}
+
+void ev_start(tsbz_ctx* ctx, int fam) {
+  if (!ctx->prof) return;
+  while (ctx->ev_pool.size() < ctx->ev_next + 2) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    ctx->ev_pool.push_back(e);
+  }
+  cudaEventRecord(ctx->ev_pool[ctx->ev_next], ctx->stream);
+  ctx->ev_marks.push_back({fam, (int)ctx->ev_next});
+  ctx->ev_next += 2;
+}
+
+void ev_stop(tsbz_ctx* ctx) {
+  if (!ctx->prof) return;
+  cudaEventRecord(ctx->ev_pool[ctx->ev_marks.back().second + 1], ctx->stream);
+}
+
+LaunchSet make_set(tsbz_ctx* ctx, HostCell& hc) {
+  LaunchSet L;
+  L.cell = hc.dev;
+  L.units = ctx->d_units;
+  L.unit_ids = hc.d_unit_ids;
+  L.n_units = (int)hc.unit_ids.size();
+  L.subs = ctx->d_subs;
+  L.kcart = ctx->kcart;
+  L.q_half = ctx->q_half;
+  L.q_obs = ctx->q_obs;
+  L.ph_half = ctx->ph_half;
+  L.ph_obs = ctx->ph_obs;
+  L.ph_stride = ctx->ph_stride;
+  return L;
+}
+
+int layout(tsbz_ctx* ctx) {
+  if (ctx->laid_out) return TSBZ_OK;
+  if (ctx->subs.empty()) return set_err(ctx, TSBZ_ESTATE, "no sub-simulation added");
+  const size_t es = ctx->elem_size();
+  std::vector<UnitDev> units;
+  std::vector<double> kc;
+  long long psi_e = 0, p_e = 0, pa_e = 0, rho_e = 0, jk_e = 0, nrm_e = 0;
+  long long ph_stride = 1, stage_max = 0, work_max = 0;
+  for (auto& hc : ctx->cells) {
+    hc.unit_ids.clear();
+    hc.hxc_subs.clear();
+    ph_stride = std::max<long long>(ph_stride, (long long)hc.dev.n_atoms * 3 * hc.dev.nmax);
+  }
+  for (size_t s = 0; s < ctx->subs.size(); ++s) {
+    HostSub& hs = ctx->subs[s];
+    HostCell& hc = ctx->cells[hs.cell];
+    const CellDev& c = hc.dev;
+    hs.unit0 = (int)units.size();
+    for (int k = 0; k < hs.n_k; ++k) {
+      UnitDev U;
+      U.psi_off = psi_e;
+      U.p_off = p_e;
+      U.pa_off = pa_e;
+      U.rho_off = rho_e;
+      U.jk_off = jk_e;
+      U.nrm_off = nrm_e;
+      U.sub = (int)s;
+      U.kloc = k;
+      psi_e += (long long)c.n_bands * c.npts;
+      p_e += (long long)c.n_bands * c.n_proj;
+      pa_e += 4LL * c.n_bands * c.n_proj;
+      rho_e += (long long)c.n_bgroups * c.npts;
+      jk_e += 3LL * c.n_tiles * c.n_bgroups;
+      nrm_e += (long long)c.n_tiles * c.n_bands;
+      hc.unit_ids.push_back((int)units.size());
+      ctx->unit_psi_off.push_back(U.psi_off);
+      units.push_back(U);
+      for (int ax = 0; ax < 3; ++ax) kc.push_back(hs.k[3 * k + ax]);
+    }
+    if (hc.desc.hxc_mode == TSBZ_HXC_SCF) hc.hxc_subs.push_back((int)s);
+    stage_max = std::max<long long>(stage_max, (long long)hs.n_k * c.n_bands * c.npts);
+  }
+  for (auto& hc : ctx->cells) work_max = std::max<long long>(work_max, (long long)hc.hxc_subs.size() * hc.dev.npts);
+  ctx->n_units = (long long)units.size();
+  ctx->ph_stride = ph_stride;
+  int rc;
+  if ((rc = dalloc(ctx, psi_e * es, &ctx->psi))) return rc;
+  if ((rc = dalloc(ctx, psi_e * es, &ctx->tA))) return rc;
+  if ((rc = dalloc(ctx, psi_e * es, &ctx->tB))) return rc;
+  if ((rc = dalloc(ctx, std::max<long long>(p_e, 1) * es, &ctx->P))) return rc;
+  if ((rc = dalloc(ctx, std::max<long long>(pa_e, 1) * es, &ctx->Pa))) return rc;
+  if ((rc = dalloc(ctx, ctx->n_units * ph_stride * es, &ctx->ph_half))) return rc;
+  if ((rc = dalloc(ctx, ctx->n_units * ph_stride * es, &ctx->ph_obs))) return rc;
+  if ((rc = dalloc_t(ctx, rho_e, &ctx->rho_part))) return rc;
+  if ((rc = dalloc_t(ctx, std::max<long long>(jk_e, 1), &ctx->jk_part))) return rc;
+  if ((rc = dalloc_t(ctx, std::max<long long>(nrm_e, 1), &ctx->nrm_part))) return rc;
+  if ((rc = dalloc_t(ctx, 3 * ctx->n_units, &ctx->q_half))) return rc;
+  if ((rc = dalloc_t(ctx, 3 * ctx->n_units, &ctx->q_obs))) return rc;
+  if ((rc = dalloc_t(ctx, 3 * ctx->n_units, &ctx->kcart))) return rc;
+  if ((rc = dalloc_t(ctx, ctx->n_units, &ctx->d_units))) return rc;
+  if ((rc = dalloc_t(ctx, ctx->subs.size(), &ctx->d_subs))) return rc;
+  if ((rc = dalloc_t(ctx, ctx->cells.size(), &ctx->d_cells))) return rc;
+  if ((rc = dalloc_t(ctx, ctx->subs.size(), &ctx->d_steps))) return rc;
+  if ((rc = dalloc_t(ctx, ctx->subs.size(), &ctx->d_status))) return rc;
+  if ((rc = dalloc_t(ctx, ctx->subs.size(), &ctx->d_mask))) return rc;
+  if ((rc = dalloc_t(ctx, std::max<long long>(work_max, 1), &ctx->work_a))) return rc;
+  if ((rc = dalloc_t(ctx, std::max<long long>(work_max, 1), &ctx->work_b))) return rc;
+  if ((rc = dalloc_t(ctx, stage_max, &ctx->staging))) return rc;
+  ctx->staging_elems = stage_max;
+  std::vector<SubDev> sd(ctx->subs.size());
+  for (size_t s = 0; s < ctx->subs.size(); ++s) {
+    HostSub& hs = ctx->subs[s];
+    HostCell& hc = ctx->cells[hs.cell];
+    const CellDev& c = hc.dev;
+    const int nf = 2 * hs.max_steps + 1;
+    if ((rc = dalloc_t(ctx, 3LL * nf, &hs.A_d))) return rc;
+    if ((rc = dalloc_t(ctx, 3LL * (hs.max_steps + 1), &hs.J))) return rc;
+    if ((rc = dalloc_t(ctx, 3, &hs.J0m))) return rc;
+    if ((rc = dalloc_t(ctx, c.npts, &hs.rho))) return rc;
+    if ((rc = dalloc_t(ctx, c.npts, &hs.vhxc))) return rc;
+    if ((rc = dalloc_t(ctx, (long long)hs.n_k * c.n_bands, &hs.norms))) return rc;
+    if ((rc = dalloc(ctx, (size_t)c.npts * (ctx->precision == TSBZ_FP64 ? 8 : 4), &hs.veff))) return rc;
+    if (hs.A.empty()) hs.A.assign(3LL * nf, 0.0);
+    hs.field_dirty = true;
+    SubDev& d = sd[s];
+    d.cell = hs.cell;
+    d.n_k = hs.n_k;
+    d.unit0 = hs.unit0;
+    d.max_steps = hs.max_steps;
+    d.n_field = nf;
+    d.hxc_frozen = hc.desc.hxc_mode == TSBZ_HXC_FROZEN;
+    d.xc = hc.desc.xc;
+    d.hartree = hc.desc.hartree;
+    d.dt = hs.dt;
+    d.A = hs.A_d;
+    d.J = hs.J;
+    d.J0m = hs.J0m;
+    d.rho = hs.rho;
+    d.vhxc = hs.vhxc;
+    d.veff = hs.veff;
+    d.norms = hs.norms;
+    d.step = ctx->d_steps + s;
+    d.status = ctx->d_status + s;
+    CK(cudaMemsetAsync(hs.vhxc, 0, sizeof(double) * c.npts, ctx->stream));
+    CK(cudaMemsetAsync(hs.J, 0, sizeof(double) * 3 * (hs.max_steps + 1), ctx->stream));
+    CK(cudaMemsetAsync(hs.J0m, 0, sizeof(double) * 3, ctx->stream));
+  }
+  std::vector<CellDev> cd;
+  for (auto& hc : ctx->cells) {
+    if (!hc.unit_ids.empty()) {
+      if ((rc = dalloc_t(ctx, hc.unit_ids.size(), &hc.d_unit_ids))) return rc;
+      CK(cudaMemcpyAsync(hc.d_unit_ids, hc.unit_ids.data(), sizeof(int) * hc.unit_ids.size(), cudaMemcpyHostToDevice,
+                         ctx->stream));
+    }
+    if (!hc.hxc_subs.empty()) {
+      if ((rc = dalloc_t(ctx, hc.hxc_subs.size(), &hc.d_hxc_subs))) return rc;
+      CK(cudaMemcpyAsync(hc.d_hxc_subs, hc.hxc_subs.data(), sizeof(int) * hc.hxc_subs.size(),
+                         cudaMemcpyHostToDevice, ctx->stream));
+    }
+    cd.push_back(hc.dev);
+  }
+  CK(cudaMemcpyAsync(ctx->d_units, units.data(), sizeof(UnitDev) * units.size(), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->d_subs, sd.data(), sizeof(SubDev) * sd.size(), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->d_cells, cd.data(), sizeof(CellDev) * cd.size(), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->kcart, kc.data(), sizeof(double) * kc.size(), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_steps, 0, sizeof(int) * ctx->subs.size(), ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int) * ctx->subs.size(), ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_mask, 0, sizeof(int) * ctx->subs.size(), ctx->stream));
+  CK(cudaMemsetAsync(ctx->rho_part, 0, sizeof(double) * std::max<long long>(rho_e, 1), ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->laid_out = true;
+  return TSBZ_OK;
+}
+
+int upload_fields(tsbz_ctx* ctx) {
+  for (auto& hs : ctx->subs)
+    if (hs.field_dirty) {
+      CK(cudaMemcpyAsync(hs.A_d, hs.A.data(), sizeof(double) * hs.A.size(), cudaMemcpyHostToDevice, ctx->stream));
+      hs.field_dirty = false;
+    }
+  return TSBZ_OK;
+}
+
+// Kernel families, dispatched on the precision.
+template <typename T> int run_field(tsbz_ctx* ctx, int mode) {
+  ev_start(ctx, FAM_FIELD);
+  for (auto& hc : ctx->cells) {
+    if (hc.unit_ids.empty()) continue;
+    launch_field<T>(make_set(ctx, hc), mode, ctx->stream);
+    ++ctx->launches;
+  }
+  ev_stop(ctx);
+  return TSBZ_OK;
+}
+
+template <typename T> int run_observe(tsbz_ctx* ctx, int fin_mode) {
+  for (auto& hc : ctx->cells) {
+    if (hc.unit_ids.empty()) continue;
+    LaunchSet L = make_set(ctx, hc);
+    ev_start(ctx, FAM_BRA);
+    launch_bra<T>(L, ctx->psi, ctx->Pa, 1, 1, ctx->stream);
+    ev_stop(ctx);
+    if (hc.dev.use_proj) ++ctx->launches;
+    ev_start(ctx, FAM_OBS);
+    launch_observe<T>(L, ctx->psi, ctx->rho_part, ctx->jk_part, ctx->nrm_part, ctx->stream);
+    ev_stop(ctx);
+    ++ctx->launches;
+  }
+  ev_start(ctx, FAM_FIN);
+  launch_finalize_t<T>(ctx->d_subs, (int)ctx->subs.size(), ctx->d_units, ctx->d_cells, ctx->q_obs, ctx->Pa,
+                       ctx->rho_part, ctx->jk_part, ctx->nrm_part, ctx->d_mask, fin_mode, ctx->stream);
+  ev_stop(ctx);
+  ++ctx->launches;
+  return TSBZ_OK;
+}
+
+template <typename T> int run_hxc(tsbz_ctx* ctx) {
+  ev_start(ctx, FAM_HXC);
+  for (auto& hc : ctx->cells) {
+    if (hc.hxc_subs.empty()) continue;
+    ctx->launches += launch_hxc_t<T>(ctx->d_subs, hc.d_hxc_subs, (int)hc.hxc_subs.size(), hc.dev, ctx->work_a,
+                                     ctx->work_b, hc.tw, ctx->stream);
+  }
+  ev_stop(ctx);
+  return TSBZ_OK;
+}
+
+template <typename T> int run_step(tsbz_ctx* ctx) {
+  run_field<T>(ctx, TSBZ_FIELD_STEP);
+  void* srcs[4] = {ctx->psi, ctx->tA, ctx->tB, ctx->tA};
+  void* dsts[4] = {ctx->tA, ctx->tB, ctx->tA, nullptr};
+  for (int m = 1; m <= 4; ++m) {
+    for (auto& hc : ctx->cells) {
+      if (hc.unit_ids.empty()) continue;
+      LaunchSet L = make_set(ctx, hc);
+      ev_start(ctx, FAM_BRA);
+      launch_bra<T>(L, srcs[m - 1], ctx->P, 0, 0, ctx->stream);
+      ev_stop(ctx);
+      if (hc.dev.use_proj) ++ctx->launches;
+      ev_start(ctx, FAM_STAGE);
+      launch_stage<T>(L, srcs[m - 1], dsts[m - 1], ctx->psi, ctx->P, m, ctx->stream);
+      ev_stop(ctx);
+      ++ctx->launches;
+    }
+  }
+  run_observe<T>(ctx, TSBZ_FIN_STEP);
+  run_hxc<T>(ctx);
+  return TSBZ_OK;
+}
+
+template <typename T> int run_init(tsbz_ctx* ctx, bool minus, bool plus) {
+  std::vector<int> mask(ctx->subs.size(), 0);
+  if (minus) {
+    for (size_t s = 0; s < ctx->subs.size(); ++s) mask[s] = ctx->subs[s].need_init ? 1 : 0;
+    CK(cudaMemcpyAsync(ctx->d_mask, mask.data(), sizeof(int) * mask.size(), cudaMemcpyHostToDevice, ctx->stream));
+    run_field<T>(ctx, TSBZ_FIELD_J0MINUS);
+    run_observe<T>(ctx, TSBZ_FIN_J0MINUS);
+    run_hxc<T>(ctx);
+    for (size_t s = 0; s < ctx->subs.size(); ++s) {
+      HostSub& hs = ctx->subs[s];
+      if (ctx->cells[hs.cell].desc.hxc_mode == TSBZ_HXC_FROZEN) {
+        launch_veff_frozen_t<T>(ctx->d_subs, (int)s, ctx->cells[hs.cell].dev, ctx->stream);
+        ++ctx->launches;
+      }
+    }
+  }
+  if (plus) {
+    for (size_t s = 0; s < ctx->subs.size(); ++s)
+      mask[s] = (ctx->subs[s].need_j0plus || ctx->subs[s].need_init) ? 1 : 0;
+    CK(cudaMemcpyAsync(ctx->d_mask, mask.data(), sizeof(int) * mask.size(), cudaMemcpyHostToDevice, ctx->stream));
+    run_field<T>(ctx, TSBZ_FIELD_J0PLUS);
+    run_observe<T>(ctx, TSBZ_FIN_J0PLUS);
+  }
+  return TSBZ_OK;
+}
+
+int ensure_ready(tsbz_ctx* ctx) {
+  if (!ctx->laid_out) return set_err(ctx, TSBZ_ESTATE, "no ground state loaded");
+  for (size_t s = 0; s < ctx->subs.size(); ++s)
+    if (!ctx->subs[s].loaded)
+      return set_err(ctx, TSBZ_ESTATE, "sub-simulation " + std::to_string(s) + " has no ground state");
+  int rc = upload_fields(ctx);
+  if (rc) return rc;
+  bool minus = false, plus = false;
+  for (auto& hs : ctx->subs) {
+    minus = minus || hs.need_init;
+    plus = plus || hs.need_init || (hs.need_j0plus && hs.steps == 0);
+  }
+  if (minus || plus) {
+    rc = ctx->precision == TSBZ_FP64 ? run_init<double>(ctx, minus, plus) : run_init<float>(ctx, minus, plus);
+    if (rc) return rc;
+    CK(cudaGetLastError());
+    for (auto& hs : ctx->subs) {
+      hs.need_init = false;
+      if (hs.steps == 0) hs.need_j0plus = false;
+    }
+  }
+  return TSBZ_OK;
+}
+
+int check_sub(tsbz_ctx* ctx, int s) {
+  if (!ctx) return TSBZ_EINVAL;
+  if (s < 0 || s >= (int)ctx->subs.size()) return set_err(ctx, TSBZ_EINVAL, "bad sub-simulation id");
+  return TSBZ_OK;
+}
+
+int copy_state_in(tsbz_ctx* ctx, int s, const double* psi, size_t n_elems, int on_device) {
+  HostSub& hs = ctx->subs[s];
+  const CellDev& c = ctx->cells[hs.cell].dev;
+  const long long need = (long long)hs.n_k * c.n_bands * c.npts;
+  if (!psi) return set_err(ctx, TSBZ_EINVAL, "psi is NULL");
+  if ((long long)n_elems != need)
+    return set_err(ctx, TSBZ_EINVAL, "psi has " + std::to_string(n_elems) + " complex values, expected " +
+                                         std::to_string(need));
+  CK(cudaMemcpyAsync(ctx->staging, psi, sizeof(double2) * need,
+                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+  char* dst = (char*)ctx->psi + ctx->unit_psi_off[hs.unit0] * ctx->elem_size();
+  if (ctx->precision == TSBZ_FP64)
+    launch_convert_in_t<double>(ctx->staging, dst, need, ctx->stream);
+  else
+    launch_convert_in_t<float>(ctx->staging, dst, need, ctx->stream);
+  ++ctx->launches;
+  CK(cudaGetLastError());
+  return TSBZ_OK;
+}
+
+int sync_and_check(tsbz_ctx* ctx) {
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaGetLastError());
+  return TSBZ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tsbz_version(void) { return 10000; }
+
+int tsbz_create(tsbz_ctx** out, int device, int precision, void* cuda_stream, const tsbz_alloc* alloc) {
+  if (!out) return TSBZ_EINVAL;
+  *out = nullptr;
+  if (precision != TSBZ_FP64 && precision != TSBZ_FP32) return TSBZ_EINVAL;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return TSBZ_ECUDA;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return TSBZ_ECUDA;
+  tsbz_ctx* ctx = new (std::nothrow) tsbz_ctx();
+  if (!ctx) return TSBZ_ENOMEM;
+  ctx->device = device;
+  ctx->precision = precision;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  if (alloc && alloc->alloc && alloc->free) {
+    ctx->has_alloc = true;
+    ctx->alloc = *alloc;
+  }
+  *out = ctx;
+  return TSBZ_OK;
+}
+
+int tsbz_init_cell(tsbz_ctx* ctx, const tsbz_cell_desc* d, int* cell_id) {
+  if (!ctx || !d || !cell_id) return TSBZ_EINVAL;
+  if (ctx->laid_out) return set_err(ctx, TSBZ_ESTATE, "cells must be added before the first ground state");
+  if (d->fd_nd < 1 || d->fd_nd > TSBZ_MAX_ND) return set_err(ctx, TSBZ_EINVAL, "fd_nd must be 1..6");
+  for (int ax = 0; ax < 3; ++ax) {
+    if (d->n[ax] < 2 * d->fd_nd + 1 || d->n[ax] > 1024)
+      return set_err(ctx, TSBZ_EINVAL, "grid size must be in [2 fd_nd + 1, 1024]");
+    if (!(d->a[ax] > 0.0)) return set_err(ctx, TSBZ_EINVAL, "cell edges must be positive");
+  }
+  if (d->n_bands < 1 || d->n_atoms < 0 || (d->n_atoms > 0 && !d->atom_frac))
+    return set_err(ctx, TSBZ_EINVAL, "bad band or atom count");
+  if (d->use_projectors && (d->n_atoms == 0 || !(d->proj_half > 0.0) || !(d->r_proj > 0.0)))
+    return set_err(ctx, TSBZ_EINVAL, "projectors need atoms, r_proj > 0 and proj_half > 0");
+  if (d->hxc_mode != TSBZ_HXC_SCF && d->hxc_mode != TSBZ_HXC_FROZEN) return set_err(ctx, TSBZ_EINVAL, "bad hxc_mode");
+  const long long npts = (long long)d->n[0] * d->n[1] * d->n[2];
+  if (npts > (1LL << 30)) return set_err(ctx, TSBZ_EINVAL, "grid too large");
+  HostCell hc;
+  hc.desc = *d;
+  hc.atoms.assign(d->atom_frac, d->atom_frac + 3 * d->n_atoms);
+  hc.desc.atom_frac = hc.atoms.data();
+  CellDev& c = hc.dev;
+  std::memset(&c, 0, sizeof(c));
+  c.n1 = d->n[0];
+  c.n2 = d->n[1];
+  c.n3 = d->n[2];
+  c.npts = (int)npts;
+  c.nmax = std::max(c.n1, std::max(c.n2, c.n3));
+  c.n_atoms = d->n_atoms;
+  c.use_proj = d->use_projectors ? 1 : 0;
+  c.n_proj = c.use_proj ? 4 * d->n_atoms : 0;
+  c.n_bands = d->n_bands;
+  c.nd = d->fd_nd;
+  c.n_tiles = (c.npts + TSBZ_PT - 1) / TSBZ_PT;
+  c.n_bgroups = (c.n_bands + TSBZ_BG - 1) / TSBZ_BG;
+  c.omega = d->a[0] * d->a[1] * d->a[2];
+  c.dv = c.omega / (double)npts;
+  c.occ = d->occ;
+  double cw[TSBZ_MAX_ND + 1], dw[TSBZ_MAX_ND + 1];
+  tsbz::fd_weights(d->fd_nd, cw, dw);
+  for (int ax = 0; ax < 3; ++ax) {
+    const double h = d->a[ax] / d->n[ax];
+    for (int m = 0; m <= d->fd_nd; ++m) {
+      c.lapw[ax][m] = cw[m] / (h * h);
+      c.gradw[ax][m] = dw[m] / h;
+    }
+    c.gsq_scale[ax] = 2.0 * 3.14159265358979323846 / d->a[ax];
+  }
+  tsbz::local_potential(hc.desc, hc.vloc);
+  std::vector<double> g1, d1, ekb;
+  if (c.use_proj) {
+    tsbz::projector_tables(hc.desc, g1, d1, hc.pnorm, c.nmax);
+  } else {
+    g1.assign(1, 0.0);
+    d1.assign(std::max(1, d->n_atoms * 3 * c.nmax), 0.0);
+    hc.pnorm.assign(std::max(1, 4 * d->n_atoms), 0.0);
+  }
+  if (d1.size() < (size_t)std::max(1, d->n_atoms * 3 * c.nmax)) d1.resize(std::max(1, d->n_atoms * 3 * c.nmax), 0.0);
+  for (int a = 0; a < d->n_atoms; ++a) {
+    ekb.push_back(d->e_kb_s);
+    for (int t = 0; t < 3; ++t) ekb.push_back(d->e_kb_p);
+  }
+  if (ekb.empty()) ekb.push_back(0.0);
+  double *vl, *gg, *dd, *pn, *ek;
+  int rc;
+  if ((rc = dalloc_t(ctx, hc.vloc.size(), &vl))) return rc;
+  if ((rc = dalloc_t(ctx, g1.size(), &gg))) return rc;
+  if ((rc = dalloc_t(ctx, d1.size(), &dd))) return rc;
+  if ((rc = dalloc_t(ctx, hc.pnorm.size(), &pn))) return rc;
+  if ((rc = dalloc_t(ctx, ekb.size(), &ek))) return rc;
+  CK(cudaMemcpy(vl, hc.vloc.data(), sizeof(double) * hc.vloc.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(gg, g1.data(), sizeof(double) * g1.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(dd, d1.data(), sizeof(double) * d1.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(pn, hc.pnorm.data(), sizeof(double) * hc.pnorm.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ek, ekb.data(), sizeof(double) * ekb.size(), cudaMemcpyHostToDevice));
+  c.vloc = vl;
+  c.g1 = gg;
+  c.d1 = dd;
+  c.pnorm = pn;
+  c.ekb = ek;
+  const int nn[3] = {c.n1, c.n2, c.n3};
+  for (int ax = 0; ax < 3; ++ax) {
+    std::vector<double2> tw(nn[ax]);
+    for (int m = 0; m < nn[ax]; ++m) {
+      const double ang = 2.0 * 3.14159265358979323846 * m / nn[ax];
+      tw[m] = make_double2(std::cos(ang), std::sin(ang));
+    }
+    if ((rc = dalloc_t(ctx, tw.size(), &hc.tw[ax]))) return rc;
+    CK(cudaMemcpy(hc.tw[ax], tw.data(), sizeof(double2) * tw.size(), cudaMemcpyHostToDevice));
+  }
+  ctx->cells.push_back(std::move(hc));
+  *cell_id = (int)ctx->cells.size() - 1;
+  return TSBZ_OK;
+}
+
+int tsbz_add_subsim(tsbz_ctx* ctx, int cell_id, int n_k, const double* k_cart, double dt, int max_steps,
+                    int* subsim_id) {
+  if (!ctx || !subsim_id) return TSBZ_EINVAL;
+  if (ctx->laid_out) return set_err(ctx, TSBZ_ESTATE, "sub-simulations must be added before the first ground state");
+  if (cell_id < 0 || cell_id >= (int)ctx->cells.size()) return set_err(ctx, TSBZ_EINVAL, "bad cell id");
+  if (n_k < 1 || !k_cart) return set_err(ctx, TSBZ_EINVAL, "need n_k >= 1 k-points");
+  if (!(dt > 0.0) || max_steps < 0 || max_steps > 100000000) return set_err(ctx, TSBZ_EINVAL, "bad dt or max_steps");
+  HostSub hs;
+  hs.cell = cell_id;
+  hs.n_k = n_k;
+  hs.k.assign(k_cart, k_cart + 3LL * n_k);
+  hs.dt = dt;
+  hs.max_steps = max_steps;
+  ctx->subs.push_back(std::move(hs));
+  *subsim_id = (int)ctx->subs.size() - 1;
+  return TSBZ_OK;
+}
+
+int tsbz_load_ground_state(tsbz_ctx* ctx, int s, const double* psi, size_t n_elems, int psi_on_device,
+                           const double* v_hxc_frozen) {
+  int rc = check_sub(ctx, s);
+  if (rc) return rc;
+  if ((rc = layout(ctx))) return rc;
+  HostSub& hs = ctx->subs[s];
+  HostCell& hc = ctx->cells[hs.cell];
+  if (hc.desc.hxc_mode == TSBZ_HXC_FROZEN) {
+    if (!v_hxc_frozen) return set_err(ctx, TSBZ_EINVAL, "frozen mode needs v_hxc_frozen");
+    CK(cudaMemcpyAsync(hs.vhxc, v_hxc_frozen, sizeof(double) * hc.dev.npts, cudaMemcpyHostToDevice, ctx->stream));
+  }
+  if ((rc = copy_state_in(ctx, s, psi, n_elems, psi_on_device))) return rc;
+  CK(cudaMemsetAsync(ctx->d_steps + s, 0, sizeof(int), ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_status + s, 0, sizeof(int), ctx->stream));
+  hs.steps = 0;
+  hs.loaded = true;
+  hs.need_init = true;
+  hs.need_j0plus = true;
+  return sync_and_check(ctx);
+}
+
+int tsbz_set_kick(tsbz_ctx* ctx, int s, double k0, const double dir[3]) {
+  if (!ctx || !dir) return TSBZ_EINVAL;
+  if (s < -1 || s >= (int)ctx->subs.size()) return set_err(ctx, TSBZ_EINVAL, "bad sub-simulation id");
+  for (size_t i = 0; i < ctx->subs.size(); ++i) {
+    if (s >= 0 && (int)i != s) continue;
+    HostSub& hs = ctx->subs[i];
+    if (hs.steps > 0) return set_err(ctx, TSBZ_ESTATE, "the field can only change before the first step");
+    const size_t nf = 2 * (size_t)hs.max_steps + 1;
+    hs.A.assign(3 * nf, 0.0);
+    for (size_t j = 0; j < nf; ++j)
+      for (int ax = 0; ax < 3; ++ax) hs.A[3 * j + ax] = -k0 * dir[ax];
+    hs.field_dirty = true;
+    hs.need_j0plus = true;
+  }
+  return TSBZ_OK;
+}
+
+int tsbz_set_field(tsbz_ctx* ctx, int s, int n_steps, const double* a_samples) {
+  int rc = check_sub(ctx, s);
+  if (rc) return rc;
+  HostSub& hs = ctx->subs[s];
+  if (!a_samples || n_steps < 0 || n_steps > hs.max_steps)
+    return set_err(ctx, TSBZ_EINVAL, "field needs 0 <= n_steps <= max_steps and samples");
+  if (hs.steps > 0) return set_err(ctx, TSBZ_ESTATE, "the field can only change before the first step");
+  const size_t nf = 2 * (size_t)hs.max_steps + 1;
+  hs.A.assign(3 * nf, 0.0);
+  std::memcpy(hs.A.data(), a_samples, sizeof(double) * 3 * (2 * (size_t)n_steps + 1));
+  hs.field_dirty = true;
+  hs.need_j0plus = true;
+  return TSBZ_OK;
+}
+
+int tsbz_propagate(tsbz_ctx* ctx, int n_steps) {
+  if (!ctx || n_steps < 0) return TSBZ_EINVAL;
+  int rc = ensure_ready(ctx);
+  if (rc) return rc;
+  for (size_t s = 0; s < ctx->subs.size(); ++s)
+    if (ctx->subs[s].steps + n_steps > ctx->subs[s].max_steps)
+      return set_err(ctx, TSBZ_EINVAL, "sub-simulation " + std::to_string(s) + " would exceed its max_steps");
+  ctx->ev_marks.clear();
+  ctx->ev_next = 0;
+  for (int i = 0; i < n_steps; ++i) {
+    rc = ctx->precision == TSBZ_FP64 ? run_step<double>(ctx) : run_step<float>(ctx);
+    if (rc) return rc;
+  }
+  CK(cudaGetLastError());
+  if ((rc = sync_and_check(ctx))) return rc;
+  for (auto& hs : ctx->subs) hs.steps += n_steps;
+  if (ctx->prof) {
+    for (int f = 0; f < 6; ++f) ctx->times[f] = 0.0;
+    for (auto& m : ctx->ev_marks) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ctx->ev_pool[m.second], ctx->ev_pool[m.second + 1]);
+      ctx->times[m.first] += ms;
+    }
+  }
+  std::vector<int> st(ctx->subs.size(), 0);
+  CK(cudaMemcpy(st.data(), ctx->d_status, sizeof(int) * st.size(), cudaMemcpyDeviceToHost));
+  for (size_t s = 0; s < st.size(); ++s)
+    if (st[s]) return set_err(ctx, TSBZ_ENONFINITE, "non-finite current in sub-simulation " + std::to_string(s));
+  return TSBZ_OK;
+}
+
+int tsbz_get_current(tsbz_ctx* ctx, int s, int first, int count, double* J, double* J0_minus) {
+  if (!ctx || first < 0 || count < 0 || (count > 0 && !J)) return TSBZ_EINVAL;
+  if (s < -1 || s >= (int)ctx->subs.size()) return set_err(ctx, TSBZ_EINVAL, "bad sub-simulation id");
+  int rc = ensure_ready(ctx);
+  if (rc) return rc;
+  if ((rc = sync_and_check(ctx))) return rc;
+  if (s >= 0) {
+    HostSub& hs = ctx->subs[s];
+    if (first + count > hs.steps + 1) return set_err(ctx, TSBZ_EINVAL, "requested steps not computed yet");
+    if (count) CK(cudaMemcpy(J, hs.J + 3LL * first, sizeof(double) * 3 * count, cudaMemcpyDeviceToHost));
+    if (J0_minus) CK(cudaMemcpy(J0_minus, hs.J0m, sizeof(double) * 3, cudaMemcpyDeviceToHost));
+    return TSBZ_OK;
+  }
+  const double dt0 = ctx->subs[0].dt;
+  for (auto& hs : ctx->subs) {
+    if (hs.dt != dt0) return set_err(ctx, TSBZ_EINVAL, "two-step average needs equal dt");
+    if (first + count > hs.steps + 1) return set_err(ctx, TSBZ_EINVAL, "requested steps not computed yet");
+  }
+  std::vector<double> acc(3 * (size_t)count, 0.0), buf(3 * (size_t)count), j0(3);
+  for (auto& hs : ctx->subs) {
+    if (count) CK(cudaMemcpy(buf.data(), hs.J + 3LL * first, sizeof(double) * 3 * count, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(j0.data(), hs.J0m, sizeof(double) * 3, cudaMemcpyDeviceToHost));
+    for (int i = 0; i < count; ++i)
+      for (int ax = 0; ax < 3; ++ax) acc[3 * i + ax] += buf[3 * i + ax] - j0[ax];
+  }
+  const double inv = 1.0 / (double)ctx->subs.size();
+  for (size_t i = 0; i < acc.size(); ++i) J[i] = acc[i] * inv;
+  if (J0_minus) J0_minus[0] = J0_minus[1] = J0_minus[2] = 0.0;
+  return TSBZ_OK;
+}
+
+int tsbz_get_density(tsbz_ctx* ctx, int s, double* rho, size_t cap) {
+  int rc = check_sub(ctx, s);
+  if (rc) return rc;
+  const CellDev& c = ctx->cells[ctx->subs[s].cell].dev;
+  if (!rho || cap < (size_t)c.npts) return set_err(ctx, TSBZ_EINVAL, "rho buffer too small");
+  if ((rc = ensure_ready(ctx))) return rc;
+  if ((rc = sync_and_check(ctx))) return rc;
+  CK(cudaMemcpy(rho, ctx->subs[s].rho, sizeof(double) * c.npts, cudaMemcpyDeviceToHost));
+  return TSBZ_OK;
+}
+
+int tsbz_get_norms(tsbz_ctx* ctx, int s, double* norms, size_t cap) {
+  int rc = check_sub(ctx, s);
+  if (rc) return rc;
+  const HostSub& hs = ctx->subs[s];
+  const size_t n = (size_t)hs.n_k * ctx->cells[hs.cell].dev.n_bands;
+  if (!norms || cap < n) return set_err(ctx, TSBZ_EINVAL, "norms buffer too small");
+  if ((rc = ensure_ready(ctx))) return rc;
+  if ((rc = sync_and_check(ctx))) return rc;
+  CK(cudaMemcpy(norms, hs.norms, sizeof(double) * n, cudaMemcpyDeviceToHost));
+  return TSBZ_OK;
+}
+
+int tsbz_get_step(tsbz_ctx* ctx, int s, int* step) {
+  int rc = check_sub(ctx, s);
+  if (rc) return rc;
+  if (!step) return TSBZ_EINVAL;
+  *step = ctx->subs[s].steps;
+  return TSBZ_OK;
+}
+
+int tsbz_get_state(tsbz_ctx* ctx, int s, double* psi, size_t cap, int* step) {
+  int rc = check_sub(ctx, s);
+  if (rc) return rc;
+  if (!ctx->laid_out) return set_err(ctx, TSBZ_ESTATE, "no state");
+  const HostSub& hs = ctx->subs[s];
+  const CellDev& c = ctx->cells[hs.cell].dev;
+  const long long n = (long long)hs.n_k * c.n_bands * c.npts;
+  if (!psi || (long long)cap < n) return set_err(ctx, TSBZ_EINVAL, "psi buffer too small");
+  const char* src = (const char*)ctx->psi + ctx->unit_psi_off[hs.unit0] * ctx->elem_size();
+  if (ctx->precision == TSBZ_FP64)
+    launch_convert_out_t<double>(src, ctx->staging, n, ctx->stream);
+  else
+    launch_convert_out_t<float>(src, ctx->staging, n, ctx->stream);
+  ++ctx->launches;
+  CK(cudaMemcpyAsync(psi, ctx->staging, sizeof(double2) * n, cudaMemcpyDeviceToHost, ctx->stream));
+  if ((rc = sync_and_check(ctx))) return rc;
+  if (step) *step = hs.steps;
+  return TSBZ_OK;
+}
+
+int tsbz_load_state(tsbz_ctx* ctx, int s, const double* psi, size_t n_elems, int step) {
+  int rc = check_sub(ctx, s);
+  if (rc) return rc;
+  if (!ctx->laid_out || !ctx->subs[s].loaded) return set_err(ctx, TSBZ_ESTATE, "load a ground state first");
+  HostSub& hs = ctx->subs[s];
+  if (step < 0 || step > hs.max_steps) return set_err(ctx, TSBZ_EINVAL, "bad step");
+  if ((rc = ensure_ready(ctx))) return rc;
+  if ((rc = copy_state_in(ctx, s, psi, n_elems, 0))) return rc;
+  CK(cudaMemcpyAsync(ctx->d_steps + s, &step, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+  hs.steps = step;
+  // rho, norms and v_Hxc from the restored orbitals (no current is written)
+  std::vector<int> mask(ctx->subs.size(), 0);
+  CK(cudaMemcpyAsync(ctx->d_mask, mask.data(), sizeof(int) * mask.size(), cudaMemcpyHostToDevice, ctx->stream));
+  if (ctx->precision == TSBZ_FP64) {
+    run_field<double>(ctx, TSBZ_FIELD_J0MINUS);
+    run_observe<double>(ctx, TSBZ_FIN_J0MINUS);
+    run_hxc<double>(ctx);
+  } else {
+    run_field<float>(ctx, TSBZ_FIELD_J0MINUS);
+    run_observe<float>(ctx, TSBZ_FIN_J0MINUS);
+    run_hxc<float>(ctx);
+  }
+  return sync_and_check(ctx);
+}
+
+int tsbz_get_cell_tables(tsbz_ctx* ctx, int cell_id, double* vloc, size_t cap, double* proj_norms, size_t ncap) {
+  if (!ctx || cell_id < 0 || cell_id >= (int)ctx->cells.size()) return TSBZ_EINVAL;
+  const HostCell& hc = ctx->cells[cell_id];
+  if (vloc) {
+    if (cap < hc.vloc.size()) return set_err(ctx, TSBZ_EINVAL, "vloc buffer too small");
+    std::memcpy(vloc, hc.vloc.data(), sizeof(double) * hc.vloc.size());
+  }
+  if (proj_norms) {
+    const size_t n = 4 * (size_t)hc.desc.n_atoms;
+    if (ncap < n) return set_err(ctx, TSBZ_EINVAL, "norm buffer too small");
+    if (hc.dev.use_proj) std::memcpy(proj_norms, hc.pnorm.data(), sizeof(double) * n);
+  }
+  return TSBZ_OK;
+}
+
+int tsbz_get_launch_count(tsbz_ctx* ctx, long long* launches) {
+  if (!ctx || !launches) return TSBZ_EINVAL;
+  *launches = ctx->launches;
+  return TSBZ_OK;
+}
+
+int tsbz_set_profiling(tsbz_ctx* ctx, int on) {
+  if (!ctx) return TSBZ_EINVAL;
+  ctx->prof = on != 0;
+  return TSBZ_OK;
+}
+
+int tsbz_get_timings(tsbz_ctx* ctx, double* times_ms, int n) {
+  if (!ctx || !times_ms || n < 0) return TSBZ_EINVAL;
+  for (int i = 0; i < n && i < 6; ++i) times_ms[i] = ctx->times[i];
+  return TSBZ_OK;
+}
+
+const char* tsbz_last_error(tsbz_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+void tsbz_destroy(tsbz_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  else cudaDeviceSynchronize();
+  for (void* p : ctx->owned) {
+    if (ctx->has_alloc)
+      ctx->alloc.free(p, ctx->alloc.user);
+    else
+      cudaFree(p);
+  }
+  for (auto e : ctx->ev_pool) cudaEventDestroy(e);
+  delete ctx;
+}
+
+}  // extern "C"

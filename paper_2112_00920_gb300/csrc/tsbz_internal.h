@@ -1,0 +1,112 @@
+// Internal structures shared by the host runtime and the CUDA kernels.
+//
+// Data layout in device memory (one context):
+//   psi, tA, tB : complex T, [unit][band][n3][n2][n1]; a unit is one k-point
+//                 of one sub-simulation with all its bands (psi_off per unit)
+//   P           : complex T, [unit][band][n_proj]          projections <beta~_j|t_b>
+//   Pa          : complex T, [unit][band][n_proj][4]        <beta~_j|u>, <d_a beta~_j|u>
+//   rho_part    : double,    [unit][band group][n_pts]      sum_b occ |u_b(r)|^2
+//   jk_part     : double,    [unit][tile][band group][3]    sum occ Re(u* (-i grad) u)
+//   nrm_part    : double,    [unit][tile][band]             sum_r |u_b(r)|^2 per tile
+//   per sub-simulation: rho, v_hxc, v_eff (T), J history, J(0-), norms, step.
+#pragma once
+#include <cstdint>
+#include <cstddef>
+#include <vector_types.h>
+
+#define TSBZ_MAX_ND 6
+#define TSBZ_PT 128        // points per CTA in the point-parallel kernels
+#define TSBZ_BG 32         // max bands per band group in the point-parallel kernels
+
+struct CellDev {
+  int n1, n2, n3, npts, nmax;
+  int n_atoms, n_proj, n_bands;
+  int nd;
+  int n_tiles;       // ceil(npts / TSBZ_PT)
+  int n_bgroups;     // ceil(n_bands / TSBZ_BG)
+  int use_proj;
+  double dv, omega, occ;
+  double lapw[3][TSBZ_MAX_ND + 1];   // c_m / h_ax^2 (m = 0..nd)
+  double gradw[3][TSBZ_MAX_ND + 1];  // d_m / h_ax   (m = 1..nd)
+  double gsq_scale[3];               // (2 pi / a_ax)
+  const double* g1;     // [n_atoms][3][nmax] Gaussian factor exp(-d^2/(2 rc^2)), 0 outside the box
+  const double* d1;     // [n_atoms][3][nmax] minimum-image displacement, 0 outside the box
+  const double* pnorm;  // [n_atoms][4]        N_s, N_px, N_py, N_pz
+  const double* ekb;    // [n_proj]
+  const double* vloc;   // [npts]
+};
+
+struct UnitDev {
+  long long psi_off;   // complex elements
+  long long p_off;     // complex elements (P)
+  long long pa_off;    // complex elements (Pa)
+  long long rho_off;   // doubles
+  long long jk_off;    // doubles
+  long long nrm_off;   // doubles
+  int sub;             // sub-simulation index
+  int kloc;            // k index within the sub-simulation
+};
+
+struct SubDev {
+  int cell;
+  int n_k;
+  int unit0;
+  int max_steps;
+  int n_field;         // number of field samples available (2 n + 1)
+  int hxc_frozen;
+  int xc, hartree;
+  double dt;
+  const double* A;     // [n_field][3]
+  double* J;           // [max_steps + 1][3]
+  double* J0m;         // [3]
+  double* rho;         // [npts]
+  double* vhxc;        // [npts]
+  void* veff;          // [npts] in T
+  double* norms;       // [n_k][n_bands]
+  int* step;           // steps done
+  int* status;         // non-zero: non-finite current seen
+};
+
+// Finalize modes.
+#define TSBZ_FIN_J0MINUS 0   // write J(0-)
+#define TSBZ_FIN_J0PLUS 1    // write J[0] (t = 0+), only at step 0
+#define TSBZ_FIN_STEP 2      // write J[step + 1] and advance the step
+// Field modes (which q the observation tables use).
+#define TSBZ_FIELD_STEP 0    // q_half = k + A(t_n + dt/2), q_obs = k + A(t_{n+1})
+#define TSBZ_FIELD_J0PLUS 1  // q_obs = k + A(0+)
+#define TSBZ_FIELD_J0MINUS 2 // q_obs = k
+
+struct LaunchSet {
+  // Everything one kernel family needs for the units of one cell.
+  CellDev cell;
+  const UnitDev* units;   // global unit table
+  const int* unit_ids;    // units of this cell
+  int n_units;
+  const SubDev* subs;
+  const double* kcart;    // [unit][3]
+  double* q_half;         // [unit][3]
+  double* q_obs;          // [unit][3]
+  void* ph_half;          // [unit][n_atoms*3*nmax] complex T
+  void* ph_obs;
+  long long ph_stride;    // complex elements per unit
+};
+
+// Launchers (templated on the real type in tsbz_kernels.cuh, instantiated per precision).
+template <typename T> void launch_field(const LaunchSet& L, int mode, void* stream);
+template <typename T>
+void launch_bra(const LaunchSet& L, const void* src, void* P, int with_d, int use_obs, void* stream);
+template <typename T>
+void launch_stage(const LaunchSet& L, const void* tin, void* tout, void* psi, const void* P, int m, void* stream);
+template <typename T>
+void launch_observe(const LaunchSet& L, const void* psi, double* rho_part, double* jk_part, double* nrm_part,
+                    void* stream);
+template <typename T>
+void launch_finalize_t(const SubDev* subs, int n_subs, const UnitDev* units, const CellDev* cells_dev,
+                       const double* q_obs, const void* Pa, const double* rho_part, const double* jk_part,
+                       const double* nrm_part, const int* mask, int mode, void* stream);
+template <typename T>
+int launch_hxc_t(const SubDev* subs_dev, const int* sub_ids_dev, int n_subs, const CellDev& c, double2* wa,
+                 double2* wb, double2* const tw[3], void* stream);
+template <typename T> void launch_convert_in_t(const double2* src, void* dst, long long n, void* stream);
+template <typename T> void launch_convert_out_t(const void* src, double2* dst, long long n, void* stream);
+template <typename T> void launch_veff_frozen_t(const SubDev* subs_dev, int s, const CellDev& c, void* stream);

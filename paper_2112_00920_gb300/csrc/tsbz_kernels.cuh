@@ -1,0 +1,696 @@
+// CUDA kernels of the propagation step, templated on the real type T of
+// the orbital arithmetic (double or float).  Density, current and v_Hxc
+// are accumulated in double in both cases.
+//
+// One time step n -> n+1 of every sub-simulation (Eq. 1 with Eq. 2's h):
+//   field   : q_half = k + A(t_n + dt/2), q_obs = k + A(t_{n+1}) and the
+//             per-axis projector phase tables exp(i q_ax d_ax)
+//   4 stages m = 1..4 of the Taylor recurrence t_m = (-i dt/m) h t_{m-1}:
+//     bra   : P_jb = dV sum_r conj(beta~_j(r)) t_b(r)        (projector contraction)
+//     stage : t_m = (-i dt/m)[-1/2 lap t - i q.grad t + (q^2/2 + v_eff) t
+//                              + sum_j E_j beta~_j P_jb]; psi accumulates sum_m t_m
+//   observe : Pa = <beta~_j|u>, <d_a beta~_j|u> at q_obs; per-tile sums of
+//             occ |u|^2 (Eq. 3), Re(u* (-i grad) u) and |u_b|^2
+//   finalize: per sub-simulation rho (Eq. 3), norms and
+//             J = -(1/(Omega N_k)) sum occ <u|pi|u> (Eqs. 5-6) in a fixed order
+//   hxc     : v_H = F^-1[4 pi rho(G)/G^2] (G = 0 dropped) + PZ81 v_xc; v_eff = v_loc + v_Hxc
+// with beta~_j(r) = beta_j(d) exp(-i q.d), beta separable per axis:
+//   beta = pnorm * g_x g_y g_z * {1, d_x, d_y, d_z},  exp(i q.d) = prod_ax exp(i q_ax d_ax).
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include "tsbz_internal.h"
+
+template <typename T> struct Cplx;
+template <> struct Cplx<double> { using type = double2; };
+template <> struct Cplx<float> { using type = float2; };
+
+template <typename V> __device__ __forceinline__ V cmk(decltype(V().x) a, decltype(V().x) b) { V r; r.x = a; r.y = b; return r; }
+template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return cmk<V>(a.x + b.x, a.y + b.y); }
+template <typename V> __device__ __forceinline__ V csub(V a, V b) { return cmk<V>(a.x - b.x, a.y - b.y); }
+template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
+  return cmk<V>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// conj(a) * b
+template <typename V> __device__ __forceinline__ V cmulc(V a, V b) {
+  return cmk<V>(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+template <typename V, typename R> __device__ __forceinline__ V cscale(V a, R s) { return cmk<V>(a.x * s, a.y * s); }
+// acc += a * b
+template <typename V> __device__ __forceinline__ void cfma(V& acc, V a, V b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+}
+// acc += s * b (s real)
+template <typename V, typename R> __device__ __forceinline__ void rfma(V& acc, R s, V b) {
+  acc.x = fma(s, b.x, acc.x);
+  acc.y = fma(s, b.y, acc.y);
+}
+
+__device__ __forceinline__ int wrap_idx(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+// ----------------------------------------------------------------------------
+// field: q vectors and phase tables of every unit (k-point) of one cell
+// ----------------------------------------------------------------------------
+template <typename T>
+__global__ void k_field(LaunchSet L, int mode) {
+  using V = typename Cplx<T>::type;
+  const int u = L.unit_ids[blockIdx.x];
+  const UnitDev U = L.units[u];
+  const SubDev S = L.subs[U.sub];
+  const CellDev& c = L.cell;
+  double ah[3] = {0.0, 0.0, 0.0}, ao[3] = {0.0, 0.0, 0.0};
+  if (mode == TSBZ_FIELD_STEP) {
+    const int step = *S.step;
+    const int jh = 2 * step + 1, jo = 2 * step + 2;
+    if (jo < S.n_field) {
+      for (int ax = 0; ax < 3; ++ax) {
+        ah[ax] = S.A[3 * jh + ax];
+        ao[ax] = S.A[3 * jo + ax];
+      }
+    }
+  } else if (mode == TSBZ_FIELD_J0PLUS) {
+    for (int ax = 0; ax < 3; ++ax) ao[ax] = S.A[ax];
+  }
+  double qh[3], qo[3];
+  for (int ax = 0; ax < 3; ++ax) {
+    qh[ax] = L.kcart[3 * u + ax] + ah[ax];
+    qo[ax] = L.kcart[3 * u + ax] + ao[ax];
+  }
+  if (threadIdx.x < 3) {
+    L.q_half[3 * u + threadIdx.x] = qh[threadIdx.x];
+    L.q_obs[3 * u + threadIdx.x] = qo[threadIdx.x];
+  }
+  V* phh = (V*)L.ph_half + (long long)u * L.ph_stride;
+  V* pho = (V*)L.ph_obs + (long long)u * L.ph_stride;
+  const int tab = c.n_atoms * 3 * c.nmax;
+  for (int i = threadIdx.x; i < tab; i += blockDim.x) {
+    const int ax = (i / c.nmax) % 3;
+    const double d = c.d1[i];
+    double s, co;
+    sincos(qh[ax] * d, &s, &co);
+    phh[i] = cmk<V>((T)co, (T)s);
+    sincos(qo[ax] * d, &s, &co);
+    pho[i] = cmk<V>((T)co, (T)s);
+  }
+}
+
+// ----------------------------------------------------------------------------
+// bra: P[u][b][row] = dV sum_r C_row(r) t_b(r), C = conj(beta~) (times d_a for
+// the current rows).  Register-blocked complex GEMM (rows x bands x points)
+// with the C tile generated in shared memory from the separable tables.
+//   NW = 1: rows j = 0..n_proj-1              (projections for the ket)
+//   NW = 4: rows 4 j + a, a = 0 (beta~), 1..3 (d_x, d_y, d_z times beta~)
+// grid (row blocks, band blocks, units), 256 threads.
+// ----------------------------------------------------------------------------
+template <typename T, int NW>
+__global__ void __launch_bounds__(256) k_bra(LaunchSet L, const typename Cplx<T>::type* __restrict__ src,
+                                             typename Cplx<T>::type* __restrict__ P, int use_obs) {
+  using V = typename Cplx<T>::type;
+  constexpr int RB = 32, BB = 16;
+  constexpr int KT = sizeof(T) == 8 ? 32 : 64;
+  constexpr int APB = RB / (4 * NW);
+  __shared__ V Cs[KT][RB];
+  __shared__ V Us[KT][BB];
+  __shared__ V red[RB][BB];
+  const CellDev& c = L.cell;
+  const int u = L.unit_ids[blockIdx.z];
+  const UnitDev U = L.units[u];
+  const int rows = c.n_proj * NW;
+  const int a0 = blockIdx.x * APB;
+  const int bb0 = blockIdx.y * BB;
+  const V* ph = (const V*)(use_obs ? L.ph_obs : L.ph_half) + (long long)u * L.ph_stride;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int rg = lane >> 2, bg = lane & 3;
+  const int nm = c.nmax;
+  const V zero = cmk<V>((T)0, (T)0);
+  V acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = zero;
+  const V* srcU = src + U.psi_off;
+  for (int p0 = 0; p0 < c.npts; p0 += KT) {
+    __syncthreads();
+    for (int i = tid; i < KT * APB; i += 256) {
+      const int kk = i % KT, al = i / KT;
+      const int p = p0 + kk, a = a0 + al;
+      V vals[4 * NW];
+#pragma unroll
+      for (int r = 0; r < 4 * NW; ++r) vals[r] = zero;
+      if (p < c.npts && a < c.n_atoms) {
+        const int ix = p % c.n1, iy = (p / c.n1) % c.n2, iz = p / (c.n1 * c.n2);
+        const double* ga = c.g1 + (long long)a * 3 * nm;
+        const double* da = c.d1 + (long long)a * 3 * nm;
+        const T g = (T)(ga[ix] * ga[nm + iy] * ga[2 * nm + iz]);
+        const T d[3] = {(T)da[ix], (T)da[nm + iy], (T)da[2 * nm + iz]};
+        const V* pa = ph + (long long)a * 3 * nm;
+        const V f = cscale(cmul(cmul(pa[ix], pa[nm + iy]), pa[2 * nm + iz]), g);
+        const double* pn = c.pnorm + 4 * a;
+        const T w[4] = {(T)pn[0], (T)pn[1] * d[0], (T)pn[2] * d[1], (T)pn[3] * d[2]};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          if (NW == 1) {
+            vals[t] = cscale(f, w[t]);
+          } else {
+            vals[4 * t + 0] = cscale(f, w[t]);
+            vals[4 * t + 1] = cscale(f, w[t] * d[0]);
+            vals[4 * t + 2] = cscale(f, w[t] * d[1]);
+            vals[4 * t + 3] = cscale(f, w[t] * d[2]);
+          }
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < 4 * NW; ++r) Cs[kk][al * 4 * NW + r] = vals[r];
+    }
+    for (int i = tid; i < KT * BB; i += 256) {
+      const int kk = i % KT, b = i / KT;
+      const int p = p0 + kk, band = bb0 + b;
+      V v = zero;
+      if (p < c.npts && band < c.n_bands) v = srcU[(long long)band * c.npts + p];
+      Us[kk][b] = v;
+    }
+    __syncthreads();
+    for (int kk = warp; kk < KT; kk += 8) {
+      V cv[4], uv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        cv[i] = Cs[kk][rg * 4 + i];
+        uv[i] = Us[kk][bg * 4 + i];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) cfma(acc[i][j], cv[i], uv[j]);
+    }
+  }
+  for (int w = 0; w < 8; ++w) {
+    __syncthreads();
+    if (warp == w) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          V prev = (w == 0) ? zero : red[rg * 4 + i][bg * 4 + j];
+          red[rg * 4 + i][bg * 4 + j] = cadd(prev, acc[i][j]);
+        }
+    }
+  }
+  __syncthreads();
+  const long long off = (NW == 1) ? U.p_off : U.pa_off;
+  const T dv = (T)c.dv;
+  for (int i = tid; i < RB * BB; i += 256) {
+    const int r = i % RB, b = i / RB;
+    const int row = blockIdx.x * RB + r, band = bb0 + b;
+    if (row < rows && band < c.n_bands) P[off + (long long)band * rows + row] = cscale(red[r][b], dv);
+  }
+}
+
+// ----------------------------------------------------------------------------
+// stage m of the Taylor recurrence for all bands of one unit and TSBZ_PT points
+//   t_m = (-i dt/m) [ -1/2 lap t - i q.grad t + (|q|^2/2 + v_eff) t + V_NL t ]
+//   m = 1: write t_1                      m = 2: write t_2, psi += t_1 + t_2
+//   m = 3: write t_3, psi += t_3          m = 4: psi += t_4
+// V_NL t = sum_a conj(phase_a) g_a [W_s + d_x W_px + d_y W_py + d_z W_pz],
+// W_j = pnorm E_j P_jb staged in shared memory per band chunk.
+// grid (point tiles, units), TSBZ_PT threads, dynamic smem BC * n_proj complex.
+// ----------------------------------------------------------------------------
+template <typename T, int BC>
+__global__ void __launch_bounds__(TSBZ_PT) k_stage(LaunchSet L, const typename Cplx<T>::type* __restrict__ tin,
+                                                   typename Cplx<T>::type* __restrict__ tout,
+                                                   typename Cplx<T>::type* __restrict__ psi,
+                                                   const typename Cplx<T>::type* __restrict__ P, int m) {
+  using V = typename Cplx<T>::type;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* Ws = reinterpret_cast<V*>(smraw);
+  const CellDev& c = L.cell;
+  const int u = L.unit_ids[blockIdx.y];
+  const UnitDev U = L.units[u];
+  const SubDev S = L.subs[U.sub];
+  const int p = blockIdx.x * TSBZ_PT + threadIdx.x;
+  const bool valid = p < c.npts;
+  const int pp = valid ? p : 0;
+  const int ix = pp % c.n1, iy = (pp / c.n1) % c.n2, iz = pp / (c.n1 * c.n2);
+  const int n12 = c.n1 * c.n2;
+  const double* qd = L.q_half + 3 * u;
+  const T q[3] = {(T)qd[0], (T)qd[1], (T)qd[2]};
+  const T q2h = (T)(0.5 * (qd[0] * qd[0] + qd[1] * qd[1] + qd[2] * qd[2]));
+  const T v = valid ? reinterpret_cast<const T*>(S.veff)[pp] : (T)0;
+  const T diag = q2h + v;
+  const T hdt = (T)(S.dt / m);
+  const V* ph = (const V*)L.ph_half + (long long)u * L.ph_stride;
+  const int nm = c.nmax;
+  const V zero = cmk<V>((T)0, (T)0);
+  __shared__ T lw[3][TSBZ_MAX_ND + 1], gw[3][TSBZ_MAX_ND + 1];
+  if (threadIdx.x < 3 * (TSBZ_MAX_ND + 1)) {
+    const int ax = threadIdx.x / (TSBZ_MAX_ND + 1), mm = threadIdx.x % (TSBZ_MAX_ND + 1);
+    lw[ax][mm] = (T)(-0.5 * c.lapw[ax][mm]);
+    gw[ax][mm] = (T)c.gradw[ax][mm];
+  }
+  for (int b0 = 0; b0 < c.n_bands; b0 += BC) {
+    __syncthreads();
+    if (c.use_proj) {
+      for (int i = threadIdx.x; i < BC * c.n_proj; i += TSBZ_PT) {
+        const int bl = i / c.n_proj, j = i % c.n_proj, b = b0 + bl;
+        V w = zero;
+        if (b < c.n_bands) w = cscale(P[U.p_off + (long long)b * c.n_proj + j], (T)(c.pnorm[j] * c.ekb[j]));
+        Ws[i] = w;
+      }
+    }
+    __syncthreads();
+    if (!valid) continue;
+    V ket[BC];
+#pragma unroll
+    for (int bl = 0; bl < BC; ++bl) ket[bl] = zero;
+    if (c.use_proj) {
+      for (int a = 0; a < c.n_atoms; ++a) {
+        const double* ga = c.g1 + (long long)a * 3 * nm;
+        const double* da = c.d1 + (long long)a * 3 * nm;
+        const T g = (T)(ga[ix] * ga[nm + iy] * ga[2 * nm + iz]);
+        const T dx = (T)da[ix], dy = (T)da[nm + iy], dz = (T)da[2 * nm + iz];
+        const V* pa = ph + (long long)a * 3 * nm;
+        const V fph = cmul(cmul(pa[ix], pa[nm + iy]), pa[2 * nm + iz]);
+        const V f = cmk<V>(fph.x * g, -fph.y * g);   // g * exp(-i q.d)
+#pragma unroll
+        for (int bl = 0; bl < BC; ++bl) {
+          const V* wb = Ws + bl * c.n_proj + 4 * a;
+          V w = wb[0];
+          rfma(w, dx, wb[1]);
+          rfma(w, dy, wb[2]);
+          rfma(w, dz, wb[3]);
+          cfma(ket[bl], f, w);
+        }
+      }
+    }
+#pragma unroll
+    for (int bl = 0; bl < BC; ++bl) {
+      const int b = b0 + bl;
+      if (b >= c.n_bands) break;
+      const long long base = U.psi_off + (long long)b * c.npts;
+      const V* tb = tin + base;
+      const V ce = tb[pp];
+      // h t (local part), lap scaled by -1/2 through lw
+      V h = cmk<V>(ce.x * (lw[0][0] + lw[1][0] + lw[2][0] + diag), ce.y * (lw[0][0] + lw[1][0] + lw[2][0] + diag));
+      V qg = zero;
+      const int rowb = iz * n12 + iy * c.n1;
+      for (int mm = 1; mm <= c.nd; ++mm) {
+        // x
+        {
+          const V up = tb[rowb + wrap_idx(ix + mm, c.n1)];
+          const V dn = tb[rowb + wrap_idx(ix - mm, c.n1)];
+          rfma(h, lw[0][mm], cadd(up, dn));
+          rfma(qg, q[0] * gw[0][mm], csub(up, dn));
+        }
+        // y
+        {
+          const V up = tb[iz * n12 + wrap_idx(iy + mm, c.n2) * c.n1 + ix];
+          const V dn = tb[iz * n12 + wrap_idx(iy - mm, c.n2) * c.n1 + ix];
+          rfma(h, lw[1][mm], cadd(up, dn));
+          rfma(qg, q[1] * gw[1][mm], csub(up, dn));
+        }
+        // z
+        {
+          const V up = tb[wrap_idx(iz + mm, c.n3) * n12 + iy * c.n1 + ix];
+          const V dn = tb[wrap_idx(iz - mm, c.n3) * n12 + iy * c.n1 + ix];
+          rfma(h, lw[2][mm], cadd(up, dn));
+          rfma(qg, q[2] * gw[2][mm], csub(up, dn));
+        }
+      }
+      // -i q.grad t
+      h.x += qg.y;
+      h.y -= qg.x;
+      h = cadd(h, ket[bl]);
+      // t_m = (-i dt/m) h
+      const V t = cmk<V>(hdt * h.y, -hdt * h.x);
+      if (m < 4) tout[base + pp] = t;
+      if (m == 2) {
+        psi[base + pp] = cadd(psi[base + pp], cadd(ce, t));
+      } else if (m >= 3) {
+        psi[base + pp] = cadd(psi[base + pp], t);
+      }
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// observe: per (unit, point tile, band group) sums for rho, kinetic current
+// and band norms.  grid (point tiles, units, band groups), TSBZ_PT threads.
+// ----------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(TSBZ_PT) k_observe(LaunchSet L, const typename Cplx<T>::type* __restrict__ psi,
+                                                     double* __restrict__ rho_part, double* __restrict__ jk_part,
+                                                     double* __restrict__ nrm_part) {
+  using V = typename Cplx<T>::type;
+  __shared__ double red_n[TSBZ_BG][TSBZ_PT];
+  __shared__ double red_j[3][TSBZ_PT / 32];
+  const CellDev& c = L.cell;
+  const int u = L.unit_ids[blockIdx.y];
+  const UnitDev U = L.units[u];
+  const int tile = blockIdx.x, grp = blockIdx.z;
+  const int p = tile * TSBZ_PT + threadIdx.x;
+  const bool valid = p < c.npts;
+  const int pp = valid ? p : 0;
+  const int ix = pp % c.n1, iy = (pp / c.n1) % c.n2, iz = pp / (c.n1 * c.n2);
+  const int n12 = c.n1 * c.n2;
+  const int b_begin = grp * TSBZ_BG;
+  const int b_end = min(c.n_bands, b_begin + TSBZ_BG);
+  double rho = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
+  for (int b = b_begin; b < b_end; ++b) {
+    double n2 = 0.0;
+    if (valid) {
+      const V* tb = psi + U.psi_off + (long long)b * c.npts;
+      const V ce = tb[pp];
+      n2 = (double)ce.x * ce.x + (double)ce.y * ce.y;
+      rho += n2;
+      V g[3];
+      for (int ax = 0; ax < 3; ++ax) g[ax] = cmk<V>((T)0, (T)0);
+      for (int mm = 1; mm <= c.nd; ++mm) {
+        const T wx = (T)c.gradw[0][mm], wy = (T)c.gradw[1][mm], wz = (T)c.gradw[2][mm];
+        const int rowb = iz * n12 + iy * c.n1;
+        rfma(g[0], wx, csub(tb[rowb + wrap_idx(ix + mm, c.n1)], tb[rowb + wrap_idx(ix - mm, c.n1)]));
+        rfma(g[1], wy, csub(tb[iz * n12 + wrap_idx(iy + mm, c.n2) * c.n1 + ix],
+                            tb[iz * n12 + wrap_idx(iy - mm, c.n2) * c.n1 + ix]));
+        rfma(g[2], wz, csub(tb[wrap_idx(iz + mm, c.n3) * n12 + iy * c.n1 + ix],
+                            tb[wrap_idx(iz - mm, c.n3) * n12 + iy * c.n1 + ix]));
+      }
+      // Re(conj(u) (-i g)) = u_r g_i - u_i g_r
+      jx += (double)ce.x * g[0].y - (double)ce.y * g[0].x;
+      jy += (double)ce.x * g[1].y - (double)ce.y * g[1].x;
+      jz += (double)ce.x * g[2].y - (double)ce.y * g[2].x;
+    }
+    red_n[b - b_begin][threadIdx.x] = n2;
+  }
+  if (valid) rho_part[U.rho_off + (long long)grp * c.npts + p] = c.occ * rho;
+  // kinetic current: warp then block reduction in a fixed order
+  for (int off = 16; off > 0; off >>= 1) {
+    jx += __shfl_xor_sync(0xffffffffu, jx, off);
+    jy += __shfl_xor_sync(0xffffffffu, jy, off);
+    jz += __shfl_xor_sync(0xffffffffu, jz, off);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    red_j[0][warp] = jx;
+    red_j[1][warp] = jy;
+    red_j[2][warp] = jz;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double s = 0.0;
+    for (int w = 0; w < TSBZ_PT / 32; ++w) s += red_j[threadIdx.x][w];
+    jk_part[U.jk_off + ((long long)tile * c.n_bgroups + grp) * 3 + threadIdx.x] = s;
+  }
+  // band norms of this tile
+  for (int bl = warp; bl < b_end - b_begin; bl += TSBZ_PT / 32) {
+    double s = 0.0;
+    for (int i = lane; i < TSBZ_PT; i += 32) s += red_n[bl][i];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) nrm_part[U.nrm_off + (long long)tile * c.n_bands + b_begin + bl] = s;
+  }
+}
+
+// ----------------------------------------------------------------------------
+// finalize: one CTA per sub-simulation.  rho (Eq. 3), norms, and the current
+// J = -(1/(Omega N_k)) sum_k sum_b occ [ dV Re<u|-i grad u> + q |u|^2
+//                                        + 2 sum_j E_j Im(conj(c_j) a_j) ]   (Eqs. 5-6)
+// summed in a fixed order (warp w takes units w, w+8, ...).
+// ----------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_finalize(const SubDev* subs, const UnitDev* units, const CellDev* cells,
+                                                  const double* q_obs, const typename Cplx<T>::type* Pa,
+                                                  const double* rho_part, const double* jk_part,
+                                                  const double* nrm_part, const int* mask, int mode) {
+  using V = typename Cplx<T>::type;
+  __shared__ double red[8][3];
+  const int s = blockIdx.x;
+  const SubDev S = subs[s];
+  const CellDev c = cells[S.cell];
+  const int step = *S.step;
+  const bool write_j = (mode == TSBZ_FIN_STEP) || (mask != nullptr && mask[s] != 0 &&
+                                                   (mode == TSBZ_FIN_J0MINUS || step == 0));
+  // density
+  const double inv_nk = 1.0 / S.n_k;
+  for (int r = threadIdx.x; r < c.npts; r += blockDim.x) {
+    double acc = 0.0;
+    for (int kl = 0; kl < S.n_k; ++kl) {
+      const UnitDev U = units[S.unit0 + kl];
+      for (int g = 0; g < c.n_bgroups; ++g) acc += rho_part[U.rho_off + (long long)g * c.npts + r];
+    }
+    S.rho[r] = acc * inv_nk;
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double jw[3] = {0.0, 0.0, 0.0};
+  for (int kl = warp; kl < S.n_k; kl += 8) {
+    const UnitDev U = units[S.unit0 + kl];
+    const int u = S.unit0 + kl;
+    double jk[3] = {0.0, 0.0, 0.0}, jn[3] = {0.0, 0.0, 0.0}, nsum = 0.0;
+    for (int i = lane; i < c.n_tiles * c.n_bgroups; i += 32)
+      for (int ax = 0; ax < 3; ++ax) jk[ax] += jk_part[U.jk_off + 3LL * i + ax];
+    for (int b = 0; b < c.n_bands; ++b) {
+      double nb = 0.0;
+      for (int t = lane; t < c.n_tiles; t += 32) nb += nrm_part[U.nrm_off + (long long)t * c.n_bands + b];
+      for (int off = 16; off > 0; off >>= 1) nb += __shfl_xor_sync(0xffffffffu, nb, off);
+      nb *= c.dv;
+      if (lane == 0) S.norms[kl * c.n_bands + b] = nb;
+      nsum += nb;  // identical in every lane
+    }
+    if (c.use_proj) {
+      const int np = c.n_proj;
+      for (int i = lane; i < c.n_bands * np; i += 32) {
+        const int j = i % np;
+        const V* pr = Pa + U.pa_off + 4LL * i;
+        const double ar = pr[0].x, ai = pr[0].y;
+        const double e2 = 2.0 * c.ekb[j];
+        for (int ax = 0; ax < 3; ++ax) {
+          // Im(conj(c) a) = c_r a_i - c_i a_r
+          const double cr = pr[1 + ax].x, ci = pr[1 + ax].y;
+          jn[ax] += e2 * (cr * ai - ci * ar);
+        }
+      }
+    }
+    for (int ax = 0; ax < 3; ++ax) {
+      double v = c.dv * jk[ax] + jn[ax];
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      jw[ax] += c.occ * (v + q_obs[3 * u + ax] * nsum);
+    }
+  }
+  if (lane == 0)
+    for (int ax = 0; ax < 3; ++ax) red[warp][ax] = jw[ax];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double J[3];
+    bool finite = true;
+    for (int ax = 0; ax < 3; ++ax) {
+      double t = 0.0;
+      for (int w = 0; w < 8; ++w) t += red[w][ax];
+      J[ax] = -t / (c.omega * S.n_k);
+      finite = finite && isfinite(J[ax]);
+    }
+    if (!finite) *S.status = 1;
+    if (write_j) {
+      double* dst = (mode == TSBZ_FIN_J0MINUS) ? S.J0m : (mode == TSBZ_FIN_J0PLUS ? S.J : S.J + 3LL * (step + 1));
+      for (int ax = 0; ax < 3; ++ax) dst[ax] = J[ax];
+    }
+    if (mode == TSBZ_FIN_STEP) *S.step = step + 1;
+  }
+}
+
+// ----------------------------------------------------------------------------
+// v_Hxc: rho -> complex work, 1-D DFT passes, Poisson scaling, PZ81, v_eff
+// All sub-simulations in the list share one cell (same grid).
+// ----------------------------------------------------------------------------
+static __global__ void k_hxc_load(const SubDev* subs, const int* sub_ids, int n_subs, int npts, double2* work) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)n_subs * npts) return;
+  const int sl = (int)(e / npts), r = (int)(e % npts);
+  work[e] = make_double2(subs[sub_ids[sl]].rho[r], 0.0);
+}
+
+// out = sum_n in[.. n ..] exp(sign * 2 pi i n k / N) along one axis.
+static __global__ void k_dft_axis(const double2* __restrict__ in, double2* __restrict__ out, long long total, int npts,
+                           int stride, int N, const double2* __restrict__ tw, int sign) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  const long long sbase = (e / npts) * npts;
+  const int r = (int)(e % npts);
+  const int k = (r / stride) % N;
+  const int base = r - k * stride;
+  double sr = 0.0, si = 0.0;
+  int idx = 0;
+  for (int n = 0; n < N; ++n) {
+    const double2 x = in[sbase + base + n * stride];
+    const double2 w = tw[idx];
+    const double wi = sign * w.y;
+    sr += x.x * w.x - x.y * wi;
+    si += x.x * wi + x.y * w.x;
+    idx += k;
+    if (idx >= N) idx -= N;
+  }
+  out[e] = make_double2(sr, si);
+}
+
+static __global__ void k_poisson(double2* work, long long total, CellDev c) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  const int r = (int)(e % c.npts);
+  const int i1 = r % c.n1, i2 = (r / c.n1) % c.n2, i3 = r / (c.n1 * c.n2);
+  const int m1 = i1 < (c.n1 + 1) / 2 ? i1 : i1 - c.n1;
+  const int m2 = i2 < (c.n2 + 1) / 2 ? i2 : i2 - c.n2;
+  const int m3 = i3 < (c.n3 + 1) / 2 ? i3 : i3 - c.n3;
+  const double g1 = m1 * c.gsq_scale[0], g2 = m2 * c.gsq_scale[1], g3 = m3 * c.gsq_scale[2];
+  const double gg = g1 * g1 + g2 * g2 + g3 * g3;
+  const double f = gg > 0.0 ? 4.0 * M_PI / (gg * c.npts) : 0.0;
+  const double2 x = work[e];
+  work[e] = make_double2(x.x * f, x.y * f);
+}
+
+__device__ __forceinline__ double pz81_potential(double rho) {
+  // Perdew-Zunger 1981, unpolarised: v_xc = d(rho e_xc)/d rho.
+  const double r = fmax(rho, 1e-30);
+  const double rs = cbrt(3.0 / (4.0 * M_PI * r));
+  const double ex = -0.75 * cbrt(3.0 / M_PI) * cbrt(r);
+  const double vx = 4.0 / 3.0 * ex;
+  double vc;
+  if (rs >= 1.0) {
+    const double sq = sqrt(rs);
+    const double den = 1.0 + 1.0529 * sq + 0.3334 * rs;
+    const double ec = -0.1423 / den;
+    vc = ec * (1.0 + 7.0 / 6.0 * 1.0529 * sq + 4.0 / 3.0 * 0.3334 * rs) / den;
+  } else {
+    const double lr = log(rs);
+    vc = 0.0311 * lr + (-0.048 - 0.0311 / 3.0) + 2.0 / 3.0 * 0.0020 * rs * lr + (2.0 * -0.0116 - 0.0020) / 3.0 * rs;
+  }
+  return vx + vc;
+}
+
+template <typename T>
+__global__ void k_hxc_final(const SubDev* subs, const int* sub_ids, int n_subs, CellDev c, const double2* work) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)n_subs * c.npts) return;
+  const int sl = (int)(e / c.npts), r = (int)(e % c.npts);
+  const SubDev S = subs[sub_ids[sl]];
+  double v = 0.0;
+  if (S.hartree) v += work[e].x;
+  if (S.xc) v += pz81_potential(S.rho[r]);
+  S.vhxc[r] = v;
+  reinterpret_cast<T*>(S.veff)[r] = (T)(c.vloc[r] + v);
+}
+
+template <typename T>
+__global__ void k_veff_frozen(const SubDev* subs, int s, CellDev c) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= c.npts) return;
+  const SubDev S = subs[s];
+  reinterpret_cast<T*>(S.veff)[r] = (T)(c.vloc[r] + S.vhxc[r]);
+}
+
+template <typename T>
+__global__ void k_convert_in(const double2* __restrict__ src, typename Cplx<T>::type* __restrict__ dst, long long n) {
+  using V = typename Cplx<T>::type;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = cmk<V>((T)src[i].x, (T)src[i].y);
+}
+
+template <typename T>
+__global__ void k_convert_out(const typename Cplx<T>::type* __restrict__ src, double2* __restrict__ dst, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = make_double2((double)src[i].x, (double)src[i].y);
+}
+
+// ----------------------------------------------------------------------------
+// launchers
+// ----------------------------------------------------------------------------
+template <typename T> void launch_field(const LaunchSet& L, int mode, void* stream) {
+  if (L.n_units == 0) return;
+  k_field<T><<<L.n_units, 128, 0, (cudaStream_t)stream>>>(L, mode);
+}
+
+template <typename T>
+void launch_bra(const LaunchSet& L, const void* src, void* P, int with_d, int use_obs, void* stream) {
+  using V = typename Cplx<T>::type;
+  if (L.n_units == 0 || !L.cell.use_proj) return;
+  const int rows = L.cell.n_proj * (with_d ? 4 : 1);
+  dim3 grid((rows + 31) / 32, (L.cell.n_bands + 15) / 16, L.n_units);
+  if (with_d)
+    k_bra<T, 4><<<grid, 256, 0, (cudaStream_t)stream>>>(L, (const V*)src, (V*)P, use_obs);
+  else
+    k_bra<T, 1><<<grid, 256, 0, (cudaStream_t)stream>>>(L, (const V*)src, (V*)P, use_obs);
+}
+
+template <typename T>
+void launch_stage(const LaunchSet& L, const void* tin, void* tout, void* psi, const void* P, int m, void* stream) {
+  using V = typename Cplx<T>::type;
+  if (L.n_units == 0) return;
+  constexpr int BC = 8;
+  dim3 grid(L.cell.n_tiles, L.n_units);
+  const size_t sm = (size_t)BC * (L.cell.n_proj > 0 ? L.cell.n_proj : 1) * sizeof(V);
+  k_stage<T, BC><<<grid, TSBZ_PT, sm, (cudaStream_t)stream>>>(L, (const V*)tin, (V*)tout, (V*)psi, (const V*)P, m);
+}
+
+template <typename T>
+void launch_observe(const LaunchSet& L, const void* psi, double* rho_part, double* jk_part, double* nrm_part,
+                    void* stream) {
+  using V = typename Cplx<T>::type;
+  if (L.n_units == 0) return;
+  dim3 grid(L.cell.n_tiles, L.n_units, L.cell.n_bgroups);
+  k_observe<T><<<grid, TSBZ_PT, 0, (cudaStream_t)stream>>>(L, (const V*)psi, rho_part, jk_part, nrm_part);
+}
+
+template <typename T>
+void launch_finalize_t(const SubDev* subs, int n_subs, const UnitDev* units, const CellDev* cells_dev,
+                       const double* q_obs, const void* Pa, const double* rho_part, const double* jk_part,
+                       const double* nrm_part, const int* mask, int mode, void* stream) {
+  using V = typename Cplx<T>::type;
+  if (n_subs == 0) return;
+  k_finalize<T><<<n_subs, 256, 0, (cudaStream_t)stream>>>(subs, units, cells_dev, q_obs, (const V*)Pa, rho_part,
+                                                          jk_part, nrm_part, mask, mode);
+}
+
+template <typename T>
+int launch_hxc_t(const SubDev* subs_dev, const int* sub_ids_dev, int n_subs, const CellDev& c, double2* wa,
+                 double2* wb, double2* const tw[3], void* stream) {
+  if (n_subs == 0) return 0;
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long total = (long long)n_subs * c.npts;
+  const int thr = 256;
+  const unsigned blocks = (unsigned)((total + thr - 1) / thr);
+  int launches = 0;
+  k_hxc_load<<<blocks, thr, 0, st>>>(subs_dev, sub_ids_dev, n_subs, c.npts, wa);
+  ++launches;
+  const int nn[3] = {c.n1, c.n2, c.n3};
+  const int strides[3] = {1, c.n1, c.n1 * c.n2};
+  double2* a = wa;
+  double2* b = wb;
+  for (int ax = 0; ax < 3; ++ax) {
+    k_dft_axis<<<blocks, thr, 0, st>>>(a, b, total, c.npts, strides[ax], nn[ax], tw[ax], -1);
+    double2* t = a; a = b; b = t;
+    ++launches;
+  }
+  k_poisson<<<blocks, thr, 0, st>>>(a, total, c);
+  ++launches;
+  for (int ax = 0; ax < 3; ++ax) {
+    k_dft_axis<<<blocks, thr, 0, st>>>(a, b, total, c.npts, strides[ax], nn[ax], tw[ax], +1);
+    double2* t = a; a = b; b = t;
+    ++launches;
+  }
+  k_hxc_final<T><<<blocks, thr, 0, st>>>(subs_dev, sub_ids_dev, n_subs, c, a);
+  ++launches;
+  return launches;
+}
+
+template <typename T> void launch_convert_in_t(const double2* src, void* dst, long long n, void* stream) {
+  using V = typename Cplx<T>::type;
+  if (n == 0) return;
+  k_convert_in<T><<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(src, (V*)dst, n);
+}
+
+template <typename T> void launch_convert_out_t(const void* src, double2* dst, long long n, void* stream) {
+  using V = typename Cplx<T>::type;
+  if (n == 0) return;
+  k_convert_out<T><<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>((const V*)src, dst, n);
+}
+
+template <typename T> void launch_veff_frozen_t(const SubDev* subs_dev, int s, const CellDev& c, void* stream) {
+  k_veff_frozen<T><<<(c.npts + 255) / 256, 256, 0, (cudaStream_t)stream>>>(subs_dev, s, c);
+}

@@ -1,0 +1,217 @@
+"""GPU parity: the library (C ABI) against the oracle on the same seeded inputs.
+
+FP64 bars: err_J <= 1e-10 and err_rho, err_norm <= 1e-12 (element by element
+over every time step / grid point / orbital).  FP32 is compared with bars
+derived from float rounding (see the FP32 test).  Cases span several point
+tiles (128 points) and band groups, a ragged grid (10 x 12 x 14, non-grid
+atoms), a pulse and a kick, self-consistent and frozen v_Hxc, the two-step
+average, checkpoint/restart, the free-electron closed form and the full
+two-step workload of 64 shifted 4^3 subgrids (sampled).
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import analysis, dynamics, kpoints, scf
+from oracle.cell import Grid, local_potential
+
+from gpu_common import FP64_J_TOL, FP64_RHO_TOL, compare, gpu_run, oracle_run, random_subsim
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built_library():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2112_00920_gb300 import build_library
+    build_library()
+
+
+def _tiny_pair():
+    return W.cell_tiny(atoms="pair", n=(8, 8, 8), a=(6.0, 6.0, 6.0), n_bands=4)
+
+
+def test_cell_tables_match_oracle():
+    from paper_2112_00920_gb300 import Propagator
+    for cell in (W.cell_a(), W.cell_tiny(atoms="offgrid", n=(10, 12, 14), a=(7.0, 8.0, 9.0))):
+        P = Propagator("fp64")
+        cid = P.add_cell_spec(cell)
+        v, _ = P.cell_tables(cid)
+        ref = local_potential(cell)
+        assert np.max(np.abs(v - ref)) <= 1e-12 * np.max(np.abs(ref))
+        P.close()
+
+
+def test_parity_tiny_fp64_kick():
+    cell = _tiny_pair()
+    subs = [random_subsim(cell, (2, 2, 1), (0.25, 0.5, 0.0), 0.08, 10, W.Kick(k0=0.01), seed=1)]
+    _, g = gpu_run(cell, subs)
+    o = oracle_run(cell, subs[0])
+    compare(g[0], o, FP64_J_TOL, FP64_RHO_TOL)
+
+
+def test_parity_ragged_fp64_pulse():
+    cell = W.cell_tiny(atoms="offgrid", n=(10, 12, 14), a=(7.0, 8.0, 9.0), n_bands=3)
+    pulse = W.Pulse(e0=0.05, omega0=0.3, t_pulse=0.8, direction=(0.3, 0.4, 0.866))
+    subs = [random_subsim(cell, (5, 1, 1), (0.1, 0.2, 0.3), 0.05, 8, pulse, seed=2)]
+    _, g = gpu_run(cell, subs)
+    o = oracle_run(cell, subs[0])
+    compare(g[0], o, FP64_J_TOL, FP64_RHO_TOL)
+
+
+def test_parity_many_bands_fp64():
+    """40 bands: two band groups of the point kernels and three band blocks of the bra."""
+    cell = W.cell_tiny(atoms="one", n=(9, 9, 9), a=(6.0, 6.0, 6.0), n_bands=40, proj_half=4.5)
+    subs = [random_subsim(cell, (1, 1, 2), (0.3, 0.3, 0.3), 0.05, 4, W.Kick(k0=0.02, direction=(0, 1, 0)), seed=3)]
+    _, g = gpu_run(cell, subs)
+    o = oracle_run(cell, subs[0])
+    compare(g[0], o, FP64_J_TOL, FP64_RHO_TOL)
+
+
+def test_parity_frozen_fp64():
+    cell = _tiny_pair()
+    vf = 0.03 * np.sin(2 * np.pi * np.arange(512).reshape(8, 8, 8) / 37.0)
+    subs = [random_subsim(cell, (1, 2, 2), (0.5, 0.25, 0.75), 0.08, 6, W.Kick(k0=0.01), seed=4)]
+    _, g = gpu_run(cell, subs, hxc="frozen", v_frozen=vf)
+    o = oracle_run(cell, subs[0], hxc="frozen", v_frozen=vf)
+    compare(g[0], o, FP64_J_TOL, FP64_RHO_TOL)
+
+
+@pytest.fixture(scope="module")
+def config1_ground_state():
+    run = W.config1()
+    sub = run.subsims[0]
+    k = kpoints.kpoints_cartesian(sub.cell.a, sub.mp, sub.shift)
+    gs = scf.ground_state(sub.cell, k, seed=W.MASTER_SEED, tol=1e-8, eig_tol=1e-8)
+    return sub, gs
+
+
+def test_parity_config1_fp64(config1_ground_state):
+    """Cell A, MP 2^3, SCF ground state, kick 0.005 x, dt 0.08 (20 of the 100 steps)."""
+    sub, gs = config1_ground_state
+    s = dict(mp=sub.mp, shift=sub.shift, psi=gs["u"], dt=sub.dt, n_steps=20, field=sub.field)
+    _, g = gpu_run(sub.cell, [s])
+    o = oracle_run(sub.cell, s)
+    compare(g[0], o, FP64_J_TOL, FP64_RHO_TOL)
+    # transverse current vanishes by symmetry on the GPU as well
+    dj = g[0]["J"] - g[0]["J0m"]
+    assert np.max(np.abs(dj[:, 1:])) < 1e-6 * np.max(np.abs(dj[:, 0]))
+
+
+def test_parity_config1_fp32(config1_ground_state):
+    """FP32 stencil/Taylor/projectors with FP64 rho/J: errors stay at float
+    rounding (~1e-7 per step on each orbital, accumulated over 20 steps)."""
+    sub, gs = config1_ground_state
+    s = dict(mp=sub.mp, shift=sub.shift, psi=gs["u"], dt=sub.dt, n_steps=20, field=sub.field)
+    _, g = gpu_run(sub.cell, [s], precision="fp32")
+    o = oracle_run(sub.cell, s)
+    dj_g = g[0]["J"] - g[0]["J0m"]
+    dj_o = o["J"] - o["J0_minus"]
+    e_dj = float(np.max(np.abs(dj_g - dj_o)) / np.max(np.abs(dj_o)))
+    errs = compare(g[0], o, 1e-4, 1e-5, 1e-5)
+    assert e_dj < 1e-3, e_dj
+    print("fp32 config1:", errs, "err_dJ", e_dj)
+
+
+def test_free_electron_closed_form_gpu():
+    """Plane waves in an empty 16^3 cell: J(t) follows the closed form."""
+    cell = W.free_electron(W.cell_a(n_bands=16))
+    g = Grid(cell)
+    k = kpoints.kpoints_cartesian(cell.a, (2, 2, 2), (0.0, 0.0, 0.0))
+    gints = analysis.lowest_plane_waves(g, k, 16)
+    psi = analysis.plane_wave_orbitals(g, gints)
+    n = 15
+    kick = W.Kick(k0=0.005)
+    a = dynamics.field_samples(kick, 0.08, n)
+    jc, j0, w = analysis.free_electron_current(g, cell.occ, k, gints, 0.08, n, a)
+    s = dict(mp=(2, 2, 2), shift=(0, 0, 0), psi=psi, dt=0.08, n_steps=n, field=kick)
+    _, out = gpu_run(cell, [s])
+    assert np.max(np.abs(out[0]["J"] - jc)) <= 1e-10 * np.max(np.abs(jc))
+    np.testing.assert_allclose(out[0]["J0m"], j0, atol=1e-13 * np.max(np.abs(jc)))
+    np.testing.assert_allclose(out[0]["norms"], w, rtol=1e-12)
+
+
+def test_two_step_average_gpu():
+    """Sub-simulation id -1 returns (1/N_H) sum_m (J_m - J_m(0-)) (Eq. 9)."""
+    cell = _tiny_pair()
+    subs = [random_subsim(cell, (1, 1, 2), s, 0.08, 5, W.Kick(k0=0.01), seed=5, tag=i)
+            for i, s in enumerate(W.lattice_shifts(2))]
+    P, g = gpu_run(cell, subs)
+    avg, _ = P.current(-1)
+    orcs = [oracle_run(cell, s) for s in subs]
+    ref = dynamics.two_step_average(orcs)
+    assert np.max(np.abs(avg - ref)) <= FP64_J_TOL * np.max(np.abs(ref))
+    for gi, oi in zip(g, orcs):
+        compare(gi, oi, FP64_J_TOL, FP64_RHO_TOL)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_checkpoint_restart_bitwise(precision):
+    """propagate(6) == propagate(3) + get_state/load_state + propagate(3), bit for bit."""
+    cell = _tiny_pair()
+    subs = [random_subsim(cell, (2, 1, 1), (0.5, 0.5, 0.5), 0.08, 6, W.Kick(k0=0.01), seed=6, tag=i) for i in range(2)]
+    P1, g1 = gpu_run(cell, subs, precision=precision)
+    P2, _ = gpu_run(cell, subs, precision=precision, steps=3)
+    states = [P2.get_state(i) for i in range(2)]
+    for i, (st, step) in enumerate(states):
+        assert step == 3
+        P2.load_state(i, st, step)
+    P2.propagate(3)
+    for i in range(2):
+        J2, _ = P2.current(i)
+        np.testing.assert_array_equal(J2, g1[i]["J"])
+        np.testing.assert_array_equal(P2.density(i), g1[i]["rho"])
+        np.testing.assert_array_equal(P2.get_state(i)[0], P1.get_state(i)[0])
+
+
+def test_error_paths():
+    from paper_2112_00920_gb300 import Propagator, TsbzError
+    cell = _tiny_pair()
+    P = Propagator("fp64")
+    cid = P.add_cell_spec(cell)
+    sid = P.add_subsim(cid, np.zeros((2, 3)), 0.08, 3)
+    with pytest.raises(TsbzError) as e:
+        P.propagate(1)
+    assert e.value.code == -6
+    with pytest.raises(TsbzError) as e:
+        P.load_ground_state(sid, np.zeros((2, 4, 8, 8, 7), dtype=np.complex128))
+    assert e.value.code == -1
+    bad = np.full((2, 4, 8, 8, 8), np.nan, dtype=np.complex128)
+    P.load_ground_state(sid, bad)
+    with pytest.raises(TsbzError) as e:
+        P.propagate(1)
+    assert e.value.code == -5
+    with pytest.raises(TsbzError) as e:
+        P.propagate(5)
+    assert e.value.code == -1
+    P.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_full_two_step_workload_sampled(precision):
+    """The benchmark's launch configuration: 64 shifted 4^3 subgrids of cell A
+    (4096 k, 65 536 orbitals), plane-wave start, kick; two steps.  Sub-simulations
+    are independent, so sampled ones are checked against the oracle run alone."""
+    from paper_2112_00920_gb300 import Propagator, shifted_kpoints
+    run = W.config2(n_steps=2)
+    cell = run.subsims[0].cell
+    gints = W.plane_wave_set(cell.n_bands)
+    psi = W.plane_wave_orbitals(cell.a, cell.n, gints, 64)
+    P = Propagator(precision)
+    cid = P.add_cell_spec(cell)
+    sids = [P.add_subsim(cid, shifted_kpoints(cell.a, s.mp, s.shift), s.dt, 2) for s in run.subsims]
+    for sid in sids:
+        P.load_ground_state(sid, psi)
+    P.set_kick(-1, 0.005, (1.0, 0.0, 0.0))
+    P.propagate(2)
+    for m in (0, 37, 63):
+        sub = run.subsims[m]
+        s = dict(mp=sub.mp, shift=sub.shift, psi=psi, dt=sub.dt, n_steps=2, field=sub.field)
+        o = oracle_run(cell, s)
+        J, j0 = P.current(sids[m])
+        g = dict(J=J, J0m=j0, rho=P.density(sids[m]), norms=P.norms(sids[m]))
+        if precision == "fp64":
+            compare(g, o, FP64_J_TOL, FP64_RHO_TOL)
+        else:
+            compare(g, o, 1e-4, 1e-5, 1e-5)

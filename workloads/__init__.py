@@ -281,3 +281,37 @@ def scf_start_vectors(n_k: int, n_vec: int, n_pts: int, seed: int, tag: int = 0)
 def random_complex(shape, seed: int, tag: int = 0) -> np.ndarray:
     rng = np.random.default_rng([seed, 13, tag])
     return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+# ----------------------------------------------------------------------------
+# Initial orbitals (inputs of a propagation; no method arithmetic)
+# ----------------------------------------------------------------------------
+def random_orbitals(n_k: int, n_b: int, n: tuple, dv: float, seed: int, tag: int = 0) -> np.ndarray:
+    """Seeded random orbitals, orthonormal per k in the metric dV sum conj(u) v,
+    shape (n_k, n_b, n3, n2, n1) complex128."""
+    npts = int(n[0] * n[1] * n[2])
+    x = random_complex((n_k, npts, n_b), seed, tag)
+    out = np.empty((n_k, n_b, npts), dtype=np.complex128)
+    for k in range(n_k):
+        q, _ = np.linalg.qr(x[k])
+        out[k] = q.T / np.sqrt(dv)
+    return out.reshape((n_k, n_b, n[2], n[1], n[0]))
+
+
+def plane_wave_set(n_b: int) -> np.ndarray:
+    """The n_b integer triples with the smallest |n|^2 (ties lexicographic)."""
+    rng = range(-4, 5)
+    cands = sorted(((i * i + j * j + l * l, (i, j, l)) for i in rng for j in rng for l in rng))
+    return np.array([c[1] for c in cands[:n_b]], dtype=np.int64)
+
+
+def plane_wave_orbitals(a: tuple, n: tuple, gints: np.ndarray, n_k: int) -> np.ndarray:
+    """u_b(r) = exp(2 pi i g_b . (i/N)) / sqrt(Omega) on the grid, the same for
+    every k: shape (n_k, n_b, n3, n2, n1) complex128."""
+    i1 = np.arange(n[0]) / n[0]
+    i2 = np.arange(n[1]) / n[1]
+    i3 = np.arange(n[2]) / n[2]
+    z, y, x = np.meshgrid(i3, i2, i1, indexing="ij")
+    omega = float(a[0] * a[1] * a[2])
+    one = np.stack([np.exp(2j * np.pi * (g[0] * x + g[1] * y + g[2] * z)) for g in gints]) / np.sqrt(omega)
+    return np.broadcast_to(one, (n_k,) + one.shape).copy()
