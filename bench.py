@@ -146,10 +146,11 @@ class ClockSampler:
 # ----------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------
-def build_propagator(precision, n_steps_cap, psi_host=None, device=0):
+def build_propagator(precision, n_steps_cap, device=0, n_subsims=64):
     import workloads as W
     from paper_2112_00920_gb300 import Propagator, shifted_kpoints
     run = W.config2(n_steps=n_steps_cap)
+    run.subsims = run.subsims[:n_subsims]
     cell = run.subsims[0].cell
     P = Propagator(precision, device=device)
     cid = P.add_cell_spec(cell)
@@ -174,6 +175,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--subsims", type=int, default=64,
+                    help="number of the 64 shifted subgrids to run (profiling of a reduced case)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -206,7 +209,7 @@ def main():
     build_library()
 
     cap = args.warmup + args.steps
-    P, sids, run = build_propagator(args.precision, cap, device=local_rank)
+    P, sids, run = build_propagator(args.precision, cap, device=local_rank, n_subsims=args.subsims)
     cell = run.subsims[0].cell
     n_orb = run.n_orbitals
     gints = W.plane_wave_set(cell.n_bands)
@@ -263,7 +266,7 @@ def main():
     P.close()
     torch.cuda.synchronize()
     t_e2e = time.perf_counter()
-    P2, sids2, _ = build_propagator(args.precision, args.steps, device=local_rank)
+    P2, sids2, _ = build_propagator(args.precision, args.steps, device=local_rank, n_subsims=args.subsims)
     for sid in sids2:
         P2.load_ground_state(sid, psi_host)
     P2.set_kick(-1, 0.005, (1.0, 0.0, 0.0))
@@ -273,15 +276,15 @@ def main():
     e2e_s = time.perf_counter() - t_e2e
     P2.close()
     e2e = {"value": n_orb * args.steps * world / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": int(psi_host.nbytes * 64 / args.steps),
-           "d2h_bytes_per_step": int(J_e2e.nbytes * 64 / max(args.steps, 1)),
+           "h2d_bytes_per_step": int(psi_host.nbytes * len(sids2) / args.steps),
+           "d2h_bytes_per_step": int(J_e2e.nbytes / max(args.steps, 1)),
            "includes": "context set-up, 64 ground-state uploads (complex128 host), kick, propagation, "
                        "two-step current download"}
 
     # plain FP64 GPU path on the same workload (comparison)
     fp64 = None
     if args.precision == "fp32" and args.fp64_steps > 0:
-        P3, sids3, _ = build_propagator("fp64", args.fp64_steps + 1, device=local_rank)
+        P3, sids3, _ = build_propagator("fp64", args.fp64_steps + 1, device=local_rank, n_subsims=args.subsims)
         for sid in sids3:
             P3.load_ground_state(sid, psi_dev)
         P3.set_kick(-1, 0.005, (1.0, 0.0, 0.0))
@@ -302,7 +305,8 @@ def main():
                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
                "data": "synthetic (seeded Si-like model, plane-wave start orbitals)",
-               "config": {"workload": WORKLOAD, "n_subsims": len(run.subsims), "k_points": 4096,
+               "config": {"workload": WORKLOAD if args.subsims == 64 else f"reduced: {args.subsims} of " + WORKLOAD,
+                          "n_subsims": len(run.subsims), "k_points": 64 * len(run.subsims),
                           "orbitals_per_gpu": n_orb, "grid": "16^3", "bands": 16, "dt": 0.08,
                           "precision": args.precision, "l2": "inputs (psi 2 GiB fp32) larger than L2",
                           "parallelism": f"replica x{world} (independent shifts per GPU)"},

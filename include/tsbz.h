@@ -65,7 +65,7 @@ typedef struct {
 } tsbz_alloc;
 
 /* A cell and its synthetic norm-conserving pseudopotential (Eq. 2, Sec. III).
- *  - orthorhombic edges a[3] (bohr), grid n[3] (each 2*fd_nd+1 .. 1024);
+ *  - orthorhombic edges a[3] (bohr), grid n[3] (each fd_nd+1 .. 1024);
  *  - atoms at fractional positions atom_frac[3*n_atoms];
  *  - local part per atom: -z_ion erf(r/r_erf)/r + c_core exp(-r^2/(2 sigma_core^2)),
  *    defined through its Fourier series with the G = 0 Coulomb term removed;

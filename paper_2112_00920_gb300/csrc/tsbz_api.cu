@@ -85,6 +85,7 @@ struct tsbz_ctx {
   double* q_half = nullptr;
   double* q_obs = nullptr;
   double* kcart = nullptr;
+  void* qt_half = nullptr;
   UnitDev* d_units = nullptr;
   SubDev* d_subs = nullptr;
   CellDev* d_cells = nullptr;
@@ -177,6 +178,7 @@ LaunchSet make_set(tsbz_ctx* ctx, HostCell& hc) {
   L.ph_half = ctx->ph_half;
   L.ph_obs = ctx->ph_obs;
   L.ph_stride = ctx->ph_stride;
+  L.qt_half = ctx->qt_half;
   return L;
 }
 
@@ -239,6 +241,7 @@ int layout(tsbz_ctx* ctx) {
   if ((rc = dalloc_t(ctx, 3 * ctx->n_units, &ctx->q_half))) return rc;
   if ((rc = dalloc_t(ctx, 3 * ctx->n_units, &ctx->q_obs))) return rc;
   if ((rc = dalloc_t(ctx, 3 * ctx->n_units, &ctx->kcart))) return rc;
+  if ((rc = dalloc(ctx, 4 * ctx->n_units * (ctx->precision == TSBZ_FP64 ? 8 : 4), &ctx->qt_half))) return rc;
   if ((rc = dalloc_t(ctx, ctx->n_units, &ctx->d_units))) return rc;
   if ((rc = dalloc_t(ctx, ctx->subs.size(), &ctx->d_subs))) return rc;
   if ((rc = dalloc_t(ctx, ctx->cells.size(), &ctx->d_cells))) return rc;
@@ -506,8 +509,9 @@ int tsbz_init_cell(tsbz_ctx* ctx, const tsbz_cell_desc* d, int* cell_id) {
   if (ctx->laid_out) return set_err(ctx, TSBZ_ESTATE, "cells must be added before the first ground state");
   if (d->fd_nd < 1 || d->fd_nd > TSBZ_MAX_ND) return set_err(ctx, TSBZ_EINVAL, "fd_nd must be 1..6");
   for (int ax = 0; ax < 3; ++ax) {
-    if (d->n[ax] < 2 * d->fd_nd + 1 || d->n[ax] > 1024)
-      return set_err(ctx, TSBZ_EINVAL, "grid size must be in [2 fd_nd + 1, 1024]");
+    // the stencil wraps at most once: n > fd_nd
+    if (d->n[ax] < d->fd_nd + 1 || d->n[ax] > 1024)
+      return set_err(ctx, TSBZ_EINVAL, "grid size must be in [fd_nd + 1, 1024]");
     if (!(d->a[ax] > 0.0)) return set_err(ctx, TSBZ_EINVAL, "cell edges must be positive");
   }
   if (d->n_bands < 1 || d->n_atoms < 0 || (d->n_atoms > 0 && !d->atom_frac))
@@ -563,23 +567,45 @@ int tsbz_init_cell(tsbz_ctx* ctx, const tsbz_cell_desc* d, int* cell_id) {
     for (int t = 0; t < 3; ++t) ekb.push_back(d->e_kb_p);
   }
   if (ekb.empty()) ekb.push_back(0.0);
-  double *vl, *gg, *dd, *pn, *ek;
+  // pnorm_j * E_j per projector (the ket weight)
+  std::vector<double> wkb(ekb.size(), 0.0);
+  if (c.use_proj)
+    for (int j = 0; j < c.n_proj; ++j) wkb[j] = hc.pnorm[j] * ekb[j];
+  auto to_f = [](const std::vector<double>& v) { return std::vector<float>(v.begin(), v.end()); };
+  const std::vector<float> g1f = to_f(g1), d1f = to_f(d1), pnf = to_f(hc.pnorm), wkf = to_f(wkb);
+  double *vl, *gg, *dd, *pn, *ek, *wk;
+  float *ggf, *ddf, *pnff, *wkff;
   int rc;
   if ((rc = dalloc_t(ctx, hc.vloc.size(), &vl))) return rc;
   if ((rc = dalloc_t(ctx, g1.size(), &gg))) return rc;
   if ((rc = dalloc_t(ctx, d1.size(), &dd))) return rc;
   if ((rc = dalloc_t(ctx, hc.pnorm.size(), &pn))) return rc;
   if ((rc = dalloc_t(ctx, ekb.size(), &ek))) return rc;
+  if ((rc = dalloc_t(ctx, wkb.size(), &wk))) return rc;
+  if ((rc = dalloc_t(ctx, g1f.size(), &ggf))) return rc;
+  if ((rc = dalloc_t(ctx, d1f.size(), &ddf))) return rc;
+  if ((rc = dalloc_t(ctx, pnf.size(), &pnff))) return rc;
+  if ((rc = dalloc_t(ctx, wkf.size(), &wkff))) return rc;
   CK(cudaMemcpy(vl, hc.vloc.data(), sizeof(double) * hc.vloc.size(), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(gg, g1.data(), sizeof(double) * g1.size(), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(dd, d1.data(), sizeof(double) * d1.size(), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(pn, hc.pnorm.data(), sizeof(double) * hc.pnorm.size(), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ek, ekb.data(), sizeof(double) * ekb.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(wk, wkb.data(), sizeof(double) * wkb.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ggf, g1f.data(), sizeof(float) * g1f.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ddf, d1f.data(), sizeof(float) * d1f.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(pnff, pnf.data(), sizeof(float) * pnf.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(wkff, wkf.data(), sizeof(float) * wkf.size(), cudaMemcpyHostToDevice));
   c.vloc = vl;
   c.g1 = gg;
   c.d1 = dd;
   c.pnorm = pn;
   c.ekb = ek;
+  c.wkb = wk;
+  c.g1f = ggf;
+  c.d1f = ddf;
+  c.pnormf = pnff;
+  c.wkbf = wkff;
   const int nn[3] = {c.n1, c.n2, c.n3};
   for (int ax = 0; ax < 3; ++ax) {
     std::vector<double2> tw(nn[ax]);

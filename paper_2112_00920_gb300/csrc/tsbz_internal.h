@@ -33,7 +33,13 @@ struct CellDev {
   const double* d1;     // [n_atoms][3][nmax] minimum-image displacement, 0 outside the box
   const double* pnorm;  // [n_atoms][4]        N_s, N_px, N_py, N_pz
   const double* ekb;    // [n_proj]
+  const double* wkb;    // [n_proj]            pnorm_j * E_j
   const double* vloc;   // [npts]
+  // the same tables in float for the single-precision kernels
+  const float* g1f;
+  const float* d1f;
+  const float* pnormf;
+  const float* wkbf;
 };
 
 struct UnitDev {
@@ -89,6 +95,7 @@ struct LaunchSet {
   void* ph_half;          // [unit][n_atoms*3*nmax] complex T
   void* ph_obs;
   long long ph_stride;    // complex elements per unit
+  void* qt_half;          // [unit][4] in T: q_x, q_y, q_z, |q|^2 / 2 at t_n + dt/2
 };
 
 // Launchers (templated on the real type in tsbz_kernels.cuh, instantiated per precision).

@@ -51,6 +51,22 @@ template <typename V, typename R> __device__ __forceinline__ void rfma(V& acc, R
 
 __device__ __forceinline__ int wrap_idx(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
+// Cell tables in the arithmetic type of the kernel (float copies for the
+// single-precision path keep double operations out of its inner loops).
+template <typename T> struct Tab;
+template <> struct Tab<double> {
+  static __device__ __forceinline__ const double* g1(const CellDev& c) { return c.g1; }
+  static __device__ __forceinline__ const double* d1(const CellDev& c) { return c.d1; }
+  static __device__ __forceinline__ const double* pnorm(const CellDev& c) { return c.pnorm; }
+  static __device__ __forceinline__ const double* wkb(const CellDev& c) { return c.wkb; }
+};
+template <> struct Tab<float> {
+  static __device__ __forceinline__ const float* g1(const CellDev& c) { return c.g1f; }
+  static __device__ __forceinline__ const float* d1(const CellDev& c) { return c.d1f; }
+  static __device__ __forceinline__ const float* pnorm(const CellDev& c) { return c.pnormf; }
+  static __device__ __forceinline__ const float* wkb(const CellDev& c) { return c.wkbf; }
+};
+
 // ----------------------------------------------------------------------------
 // field: q vectors and phase tables of every unit (k-point) of one cell
 // ----------------------------------------------------------------------------
@@ -82,7 +98,10 @@ __global__ void k_field(LaunchSet L, int mode) {
   if (threadIdx.x < 3) {
     L.q_half[3 * u + threadIdx.x] = qh[threadIdx.x];
     L.q_obs[3 * u + threadIdx.x] = qo[threadIdx.x];
+    reinterpret_cast<T*>(L.qt_half)[4 * u + threadIdx.x] = (T)qh[threadIdx.x];
   }
+  if (threadIdx.x == 3)
+    reinterpret_cast<T*>(L.qt_half)[4 * u + 3] = (T)(0.5 * (qh[0] * qh[0] + qh[1] * qh[1] + qh[2] * qh[2]));
   V* phh = (V*)L.ph_half + (long long)u * L.ph_stride;
   V* pho = (V*)L.ph_obs + (long long)u * L.ph_stride;
   const int tab = c.n_atoms * 3 * c.nmax;
@@ -142,14 +161,14 @@ __global__ void __launch_bounds__(256) k_bra(LaunchSet L, const typename Cplx<T>
       for (int r = 0; r < 4 * NW; ++r) vals[r] = zero;
       if (p < c.npts && a < c.n_atoms) {
         const int ix = p % c.n1, iy = (p / c.n1) % c.n2, iz = p / (c.n1 * c.n2);
-        const double* ga = c.g1 + (long long)a * 3 * nm;
-        const double* da = c.d1 + (long long)a * 3 * nm;
-        const T g = (T)(ga[ix] * ga[nm + iy] * ga[2 * nm + iz]);
-        const T d[3] = {(T)da[ix], (T)da[nm + iy], (T)da[2 * nm + iz]};
+        const T* ga = Tab<T>::g1(c) + (long long)a * 3 * nm;
+        const T* da = Tab<T>::d1(c) + (long long)a * 3 * nm;
+        const T g = ga[ix] * ga[nm + iy] * ga[2 * nm + iz];
+        const T d[3] = {da[ix], da[nm + iy], da[2 * nm + iz]};
         const V* pa = ph + (long long)a * 3 * nm;
         const V f = cscale(cmul(cmul(pa[ix], pa[nm + iy]), pa[2 * nm + iz]), g);
-        const double* pn = c.pnorm + 4 * a;
-        const T w[4] = {(T)pn[0], (T)pn[1] * d[0], (T)pn[2] * d[1], (T)pn[3] * d[2]};
+        const T* pn = Tab<T>::pnorm(c) + 4 * a;
+        const T w[4] = {pn[0], pn[1] * d[0], pn[2] * d[1], pn[3] * d[2]};
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
           if (NW == 1) {
@@ -234,12 +253,12 @@ __global__ void __launch_bounds__(TSBZ_PT) k_stage(LaunchSet L, const typename C
   const int pp = valid ? p : 0;
   const int ix = pp % c.n1, iy = (pp / c.n1) % c.n2, iz = pp / (c.n1 * c.n2);
   const int n12 = c.n1 * c.n2;
-  const double* qd = L.q_half + 3 * u;
-  const T q[3] = {(T)qd[0], (T)qd[1], (T)qd[2]};
-  const T q2h = (T)(0.5 * (qd[0] * qd[0] + qd[1] * qd[1] + qd[2] * qd[2]));
+  const T* qt = reinterpret_cast<const T*>(L.qt_half) + 4 * u;
+  const T q[3] = {qt[0], qt[1], qt[2]};
+  const T q2h = qt[3];
   const T v = valid ? reinterpret_cast<const T*>(S.veff)[pp] : (T)0;
   const T diag = q2h + v;
-  const T hdt = (T)(S.dt / m);
+  const T hdt = (T)S.dt / (T)m;
   const V* ph = (const V*)L.ph_half + (long long)u * L.ph_stride;
   const int nm = c.nmax;
   const V zero = cmk<V>((T)0, (T)0);
@@ -255,7 +274,7 @@ __global__ void __launch_bounds__(TSBZ_PT) k_stage(LaunchSet L, const typename C
       for (int i = threadIdx.x; i < BC * c.n_proj; i += TSBZ_PT) {
         const int bl = i / c.n_proj, j = i % c.n_proj, b = b0 + bl;
         V w = zero;
-        if (b < c.n_bands) w = cscale(P[U.p_off + (long long)b * c.n_proj + j], (T)(c.pnorm[j] * c.ekb[j]));
+        if (b < c.n_bands) w = cscale(P[U.p_off + (long long)b * c.n_proj + j], Tab<T>::wkb(c)[j]);
         Ws[i] = w;
       }
     }
@@ -266,10 +285,10 @@ __global__ void __launch_bounds__(TSBZ_PT) k_stage(LaunchSet L, const typename C
     for (int bl = 0; bl < BC; ++bl) ket[bl] = zero;
     if (c.use_proj) {
       for (int a = 0; a < c.n_atoms; ++a) {
-        const double* ga = c.g1 + (long long)a * 3 * nm;
-        const double* da = c.d1 + (long long)a * 3 * nm;
-        const T g = (T)(ga[ix] * ga[nm + iy] * ga[2 * nm + iz]);
-        const T dx = (T)da[ix], dy = (T)da[nm + iy], dz = (T)da[2 * nm + iz];
+        const T* ga = Tab<T>::g1(c) + (long long)a * 3 * nm;
+        const T* da = Tab<T>::d1(c) + (long long)a * 3 * nm;
+        const T g = ga[ix] * ga[nm + iy] * ga[2 * nm + iz];
+        const T dx = da[ix], dy = da[nm + iy], dz = da[2 * nm + iz];
         const V* pa = ph + (long long)a * 3 * nm;
         const V fph = cmul(cmul(pa[ix], pa[nm + iy]), pa[2 * nm + iz]);
         const V f = cmk<V>(fph.x * g, -fph.y * g);   // g * exp(-i q.d)
@@ -337,15 +356,24 @@ __global__ void __launch_bounds__(TSBZ_PT) k_stage(LaunchSet L, const typename C
 // ----------------------------------------------------------------------------
 // observe: per (unit, point tile, band group) sums for rho, kinetic current
 // and band norms.  grid (point tiles, units, band groups), TSBZ_PT threads.
+// At one grid point the sums over the bands of the group are formed in T
+// (their terms are products of T orbitals); every sum over grid points,
+// k-points and sub-simulations is double.
 // ----------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(TSBZ_PT) k_observe(LaunchSet L, const typename Cplx<T>::type* __restrict__ psi,
                                                      double* __restrict__ rho_part, double* __restrict__ jk_part,
                                                      double* __restrict__ nrm_part) {
   using V = typename Cplx<T>::type;
-  __shared__ double red_n[TSBZ_BG][TSBZ_PT];
+  __shared__ T red_n[TSBZ_BG][TSBZ_PT];
   __shared__ double red_j[3][TSBZ_PT / 32];
+  __shared__ T gw[3][TSBZ_MAX_ND + 1];
   const CellDev& c = L.cell;
+  if (threadIdx.x < 3 * (TSBZ_MAX_ND + 1)) {
+    const int ax = threadIdx.x / (TSBZ_MAX_ND + 1), mm = threadIdx.x % (TSBZ_MAX_ND + 1);
+    gw[ax][mm] = (T)c.gradw[ax][mm];
+  }
+  __syncthreads();
   const int u = L.unit_ids[blockIdx.y];
   const UnitDev U = L.units[u];
   const int tile = blockIdx.x, grp = blockIdx.z;
@@ -356,57 +384,56 @@ __global__ void __launch_bounds__(TSBZ_PT) k_observe(LaunchSet L, const typename
   const int n12 = c.n1 * c.n2;
   const int b_begin = grp * TSBZ_BG;
   const int b_end = min(c.n_bands, b_begin + TSBZ_BG);
-  double rho = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
+  T rho = (T)0, jx = (T)0, jy = (T)0, jz = (T)0;
   for (int b = b_begin; b < b_end; ++b) {
-    double n2 = 0.0;
+    T n2 = (T)0;
     if (valid) {
       const V* tb = psi + U.psi_off + (long long)b * c.npts;
       const V ce = tb[pp];
-      n2 = (double)ce.x * ce.x + (double)ce.y * ce.y;
+      n2 = ce.x * ce.x + ce.y * ce.y;
       rho += n2;
       V g[3];
       for (int ax = 0; ax < 3; ++ax) g[ax] = cmk<V>((T)0, (T)0);
+      const int rowb = iz * n12 + iy * c.n1;
       for (int mm = 1; mm <= c.nd; ++mm) {
-        const T wx = (T)c.gradw[0][mm], wy = (T)c.gradw[1][mm], wz = (T)c.gradw[2][mm];
-        const int rowb = iz * n12 + iy * c.n1;
-        rfma(g[0], wx, csub(tb[rowb + wrap_idx(ix + mm, c.n1)], tb[rowb + wrap_idx(ix - mm, c.n1)]));
-        rfma(g[1], wy, csub(tb[iz * n12 + wrap_idx(iy + mm, c.n2) * c.n1 + ix],
-                            tb[iz * n12 + wrap_idx(iy - mm, c.n2) * c.n1 + ix]));
-        rfma(g[2], wz, csub(tb[wrap_idx(iz + mm, c.n3) * n12 + iy * c.n1 + ix],
-                            tb[wrap_idx(iz - mm, c.n3) * n12 + iy * c.n1 + ix]));
+        rfma(g[0], gw[0][mm], csub(tb[rowb + wrap_idx(ix + mm, c.n1)], tb[rowb + wrap_idx(ix - mm, c.n1)]));
+        rfma(g[1], gw[1][mm], csub(tb[iz * n12 + wrap_idx(iy + mm, c.n2) * c.n1 + ix],
+                                   tb[iz * n12 + wrap_idx(iy - mm, c.n2) * c.n1 + ix]));
+        rfma(g[2], gw[2][mm], csub(tb[wrap_idx(iz + mm, c.n3) * n12 + iy * c.n1 + ix],
+                                   tb[wrap_idx(iz - mm, c.n3) * n12 + iy * c.n1 + ix]));
       }
       // Re(conj(u) (-i g)) = u_r g_i - u_i g_r
-      jx += (double)ce.x * g[0].y - (double)ce.y * g[0].x;
-      jy += (double)ce.x * g[1].y - (double)ce.y * g[1].x;
-      jz += (double)ce.x * g[2].y - (double)ce.y * g[2].x;
+      jx += ce.x * g[0].y - ce.y * g[0].x;
+      jy += ce.x * g[1].y - ce.y * g[1].x;
+      jz += ce.x * g[2].y - ce.y * g[2].x;
     }
     red_n[b - b_begin][threadIdx.x] = n2;
   }
-  if (valid) rho_part[U.rho_off + (long long)grp * c.npts + p] = c.occ * rho;
-  // kinetic current: warp then block reduction in a fixed order
+  if (valid) rho_part[U.rho_off + (long long)grp * c.npts + p] = c.occ * (double)rho;
+  double djx = jx, djy = jy, djz = jz;
   for (int off = 16; off > 0; off >>= 1) {
-    jx += __shfl_xor_sync(0xffffffffu, jx, off);
-    jy += __shfl_xor_sync(0xffffffffu, jy, off);
-    jz += __shfl_xor_sync(0xffffffffu, jz, off);
+    djx += __shfl_xor_sync(0xffffffffu, djx, off);
+    djy += __shfl_xor_sync(0xffffffffu, djy, off);
+    djz += __shfl_xor_sync(0xffffffffu, djz, off);
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (lane == 0) {
-    red_j[0][warp] = jx;
-    red_j[1][warp] = jy;
-    red_j[2][warp] = jz;
+    red_j[0][warp] = djx;
+    red_j[1][warp] = djy;
+    red_j[2][warp] = djz;
   }
   __syncthreads();
   if (threadIdx.x < 3) {
-    double s = 0.0;
-    for (int w = 0; w < TSBZ_PT / 32; ++w) s += red_j[threadIdx.x][w];
-    jk_part[U.jk_off + ((long long)tile * c.n_bgroups + grp) * 3 + threadIdx.x] = s;
+    double sum = 0.0;
+    for (int w = 0; w < TSBZ_PT / 32; ++w) sum += red_j[threadIdx.x][w];
+    jk_part[U.jk_off + ((long long)tile * c.n_bgroups + grp) * 3 + threadIdx.x] = sum;
   }
   // band norms of this tile
   for (int bl = warp; bl < b_end - b_begin; bl += TSBZ_PT / 32) {
-    double s = 0.0;
-    for (int i = lane; i < TSBZ_PT; i += 32) s += red_n[bl][i];
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    if (lane == 0) nrm_part[U.nrm_off + (long long)tile * c.n_bands + b_begin + bl] = s;
+    T sum = (T)0;
+    for (int i = lane; i < TSBZ_PT; i += 32) sum += red_n[bl][i];
+    for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+    if (lane == 0) nrm_part[U.nrm_off + (long long)tile * c.n_bands + b_begin + bl] = (double)sum;
   }
 }
 
