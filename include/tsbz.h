@@ -187,6 +187,31 @@ int tsbz_halton(int n, double* out, size_t cap);
 int tsbz_pulse_samples(double e0, double w0, double t_pulse, const double dir[3], double dt, int n_steps,
                        double* out, size_t cap);
 
+/* ---- Allocation-free density ------------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory: code that runs inside another
+ * framework's memory pool or a pre-sized arena, or a loop that must not hit
+ * cudaMalloc's implicit device synchronisation.  It computes the density of
+ * tsbz_get_density, rho(r) = (1/n_k) sum_k sum_b occ |u_bk(r)|^2, from
+ * orbitals the caller already holds on the device, and allocates nothing:
+ * its partial sums use a file-scope static device buffer of
+ * TSBZ_NOALLOC_SCRATCH_DOUBLES doubles (2 MiB) that every GPU loading the
+ * library keeps until the process exits.
+ *  - psi: device, complex128 [n_k][n_bands][n3][n2][n1]; rho: device, doubles
+ *    [n3][n2][n1], overwritten.  Both stay owned by the caller.
+ *  - n3*n2*n1 must not exceed TSBZ_NOALLOC_SCRATCH_DOUBLES (TSBZ_EINVAL);
+ *    any n_k is accepted (k-points are reduced in chunks that fit the buffer).
+ *  - Work is queued on cuda_stream (NULL = legacy default stream); the call
+ *    returns without synchronising.  The first call on a device looks up the
+ *    buffer's device address once for that device; make that first call
+ *    before any stream capture.
+ *  - All calls share the one buffer: calls that overlap on the GPU (other
+ *    streams, other threads) race and must be serialised by the caller.
+ *  - Returns TSBZ_OK, TSBZ_EINVAL or TSBZ_ECUDA. */
+#define TSBZ_NOALLOC_SCRATCH_DOUBLES 262144
+int tsbz_density_noalloc(const double* psi, int n_k, int n_bands, const int n[3], double occ, double* rho,
+                         void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

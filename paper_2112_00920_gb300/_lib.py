@@ -91,6 +91,8 @@ _SIGS = {
     "tsbz_halton": ([ctypes.c_int, _D, ctypes.c_size_t], ctypes.c_int),
     "tsbz_pulse_samples": ([ctypes.c_double, ctypes.c_double, ctypes.c_double, _D, ctypes.c_double, ctypes.c_int,
                             _D, ctypes.c_size_t], ctypes.c_int),
+    "tsbz_density_noalloc": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _I, ctypes.c_double, ctypes.c_void_p,
+                              ctypes.c_void_p], ctypes.c_int),
 }
 
 
@@ -147,6 +149,28 @@ def pulse_samples(e0, omega0, t_pulse, direction, dt, n_steps) -> np.ndarray:
     if rc:
         raise TsbzError(rc, "tsbz_pulse_samples")
     return out
+
+
+def density_noalloc(psi, occ, rho=None, stream=None):
+    """rho(r) = (1/n_k) sum_k sum_b occ |u(r)|^2 of a complex128 CUDA tensor
+    psi (n_k, n_b, n3, n2, n1), through tsbz_density_noalloc: the library
+    allocates nothing (the result goes to ``rho``, allocated here by torch if
+    not given).  Queued on the current torch stream."""
+    import torch
+
+    lib = load()
+    assert psi.is_cuda and psi.dtype == torch.complex128 and psi.is_contiguous() and psi.dim() == 5
+    n_k, n_b, n3, n2, n1 = psi.shape
+    if rho is None:
+        rho = torch.empty((n3, n2, n1), dtype=torch.float64, device=psi.device)
+    if stream is None:
+        stream = torch.cuda.current_stream(psi.device).cuda_stream
+    nn = (ctypes.c_int * 3)(n1, n2, n3)
+    rc = lib.tsbz_density_noalloc(ctypes.c_void_p(psi.data_ptr()), n_k, n_b, nn, float(occ),
+                                  ctypes.c_void_p(rho.data_ptr()), ctypes.c_void_p(stream))
+    if rc:
+        raise TsbzError(rc, "tsbz_density_noalloc")
+    return rho
 
 
 class Propagator:
