@@ -172,7 +172,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32_tc", choices=["fp32_tc", "fp32", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--subsims", type=int, default=64,
@@ -252,12 +252,14 @@ def main():
     except OSError:
         pass
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    elem = 8 if args.precision == "fp32" else 16
+    elem = 16 if args.precision == "fp64" else 8
     n_stage = 4 * args.steps
     stage_ms = fam["stage"] / n_stage
     bytes_launch = stage_bytes_per_launch(elem, n_orb, cell.n_pts)
     achieved = bytes_launch / (stage_ms / 1e3) / 1e9
-    roof = {"kernel": "k_stage (stencil + ket + Taylor accumulate)", "bound": "hbm", "achieved": achieved,
+    kname = ("k_stage_tc (stencil + tensor-core ket + Taylor accumulate + tensor-core bra of t_m)"
+             if args.precision == "fp32_tc" else "k_stage (stencil + ket + Taylor accumulate)")
+    roof = {"kernel": kname, "bound": "hbm", "achieved": achieved,
             "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)" if peaks else "fallback 6.8 TB/s",
             "family_ms_per_step": {k: v / args.steps for k, v in fam.items()}}
@@ -283,7 +285,7 @@ def main():
 
     # plain FP64 GPU path on the same workload (comparison)
     fp64 = None
-    if args.precision == "fp32" and args.fp64_steps > 0:
+    if args.precision != "fp64" and args.fp64_steps > 0:
         P3, sids3, _ = build_propagator("fp64", args.fp64_steps + 1, device=local_rank, n_subsims=args.subsims)
         for sid in sids3:
             P3.load_ground_state(sid, psi_dev)
@@ -303,12 +305,16 @@ def main():
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-               "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+               "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
                "data": "synthetic (seeded Si-like model, plane-wave start orbitals)",
                "config": {"workload": WORKLOAD if args.subsims == 64 else f"reduced: {args.subsims} of " + WORKLOAD,
                           "n_subsims": len(run.subsims), "k_points": 64 * len(run.subsims),
                           "orbitals_per_gpu": n_orb, "grid": "16^3", "bands": 16, "dt": 0.08,
-                          "precision": args.precision, "l2": "inputs (psi 2 GiB fp32) larger than L2",
+                          "precision": {"fp32_tc": "fp32 stencil/Taylor, split-bf16x3 tensor-core projector "
+                                                   "GEMMs with fp32 accumulation, fp64 rho/J/Hartree",
+                                        "fp32": "fp32 stencil/Taylor/projectors (CUDA cores), fp64 rho/J/Hartree",
+                                        "fp64": "fp64 throughout"}[args.precision],
+                          "l2": "inputs larger than L2 (psi 2 GiB in fp32), no flush needed",
                           "parallelism": f"replica x{world} (independent shifts per GPU)"},
                "roofline": roof, "e2e": e2e, "gpu_launches": launches,
                "clocks": clk.summary(),

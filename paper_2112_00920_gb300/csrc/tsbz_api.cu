@@ -343,7 +343,10 @@ template <typename T> int run_observe(tsbz_ctx* ctx, int fin_mode) {
     if (hc.unit_ids.empty()) continue;
     LaunchSet L = make_set(ctx, hc);
     ev_start(ctx, FAM_BRA);
-    launch_bra<T>(L, ctx->psi, ctx->Pa, 1, 1, ctx->stream);
+    if (ctx->precision == TSBZ_FP32_TC)
+      launch_bra_tc(L, ctx->psi, ctx->Pa, 1, ctx->stream);
+    else
+      launch_bra<T>(L, ctx->psi, ctx->Pa, 1, 1, ctx->stream);
     ev_stop(ctx);
     if (hc.dev.use_proj) ++ctx->launches;
     ev_start(ctx, FAM_OBS);
@@ -370,7 +373,31 @@ template <typename T> int run_hxc(tsbz_ctx* ctx) {
   return TSBZ_OK;
 }
 
+int run_step_tc(tsbz_ctx* ctx) {
+  run_field<float>(ctx, TSBZ_FIELD_STEP);
+  void* srcs[4] = {ctx->psi, ctx->tA, ctx->tB, ctx->tA};
+  void* dsts[4] = {ctx->tA, ctx->tB, ctx->tA, nullptr};
+  for (auto& hc : ctx->cells) {
+    if (hc.unit_ids.empty()) continue;
+    LaunchSet L = make_set(ctx, hc);
+    ev_start(ctx, FAM_BRA);
+    launch_bra_tc(L, ctx->psi, ctx->P, 0, ctx->stream);
+    ev_stop(ctx);
+    if (hc.dev.use_proj) ++ctx->launches;
+    for (int m = 1; m <= 4; ++m) {
+      ev_start(ctx, FAM_STAGE);
+      launch_stage_tc(L, srcs[m - 1], dsts[m - 1], ctx->psi, ctx->P, m, ctx->stream);
+      ev_stop(ctx);
+      ++ctx->launches;
+    }
+  }
+  run_observe<float>(ctx, TSBZ_FIN_STEP);
+  run_hxc<float>(ctx);
+  return TSBZ_OK;
+}
+
 template <typename T> int run_step(tsbz_ctx* ctx) {
+  if (ctx->precision == TSBZ_FP32_TC) return run_step_tc(ctx);
   run_field<T>(ctx, TSBZ_FIELD_STEP);
   void* srcs[4] = {ctx->psi, ctx->tA, ctx->tB, ctx->tA};
   void* dsts[4] = {ctx->tA, ctx->tB, ctx->tA, nullptr};
@@ -484,7 +511,7 @@ int tsbz_version(void) { return 10000; }
 int tsbz_create(tsbz_ctx** out, int device, int precision, void* cuda_stream, const tsbz_alloc* alloc) {
   if (!out) return TSBZ_EINVAL;
   *out = nullptr;
-  if (precision != TSBZ_FP64 && precision != TSBZ_FP32) return TSBZ_EINVAL;
+  if (precision != TSBZ_FP64 && precision != TSBZ_FP32 && precision != TSBZ_FP32_TC) return TSBZ_EINVAL;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
     cudaGetLastError();
@@ -521,6 +548,10 @@ int tsbz_init_cell(tsbz_ctx* ctx, const tsbz_cell_desc* d, int* cell_id) {
   if (d->hxc_mode != TSBZ_HXC_SCF && d->hxc_mode != TSBZ_HXC_FROZEN) return set_err(ctx, TSBZ_EINVAL, "bad hxc_mode");
   const long long npts = (long long)d->n[0] * d->n[1] * d->n[2];
   if (npts > (1LL << 30)) return set_err(ctx, TSBZ_EINVAL, "grid too large");
+  if (ctx->precision == TSBZ_FP32_TC &&
+      (d->fd_nd != 4 || d->n_bands > 16 || (d->use_projectors && 4 * d->n_atoms > 32)))
+    return set_err(ctx, TSBZ_EINVAL,
+                   "the tensor-core mode needs fd_nd = 4, n_bands <= 16 and at most 32 projectors per cell");
   HostCell hc;
   hc.desc = *d;
   hc.atoms.assign(d->atom_frac, d->atom_frac + 3 * d->n_atoms);

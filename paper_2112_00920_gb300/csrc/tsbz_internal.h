@@ -117,3 +117,6 @@ int launch_hxc_t(const SubDev* subs_dev, const int* sub_ids_dev, int n_subs, con
 template <typename T> void launch_convert_in_t(const double2* src, void* dst, long long n, void* stream);
 template <typename T> void launch_convert_out_t(const void* src, double2* dst, long long n, void* stream);
 template <typename T> void launch_veff_frozen_t(const SubDev* subs_dev, int s, const CellDev& c, void* stream);
+// tensor-core mode (float orbitals)
+void launch_bra_tc(const LaunchSet& L, const void* psi, void* out, int with_d, void* stream);
+void launch_stage_tc(const LaunchSet& L, const void* tin, void* tout, void* psi, void* P, int m, void* stream);

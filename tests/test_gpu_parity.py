@@ -43,6 +43,35 @@ def test_cell_tables_match_oracle():
         P.close()
 
 
+TC_J_TOL, TC_RHO_TOL = 1e-4, 1e-5   # split-BF16 projector products (~2^-17 per product) + float orbitals
+
+
+@pytest.mark.parametrize("case", ["tiny", "ragged"])
+def test_parity_fp32_tc_small(case):
+    """Tensor-core mode on a tiny cell (4 point tiles) and a ragged 10 x 12 x 14 grid
+    (13.1 tiles, non-grid atoms, pulse)."""
+    if case == "tiny":
+        cell = _tiny_pair()
+        subs = [random_subsim(cell, (2, 2, 1), (0.25, 0.5, 0.0), 0.08, 6, W.Kick(k0=0.01), seed=1)]
+    else:
+        cell = W.cell_tiny(atoms="offgrid", n=(10, 12, 14), a=(7.0, 8.0, 9.0), n_bands=3)
+        pulse = W.Pulse(e0=0.05, omega0=0.3, t_pulse=0.8, direction=(0.3, 0.4, 0.866))
+        subs = [random_subsim(cell, (5, 1, 1), (0.1, 0.2, 0.3), 0.05, 6, pulse, seed=2)]
+    _, g = gpu_run(cell, subs, precision="fp32_tc")
+    o = oracle_run(cell, subs[0])
+    errs = compare(g[0], o, TC_J_TOL, TC_RHO_TOL)
+    print(f"fp32_tc {case}:", errs)
+
+
+def test_tc_mode_rejects_unsupported_cells():
+    from paper_2112_00920_gb300 import Propagator, TsbzError
+    P = Propagator("fp32_tc")
+    with pytest.raises(TsbzError) as e:
+        P.add_cell_spec(W.cell_tiny(atoms="one", n=(9, 9, 9), n_bands=40, proj_half=4.5))
+    assert e.value.code == -1
+    P.close()
+
+
 def test_parity_tiny_fp64_kick():
     cell = _tiny_pair()
     subs = [random_subsim(cell, (2, 2, 1), (0.25, 0.5, 0.0), 0.08, 10, W.Kick(k0=0.01), seed=1)]
@@ -114,6 +143,20 @@ def test_parity_config1_fp32(config1_ground_state):
     print("fp32 config1:", errs, "err_dJ", e_dj)
 
 
+def test_parity_config1_fp32_tc(config1_ground_state):
+    """Tensor-core mode on config 1 (SCF ground state, 20 steps)."""
+    sub, gs = config1_ground_state
+    s = dict(mp=sub.mp, shift=sub.shift, psi=gs["u"], dt=sub.dt, n_steps=20, field=sub.field)
+    _, g = gpu_run(sub.cell, [s], precision="fp32_tc")
+    o = oracle_run(sub.cell, s)
+    dj_g = g[0]["J"] - g[0]["J0m"]
+    dj_o = o["J"] - o["J0_minus"]
+    e_dj = float(np.max(np.abs(dj_g - dj_o)) / np.max(np.abs(dj_o)))
+    errs = compare(g[0], o, TC_J_TOL, TC_RHO_TOL, TC_RHO_TOL)
+    assert e_dj < 1e-3, e_dj
+    print("fp32_tc config1:", errs, "err_dJ", e_dj)
+
+
 def test_free_electron_closed_form_gpu():
     """Plane waves in an empty 16^3 cell: J(t) follows the closed form."""
     cell = W.free_electron(W.cell_a(n_bands=16))
@@ -146,7 +189,7 @@ def test_two_step_average_gpu():
         compare(gi, oi, FP64_J_TOL, FP64_RHO_TOL)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_tc"])
 def test_checkpoint_restart_bitwise(precision):
     """propagate(6) == propagate(3) + get_state/load_state + propagate(3), bit for bit."""
     cell = _tiny_pair()
@@ -188,7 +231,7 @@ def test_error_paths():
     P.close()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_tc"])
 def test_full_two_step_workload_sampled(precision):
     """The benchmark's launch configuration: 64 shifted 4^3 subgrids of cell A
     (4096 k, 65 536 orbitals), plane-wave start, kick; two steps.  Sub-simulations
@@ -214,4 +257,4 @@ def test_full_two_step_workload_sampled(precision):
         if precision == "fp64":
             compare(g, o, FP64_J_TOL, FP64_RHO_TOL)
         else:
-            compare(g, o, 1e-4, 1e-5, 1e-5)
+            print(precision, m, compare(g, o, 1e-4, 1e-5, 1e-5))
