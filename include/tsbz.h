@@ -163,8 +163,8 @@ int tsbz_get_cell_tables(tsbz_ctx* ctx, int cell_id, double* vloc, size_t cap, d
 int tsbz_get_launch_count(tsbz_ctx* ctx, long long* launches);
 
 /* Device time of the most recent tsbz_propagate (CUDA events on the
- * context stream) split by kernel family: times_ms[0..5] =
- * {bra, stage, observe, finalize, hxc, field}; bytes are not measured. */
+ * context stream, recorded only while profiling is on) split by kernel
+ * family: times_ms[0..6] = {bra, stage, observe, finalize, hxc, field, ket}. */
 int tsbz_get_timings(tsbz_ctx* ctx, double* times_ms, int n);
 int tsbz_set_profiling(tsbz_ctx* ctx, int on);
 

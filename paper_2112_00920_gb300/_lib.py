@@ -354,6 +354,6 @@ class Propagator:
         self._check(self.lib.tsbz_set_profiling(self.ctx, 1 if on else 0), "tsbz_set_profiling")
 
     def timings(self):
-        t = np.zeros(6)
-        self._check(self.lib.tsbz_get_timings(self.ctx, _dptr(t), 6), "tsbz_get_timings")
-        return dict(zip(["bra", "stage", "observe", "finalize", "hxc", "field"], t.tolist()))
+        t = np.zeros(7)
+        self._check(self.lib.tsbz_get_timings(self.ctx, _dptr(t), 7), "tsbz_get_timings")
+        return dict(zip(["bra", "stage", "observe", "finalize", "hxc", "field", "ket"], t.tolist()))

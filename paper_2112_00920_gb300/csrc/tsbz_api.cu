@@ -76,6 +76,7 @@ struct tsbz_ctx {
   void* tB = nullptr;
   void* P = nullptr;
   void* Pa = nullptr;
+  void* vnl = nullptr;     // non-local term of the tensor-core mode
   void* ph_half = nullptr;
   void* ph_obs = nullptr;
   long long ph_stride = 1;
@@ -100,7 +101,7 @@ struct tsbz_ctx {
   std::vector<long long> unit_psi_off;
   long long launches = 0;
   bool prof = false;
-  double times[6] = {0, 0, 0, 0, 0, 0};
+  double times[7] = {0, 0, 0, 0, 0, 0, 0};
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, int>> ev_marks;   // (family, event index of start)
   size_t ev_next = 0;
@@ -109,7 +110,8 @@ struct tsbz_ctx {
 
 namespace {
 
-enum { FAM_BRA = 0, FAM_STAGE = 1, FAM_OBS = 2, FAM_FIN = 3, FAM_HXC = 4, FAM_FIELD = 5 };
+enum { FAM_BRA = 0, FAM_STAGE = 1, FAM_OBS = 2, FAM_FIN = 3, FAM_HXC = 4, FAM_FIELD = 5, FAM_KET = 6 };
+#define TSBZ_N_FAM 7
 
 int set_err(tsbz_ctx* c, int code, const std::string& msg) {
   if (c) c->err = msg;
@@ -232,6 +234,7 @@ int layout(tsbz_ctx* ctx) {
   if ((rc = dalloc(ctx, psi_e * es, &ctx->tA))) return rc;
   if ((rc = dalloc(ctx, psi_e * es, &ctx->tB))) return rc;
   if ((rc = dalloc(ctx, std::max<long long>(p_e, 1) * es, &ctx->P))) return rc;
+  if (ctx->precision == TSBZ_FP32_TC && (rc = dalloc(ctx, psi_e * es, &ctx->vnl))) return rc;
   if ((rc = dalloc(ctx, std::max<long long>(pa_e, 1) * es, &ctx->Pa))) return rc;
   if ((rc = dalloc(ctx, ctx->n_units * ph_stride * es, &ctx->ph_half))) return rc;
   if ((rc = dalloc(ctx, ctx->n_units * ph_stride * es, &ctx->ph_obs))) return rc;
@@ -385,10 +388,19 @@ int run_step_tc(tsbz_ctx* ctx) {
     ev_stop(ctx);
     if (hc.dev.use_proj) ++ctx->launches;
     for (int m = 1; m <= 4; ++m) {
-      ev_start(ctx, FAM_STAGE);
-      launch_stage_tc(L, srcs[m - 1], dsts[m - 1], ctx->psi, ctx->P, m, ctx->stream);
+      ev_start(ctx, FAM_KET);
+      launch_ket_tc(L, ctx->P, ctx->vnl, ctx->stream);
       ev_stop(ctx);
-      ++ctx->launches;
+      ev_start(ctx, FAM_STAGE);
+      launch_stage_v(L, srcs[m - 1], dsts[m - 1], ctx->psi, ctx->vnl, m, ctx->stream);
+      ev_stop(ctx);
+      ctx->launches += 2;
+      if (m < 4 && hc.dev.use_proj) {
+        ev_start(ctx, FAM_BRA);
+        launch_bra_tc(L, dsts[m - 1], ctx->P, 0, ctx->stream);
+        ev_stop(ctx);
+        ++ctx->launches;
+      }
     }
   }
   run_observe<float>(ctx, TSBZ_FIN_STEP);
@@ -549,9 +561,11 @@ int tsbz_init_cell(tsbz_ctx* ctx, const tsbz_cell_desc* d, int* cell_id) {
   const long long npts = (long long)d->n[0] * d->n[1] * d->n[2];
   if (npts > (1LL << 30)) return set_err(ctx, TSBZ_EINVAL, "grid too large");
   if (ctx->precision == TSBZ_FP32_TC &&
-      (d->fd_nd != 4 || d->n_bands > 16 || (d->use_projectors && 4 * d->n_atoms > 32)))
+      (d->fd_nd != 4 || d->n_bands > 16 || (d->use_projectors && 4 * d->n_atoms > 32) ||
+       std::max(d->n[0], std::max(d->n[1], d->n[2])) > 32))
     return set_err(ctx, TSBZ_EINVAL,
-                   "the tensor-core mode needs fd_nd = 4, n_bands <= 16 and at most 32 projectors per cell");
+                   "the tensor-core mode needs fd_nd = 4, n_bands <= 16, at most 32 projectors and "
+                   "grid edges <= 32 per cell");
   HostCell hc;
   hc.desc = *d;
   hc.atoms.assign(d->atom_frac, d->atom_frac + 3 * d->n_atoms);
@@ -580,6 +594,8 @@ int tsbz_init_cell(tsbz_ctx* ctx, const tsbz_cell_desc* d, int* cell_id) {
     for (int m = 0; m <= d->fd_nd; ++m) {
       c.lapw[ax][m] = cw[m] / (h * h);
       c.gradw[ax][m] = dw[m] / h;
+      c.hlapf[ax][m] = (float)(-0.5 * cw[m] / (h * h));
+      c.gradwf[ax][m] = (float)(dw[m] / h);
     }
     c.gsq_scale[ax] = 2.0 * 3.14159265358979323846 / d->a[ax];
   }
@@ -740,7 +756,7 @@ int tsbz_propagate(tsbz_ctx* ctx, int n_steps) {
   if ((rc = sync_and_check(ctx))) return rc;
   for (auto& hs : ctx->subs) hs.steps += n_steps;
   if (ctx->prof) {
-    for (int f = 0; f < 6; ++f) ctx->times[f] = 0.0;
+    for (int f = 0; f < TSBZ_N_FAM; ++f) ctx->times[f] = 0.0;
     for (auto& m : ctx->ev_marks) {
       float ms = 0.f;
       cudaEventElapsedTime(&ms, ctx->ev_pool[m.second], ctx->ev_pool[m.second + 1]);
@@ -890,7 +906,7 @@ int tsbz_set_profiling(tsbz_ctx* ctx, int on) {
 
 int tsbz_get_timings(tsbz_ctx* ctx, double* times_ms, int n) {
   if (!ctx || !times_ms || n < 0) return TSBZ_EINVAL;
-  for (int i = 0; i < n && i < 6; ++i) times_ms[i] = ctx->times[i];
+  for (int i = 0; i < n && i < TSBZ_N_FAM; ++i) times_ms[i] = ctx->times[i];
   return TSBZ_OK;
 }
 

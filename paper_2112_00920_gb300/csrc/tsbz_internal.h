@@ -28,6 +28,8 @@ struct CellDev {
   double dv, omega, occ;
   double lapw[3][TSBZ_MAX_ND + 1];   // c_m / h_ax^2 (m = 0..nd)
   double gradw[3][TSBZ_MAX_ND + 1];  // d_m / h_ax   (m = 1..nd)
+  float hlapf[3][TSBZ_MAX_ND + 1];   // -1/2 c_m / h_ax^2 in float
+  float gradwf[3][TSBZ_MAX_ND + 1];  // d_m / h_ax in float
   double gsq_scale[3];               // (2 pi / a_ax)
   const double* g1;     // [n_atoms][3][nmax] Gaussian factor exp(-d^2/(2 rc^2)), 0 outside the box
   const double* d1;     // [n_atoms][3][nmax] minimum-image displacement, 0 outside the box
@@ -120,3 +122,5 @@ template <typename T> void launch_veff_frozen_t(const SubDev* subs_dev, int s, c
 // tensor-core mode (float orbitals)
 void launch_bra_tc(const LaunchSet& L, const void* psi, void* out, int with_d, void* stream);
 void launch_stage_tc(const LaunchSet& L, const void* tin, void* tout, void* psi, void* P, int m, void* stream);
+void launch_ket_tc(const LaunchSet& L, const void* P, void* V, void* stream);
+void launch_stage_v(const LaunchSet& L, const void* tin, void* tout, void* psi, const void* V, int m, void* stream);

@@ -354,6 +354,171 @@ __global__ void __launch_bounds__(TSBZ_PT) k_stage(LaunchSet L, const typename C
 }
 
 // ----------------------------------------------------------------------------
+// stage m with the non-local term supplied: t_m = (-i dt/m)[h_loc t + V]
+// (V = sum_j beta~_j E_j P_jb from the tensor-core ket), psi accumulation as
+// in k_stage.  Thread per point with its 2 x 3 x ND neighbour offsets
+// computed once; grid (point tiles, units), TSBZ_PT threads.
+// ----------------------------------------------------------------------------
+template <typename T, int ND>
+__global__ void __launch_bounds__(TSBZ_PT) k_stage_v(LaunchSet L, const typename Cplx<T>::type* __restrict__ tin,
+                                                     typename Cplx<T>::type* __restrict__ tout,
+                                                     typename Cplx<T>::type* __restrict__ psi,
+                                                     const typename Cplx<T>::type* __restrict__ V, int m) {
+  using VT = typename Cplx<T>::type;
+  const CellDev& c = L.cell;
+  const int u = L.unit_ids[blockIdx.y];
+  const UnitDev U = L.units[u];
+  const SubDev S = L.subs[U.sub];
+  const int p = blockIdx.x * TSBZ_PT + threadIdx.x;
+  if (p >= c.npts) return;
+  const int n12 = c.n1 * c.n2;
+  const int ix = p % c.n1, iy = (p / c.n1) % c.n2, iz = p / n12;
+  int off[6 * ND];
+#pragma unroll
+  for (int mm = 1; mm <= ND; ++mm) {
+    off[6 * (mm - 1) + 0] = wrap_idx(ix + mm, c.n1) - ix;
+    off[6 * (mm - 1) + 1] = wrap_idx(ix - mm, c.n1) - ix;
+    off[6 * (mm - 1) + 2] = (wrap_idx(iy + mm, c.n2) - iy) * c.n1;
+    off[6 * (mm - 1) + 3] = (wrap_idx(iy - mm, c.n2) - iy) * c.n1;
+    off[6 * (mm - 1) + 4] = (wrap_idx(iz + mm, c.n3) - iz) * n12;
+    off[6 * (mm - 1) + 5] = (wrap_idx(iz - mm, c.n3) - iz) * n12;
+  }
+  const T* qt = reinterpret_cast<const T*>(L.qt_half) + 4 * u;
+  const T q0 = qt[0], q1 = qt[1], q2 = qt[2];
+  const T dg = (T)(c.hlapf[0][0] + c.hlapf[1][0] + c.hlapf[2][0]) + qt[3] + reinterpret_cast<const T*>(S.veff)[p];
+  const T hdt = (T)S.dt / (T)m;
+  for (int b = 0; b < c.n_bands; ++b) {
+    const long long base = U.psi_off + (long long)b * c.npts + p;
+    const VT* tb = tin + base;
+    const VT ce = tb[0];
+    T hx = dg * ce.x, hy = dg * ce.y;
+    T gxr = 0, gxi = 0, gyr = 0, gyi = 0, gzr = 0, gzi = 0;
+#pragma unroll
+    for (int mm = 1; mm <= ND; ++mm) {
+      const VT xu = tb[off[6 * (mm - 1) + 0]], xd = tb[off[6 * (mm - 1) + 1]];
+      const VT yu = tb[off[6 * (mm - 1) + 2]], yd = tb[off[6 * (mm - 1) + 3]];
+      const VT zu = tb[off[6 * (mm - 1) + 4]], zd = tb[off[6 * (mm - 1) + 5]];
+      hx = fma((T)c.hlapf[0][mm], xu.x + xd.x, hx);
+      hy = fma((T)c.hlapf[0][mm], xu.y + xd.y, hy);
+      hx = fma((T)c.hlapf[1][mm], yu.x + yd.x, hx);
+      hy = fma((T)c.hlapf[1][mm], yu.y + yd.y, hy);
+      hx = fma((T)c.hlapf[2][mm], zu.x + zd.x, hx);
+      hy = fma((T)c.hlapf[2][mm], zu.y + zd.y, hy);
+      gxr = fma((T)c.gradwf[0][mm], xu.x - xd.x, gxr);
+      gxi = fma((T)c.gradwf[0][mm], xu.y - xd.y, gxi);
+      gyr = fma((T)c.gradwf[1][mm], yu.x - yd.x, gyr);
+      gyi = fma((T)c.gradwf[1][mm], yu.y - yd.y, gyi);
+      gzr = fma((T)c.gradwf[2][mm], zu.x - zd.x, gzr);
+      gzi = fma((T)c.gradwf[2][mm], zu.y - zd.y, gzi);
+    }
+    const VT v = V[base];
+    const T qgr = fma(q0, gxr, fma(q1, gyr, q2 * gzr));
+    const T qgi = fma(q0, gxi, fma(q1, gyi, q2 * gzi));
+    const T hr = hx + qgi + v.x;
+    const T hi = hy - qgr + v.y;
+    const VT t = cmk<VT>(hdt * hi, -hdt * hr);
+    if (m < 4) tout[base] = t;
+    if (m == 2) {
+      psi[base] = cadd(psi[base], cadd(ce, t));
+    } else if (m >= 3) {
+      psi[base] = cadd(psi[base], t);
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// stage m, 2.5-D form: one CTA per (band, unit), one thread per (x, y) column
+// marching in z.  Each thread keeps the 2 ND + 1 values of its column around
+// the current plane in a register queue; the current plane is also written
+// to shared memory for the in-plane neighbours; plane z + ND + 1 is loaded
+// one step ahead.  t_m = (-i dt/m)[h_loc t + V], psi accumulation as in
+// k_stage.  Requires n1 * n2 <= blockDim.x (one thread per column).
+// ----------------------------------------------------------------------------
+template <typename T, int ND>
+__global__ void __launch_bounds__(256, 4) k_stage_z(LaunchSet L, const typename Cplx<T>::type* __restrict__ tin,
+                                                 typename Cplx<T>::type* __restrict__ tout,
+                                                 typename Cplx<T>::type* __restrict__ psi,
+                                                 const typename Cplx<T>::type* __restrict__ V, int m) {
+  using VT = typename Cplx<T>::type;
+  extern __shared__ __align__(16) unsigned char zraw[];
+  VT* plane = reinterpret_cast<VT*>(zraw);
+  const CellDev& c = L.cell;
+  const int b = blockIdx.x;
+  const int u = L.unit_ids[blockIdx.y];
+  const UnitDev U = L.units[u];
+  const SubDev S = L.subs[U.sub];
+  const int n1 = c.n1, n2 = c.n2, n3 = c.n3, n12 = n1 * n2;
+  const int col = threadIdx.x;
+  const bool act = col < n12;
+  const int ix = act ? col % n1 : 0, iy = act ? col / n1 : 0;
+  const int rowb = iy * n1;
+  const T* qt = reinterpret_cast<const T*>(L.qt_half) + 4 * u;
+  const T q0 = qt[0], q1 = qt[1], q2 = qt[2];
+  const T dg0 = (T)(c.hlapf[0][0] + c.hlapf[1][0] + c.hlapf[2][0]) + qt[3];
+  const T hdt = (T)S.dt / (T)m;
+  const T* veff = reinterpret_cast<const T*>(S.veff);
+  const long long base0 = U.psi_off + (long long)b * c.npts + col;
+  const VT* tb = tin + base0;
+  // queue[k] = t(z - ND + k) of this column
+  VT qv[2 * ND + 1];
+  const VT zero = cmk<VT>((T)0, (T)0);
+#pragma unroll
+  for (int k = 0; k < 2 * ND + 1; ++k) {
+    const int zz = wrap_idx(k - ND, n3);
+    qv[k] = act ? tb[(long long)zz * n12] : zero;
+  }
+  for (int z = 0; z < n3; ++z) {
+    // prefetch t(z + ND + 1)
+    const int zn = wrap_idx(wrap_idx(z + ND + 1, n3), n3);
+    const VT nxt = act ? tb[(long long)zn * n12] : zero;
+    __syncthreads();
+    if (act) plane[col] = qv[ND];
+    __syncthreads();
+    if (act) {
+      const VT ce = qv[ND];
+      const long long idx = base0 + (long long)z * n12;
+      const T dg = dg0 + veff[z * n12 + col];
+      T hx = dg * ce.x, hy = dg * ce.y;
+      T gxr = 0, gxi = 0, gyr = 0, gyi = 0, gzr = 0, gzi = 0;
+#pragma unroll
+      for (int mm = 1; mm <= ND; ++mm) {
+        const VT xu = plane[rowb + wrap_idx(ix + mm, n1)], xd = plane[rowb + wrap_idx(ix - mm, n1)];
+        const VT yu = plane[wrap_idx(iy + mm, n2) * n1 + ix], yd = plane[wrap_idx(iy - mm, n2) * n1 + ix];
+        const VT zu = qv[ND + mm], zd = qv[ND - mm];
+        hx = fma((T)c.hlapf[0][mm], xu.x + xd.x, hx);
+        hy = fma((T)c.hlapf[0][mm], xu.y + xd.y, hy);
+        hx = fma((T)c.hlapf[1][mm], yu.x + yd.x, hx);
+        hy = fma((T)c.hlapf[1][mm], yu.y + yd.y, hy);
+        hx = fma((T)c.hlapf[2][mm], zu.x + zd.x, hx);
+        hy = fma((T)c.hlapf[2][mm], zu.y + zd.y, hy);
+        gxr = fma((T)c.gradwf[0][mm], xu.x - xd.x, gxr);
+        gxi = fma((T)c.gradwf[0][mm], xu.y - xd.y, gxi);
+        gyr = fma((T)c.gradwf[1][mm], yu.x - yd.x, gyr);
+        gyi = fma((T)c.gradwf[1][mm], yu.y - yd.y, gyi);
+        gzr = fma((T)c.gradwf[2][mm], zu.x - zd.x, gzr);
+        gzi = fma((T)c.gradwf[2][mm], zu.y - zd.y, gzi);
+      }
+      const VT v = V[idx];
+      const T qgr = fma(q0, gxr, fma(q1, gyr, q2 * gzr));
+      const T qgi = fma(q0, gxi, fma(q1, gyi, q2 * gzi));
+      const T hr = hx + qgi + v.x;
+      const T hi = hy - qgr + v.y;
+      const VT t = cmk<VT>(hdt * hi, -hdt * hr);
+      if (m < 4) tout[idx] = t;
+      if (m == 2) {
+        psi[idx] = cadd(psi[idx], cadd(ce, t));
+      } else if (m >= 3) {
+        psi[idx] = cadd(psi[idx], t);
+      }
+    }
+    // advance the queue
+#pragma unroll
+    for (int k = 0; k < 2 * ND; ++k) qv[k] = qv[k + 1];
+    qv[2 * ND] = nxt;
+  }
+}
+
+// ----------------------------------------------------------------------------
 // observe: per (unit, point tile, band group) sums for rho, kinetic current
 // and band norms.  grid (point tiles, units, band groups), TSBZ_PT threads.
 // At one grid point the sums over the bands of the group are formed in T

@@ -9,19 +9,45 @@ static void tc_set_attributes() {
   if (tc_attr_set) return;
   cudaFuncSetAttribute(k_bra_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TcSmem));
   cudaFuncSetAttribute(k_stage_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TcSmem));
+  cudaFuncSetAttribute(k_ket_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TcSmem));
   tc_attr_set = true;
 }
 
 void launch_bra_tc(const LaunchSet& L, const void* psi, void* out, int with_d, void* stream) {
   if (L.n_units == 0 || !L.cell.use_proj) return;
   tc_set_attributes();
-  dim3 grid(with_d ? 4 : 1, L.n_units);
-  k_bra_tc<<<grid, TC_THREADS, sizeof(TcSmem), (cudaStream_t)stream>>>(L, (const float2*)psi, (float2*)out, with_d);
+  // one cluster of TC_CL CTAs per unit (all four current weightings in one pass when with_d)
+  k_bra_tc<<<L.n_units * TC_CL, TC_THREADS, sizeof(TcSmem), (cudaStream_t)stream>>>(L, (const float2*)psi,
+                                                                                      (float2*)out, with_d);
 }
 
 void launch_stage_tc(const LaunchSet& L, const void* tin, void* tout, void* psi, void* P, int m, void* stream) {
   if (L.n_units == 0) return;
   tc_set_attributes();
-  k_stage_tc<<<L.n_units, TC_THREADS, sizeof(TcSmem), (cudaStream_t)stream>>>(
+  k_stage_tc<<<L.n_units * TC_CL, TC_THREADS, sizeof(TcSmem), (cudaStream_t)stream>>>(
       L, (const float2*)tin, (float2*)tout, (float2*)psi, (const float2*)P, (float2*)P, m);
+}
+
+void launch_ket_tc(const LaunchSet& L, const void* P, void* V, void* stream) {
+  if (L.n_units == 0) return;
+  tc_set_attributes();
+  const int n_tiles = (L.cell.npts + TC_PT - 1) / TC_PT;
+  dim3 grid((n_tiles + TC_KET_TILES - 1) / TC_KET_TILES, L.n_units);
+  k_ket_tc<<<grid, TC_THREADS, sizeof(TcSmem), (cudaStream_t)stream>>>(L, (const float2*)P, (float2*)V);
+}
+
+void launch_stage_v(const LaunchSet& L, const void* tin, void* tout, void* psi, const void* V, int m, void* stream) {
+  if (L.n_units == 0) return;
+  const int n12 = L.cell.n1 * L.cell.n2;
+  if (n12 <= 256) {
+    // 2.5-D z-march: one CTA per (band, unit), one thread per (x, y) column
+    const int threads = ((n12 + 31) / 32) * 32;
+    dim3 grid(L.cell.n_bands, L.n_units);
+    k_stage_z<float, TC_ND><<<grid, threads, n12 * sizeof(float2), (cudaStream_t)stream>>>(
+        L, (const float2*)tin, (float2*)tout, (float2*)psi, (const float2*)V, m);
+    return;
+  }
+  dim3 grid(L.cell.n_tiles, L.n_units);
+  k_stage_v<float, TC_ND><<<grid, TSBZ_PT, 0, (cudaStream_t)stream>>>(L, (const float2*)tin, (float2*)tout,
+                                                                      (float2*)psi, (const float2*)V, m);
 }

@@ -1,20 +1,25 @@
 // Tensor-core projector contractions (split-BF16, FP32 accumulate) and the
 // fused Taylor stage of the single-precision tensor-core mode.
 //
-// Projector values of one k-point, C_j(r) = conj(beta~_j(r)) = pnorm_j g(r) w_j(d) exp(+i q.d),
-// are generated per tile of TC_PT grid points in shared memory as a real
-// matrix Cs[pt][j'] (j' < 32: Re C_j, j' >= 32: Im C_j), each value split into
-// a BF16 high part and a BF16 low part (x ~ hi + lo).  A product A B is
-// evaluated as A_hi B_hi + A_hi B_lo + A_lo B_hi with mma.sync m16n8k16 and
-// FP32 accumulation.
+// Projector values of one k-point, C_j(r) = conj(beta~_j(r)) = pnorm_j F_x F_y F_z w_j,
+// with the per-axis factors F_ax(i) = g_ax(i) exp(+i q_ax d_ax(i)) and
+// w_j in {1, d_x, d_y, d_z}, are generated per tile of TC_PT grid points in
+// shared memory as a real matrix Cs[pt][j'] (j' < 32: Re C_j, j' >= 32:
+// Im C_j), each value split into a BF16 high part and a BF16 low part
+// (x ~ hi + lo).  A product A B is evaluated as A_hi B_hi + A_hi B_lo +
+// A_lo B_hi with mma.sync m16n8k16 and FP32 accumulation.
 //   bra  P_jb = dV sum_r C_j(r) t_b(r):  D[j'][n'] = sum_pt Cs[pt][j'] Ts[n'][pt]
 //        (n' < 16: Re t_b, n' >= 16: Im t_b), P_re = D[j][b] - D[32+j][16+b],
 //        P_im = D[j][16+b] + D[32+j][b]
 //   ket  V_b(r) = sum_j conj(C_j(r)) E_j P_jb:  V[pt][n'] = sum_j' Cs[pt][j'] Wt[n'][j']
 //        with Wt built from W = E P so that V[pt][b] = Re V_b, V[pt][16+b] = Im V_b.
-// One CTA handles one unit (k-point, all bands <= 16, projectors <= 32) and
-// loops over all point tiles, so every projection is complete inside the CTA.
+// A cluster of TC_CL CTAs handles one unit (k-point; bands <= 16,
+// projectors <= 32, grid edges <= 32); CTA rank r of the cluster takes a
+// contiguous chunk of the point tiles, so the CTAs of one unit run together
+// and share its orbitals in L2.  The per-CTA bra sums are added across the
+// cluster through distributed shared memory in rank order (deterministic).
 #pragma once
+#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -26,8 +31,11 @@
 #define TC_CS_PITCH 72     // bf16 per Cs row (64 + 8 padding)
 #define TC_W_PITCH 72      // bf16 per Wt row
 #define TC_TS_PITCH 136    // bf16 per Ts row (128 + 8 padding)
-#define TC_V_PITCH 33      // floats per Vs row
+#define TC_D_PITCH 33      // floats per row of the final bra combination
 #define TC_ND 4            // stencil half-width of the fused stage
+#define TC_NMAX 32         // largest grid edge
+#define TC_NA 8            // atoms (projectors / 4)
+#define TC_CL 8            // CTAs per cluster (one cluster per unit)
 
 struct TcSmem {
   __nv_bfloat16 cs_hi[TC_PT * TC_CS_PITCH];
@@ -36,12 +44,14 @@ struct TcSmem {
   __nv_bfloat16 ts_lo[32 * TC_TS_PITCH];
   __nv_bfloat16 w_hi[32 * TC_W_PITCH];
   __nv_bfloat16 w_lo[32 * TC_W_PITCH];
-  float vs[TC_PT * TC_V_PITCH];
+  float2 fac[TC_NA * 3 * TC_NMAX];   // F_ax(i) per atom and axis
+  float dis[TC_NA * 3 * TC_NMAX];    // d_ax(i)
+  float pn[TC_NA * 4];               // pnorm
 };
 
 // Split a pair (x, y) into packed BF16 high parts and packed BF16 low parts
-// (round to nearest for both); one packed conversion per part, because on
-// this GPU conversions issue on a narrow pipe.
+// (round to nearest for both); one packed conversion per part, because
+// conversions issue on a narrow pipe.
 __device__ __forceinline__ void tc_split2(float x, float y, uint32_t& hi, uint32_t& lo) {
   const __nv_bfloat162 h = __floats2bfloat162_rn(x, y);
   const float2 hf = __bfloat1622float2(h);
@@ -71,29 +81,42 @@ __device__ __forceinline__ void tc_ldsm_x4_trans(uint32_t (&r)[4], const __nv_bf
                : "r"(addr));
 }
 
-// Generate Cs for points p0 .. p0+TC_PT-1 of unit u.  alpha = 0: plain
-// projector rows; alpha = 1..3: rows multiplied by d_x, d_y, d_z.
-__device__ __forceinline__ void tc_gen_c(TcSmem& sm, const CellDev& c, const float2* ph, int p0, int alpha) {
+// Per-axis factors F_ax(i) = g_ax(i) * phase_ax(i), displacements and
+// normalisations of one unit into shared memory.
+__device__ __forceinline__ void tc_load_tables(TcSmem& sm, const CellDev& c, const float2* ph) {
   const int nm = c.nmax;
-  for (int i = threadIdx.x; i < TC_PT * 8; i += TC_THREADS) {
+  const int n = c.n_atoms * 3 * nm;
+  for (int i = threadIdx.x; i < n; i += TC_THREADS) {
+    const int a = i / (3 * nm), r = i % (3 * nm);
+    const int ax = r / nm, ii = r % nm;
+    const float g = c.g1f[i];
+    const float2 p = ph[i];
+    sm.fac[(a * 3 + ax) * TC_NMAX + ii] = make_float2(g * p.x, g * p.y);
+    sm.dis[(a * 3 + ax) * TC_NMAX + ii] = c.d1f[i];
+  }
+  for (int i = threadIdx.x; i < 4 * c.n_atoms; i += TC_THREADS) sm.pn[i] = c.pnormf[i];
+}
+
+// Cs for points p0 .. p0+TC_PT-1.  alpha = 0: plain projector rows;
+// alpha = 1..3: rows multiplied by d_x, d_y, d_z.
+__device__ __forceinline__ void tc_gen_c(TcSmem& sm, const CellDev& c, int p0, int alpha) {
+  for (int i = threadIdx.x; i < TC_PT * TC_NA; i += TC_THREADS) {
     const int pt = i % TC_PT, a = i / TC_PT;
     const int p = p0 + pt;
     float cr[4] = {0.f, 0.f, 0.f, 0.f}, ci[4] = {0.f, 0.f, 0.f, 0.f};
     if (p < c.npts && a < c.n_atoms) {
       const int ix = p % c.n1, iy = (p / c.n1) % c.n2, iz = p / (c.n1 * c.n2);
-      const float* ga = c.g1f + (long long)a * 3 * nm;
-      const float* da = c.d1f + (long long)a * 3 * nm;
-      const float g = ga[ix] * ga[nm + iy] * ga[2 * nm + iz];
-      const float d[3] = {da[ix], da[nm + iy], da[2 * nm + iz]};
-      const float2* pa = ph + (long long)a * 3 * nm;
-      const float2 px = pa[ix], py = pa[nm + iy], pz = pa[2 * nm + iz];
-      const float2 pxy = make_float2(px.x * py.x - px.y * py.y, px.x * py.y + px.y * py.x);
-      float fr = pxy.x * pz.x - pxy.y * pz.y, fi = pxy.x * pz.y + pxy.y * pz.x;
-      float sc = g;
-      if (alpha > 0) sc *= d[alpha - 1];
-      fr *= sc;
-      fi *= sc;
-      const float* pn = c.pnormf + 4 * a;
+      const float2* fa = sm.fac + a * 3 * TC_NMAX;
+      const float* da = sm.dis + a * 3 * TC_NMAX;
+      const float2 fx = fa[ix], fy = fa[TC_NMAX + iy], fz = fa[2 * TC_NMAX + iz];
+      const float d[3] = {da[ix], da[TC_NMAX + iy], da[2 * TC_NMAX + iz]};
+      const float2 fxy = make_float2(fx.x * fy.x - fx.y * fy.y, fx.x * fy.y + fx.y * fy.x);
+      float fr = fxy.x * fz.x - fxy.y * fz.y, fi = fxy.x * fz.y + fxy.y * fz.x;
+      if (alpha > 0) {
+        fr *= d[alpha - 1];
+        fi *= d[alpha - 1];
+      }
+      const float* pn = sm.pn + 4 * a;
       const float w[4] = {pn[0], pn[1] * d[0], pn[2] * d[1], pn[3] * d[2]};
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
@@ -141,36 +164,54 @@ __device__ __forceinline__ void tc_bra_tile(const TcSmem& sm, float (&acc)[2][4]
   }
 }
 
-// Write the bra result (dV * complex combination) of one unit: out[b * stride + j * jstep + joff]
-__device__ __forceinline__ void tc_bra_store(TcSmem& sm, const float (&acc)[2][4], const CellDev& c, float2* out,
-                                             int stride, int jstep, int joff) {
+// Finish a bra: each CTA writes its partial D[j'][n'] (64 x 32) into its
+// Cs area at slot `slot`; after a cluster barrier, CTA rank r forms the
+// outputs (j, b) with b in its share of the bands, summing the partials of
+// ranks 0..TC_CL-1 in order:
+//   out[b * stride + j * jstep + joff] = dV (P_re, P_im).
+// The caller runs the cluster barrier that ends the reads (tc_cluster_done).
+__device__ __forceinline__ void tc_bra_partial(TcSmem& sm, const float (&acc)[2][4], int slot) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, t = lane & 3;
   const int mt = warp >> 1, nt0 = 2 * (warp & 1);
-  float* D = sm.vs;  // [64][33]
-  __syncthreads();
+  float* D = reinterpret_cast<float*>(sm.cs_hi) + slot * 64 * TC_D_PITCH;
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
     const int n = 8 * (nt0 + j) + 2 * t;
     const int row = 16 * mt + g;
-    D[row * TC_V_PITCH + n] = acc[j][0];
-    D[row * TC_V_PITCH + n + 1] = acc[j][1];
-    D[(row + 8) * TC_V_PITCH + n] = acc[j][2];
-    D[(row + 8) * TC_V_PITCH + n + 1] = acc[j][3];
+    D[row * TC_D_PITCH + n] = acc[j][0];
+    D[row * TC_D_PITCH + n + 1] = acc[j][1];
+    D[(row + 8) * TC_D_PITCH + n] = acc[j][2];
+    D[(row + 8) * TC_D_PITCH + n + 1] = acc[j][3];
   }
-  __syncthreads();
+}
+
+__device__ __forceinline__ void tc_bra_reduce(TcSmem& sm, const CellDev& c, float2* out, int stride, int jstep,
+                                              int joff, int slot) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  float* Dloc = reinterpret_cast<float*>(sm.cs_hi) + slot * 64 * TC_D_PITCH;
   const float dv = (float)c.dv;
-  for (int i = threadIdx.x; i < 32 * 16; i += TC_THREADS) {
-    const int j = i % 32, b = i / 32;
+  const int per = (32 * 16) / TC_CL;   // outputs per CTA
+  for (int i = threadIdx.x; i < per; i += TC_THREADS) {
+    const int o = rank * per + i;
+    const int j = o % 32, b = o / 32;
     if (j < c.n_proj && b < c.n_bands) {
-      const float pr = D[j * TC_V_PITCH + b] - D[(32 + j) * TC_V_PITCH + 16 + b];
-      const float pi = D[j * TC_V_PITCH + 16 + b] + D[(32 + j) * TC_V_PITCH + b];
-      out[(long long)b * stride + j * jstep + joff] = make_float2(dv * pr, dv * pi);
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+      for (int r = 0; r < TC_CL; ++r) {
+        const float* D = cluster.map_shared_rank(Dloc, r);
+        a0 += D[j * TC_D_PITCH + b];
+        a1 += D[(32 + j) * TC_D_PITCH + 16 + b];
+        a2 += D[j * TC_D_PITCH + 16 + b];
+        a3 += D[(32 + j) * TC_D_PITCH + b];
+      }
+      out[(long long)b * stride + j * jstep + joff] = make_float2(dv * (a0 - a1), dv * (a2 + a3));
     }
   }
 }
 
-// Load a tile of orbitals (all bands) into Ts as split BF16.
+// A tile of orbitals (all bands) into Ts as split BF16.
 __device__ __forceinline__ void tc_load_ts(TcSmem& sm, const CellDev& c, const float2* src, int p0) {
   for (int i = threadIdx.x; i < TC_PT * 16; i += TC_THREADS) {
     const int pt = i % TC_PT, b = i / TC_PT;
@@ -187,56 +228,210 @@ __device__ __forceinline__ void tc_load_ts(TcSmem& sm, const CellDev& c, const f
 }
 
 // ----------------------------------------------------------------------------
-// Stand-alone bra of psi on tensor cores.  grid (4 alphas or 1, units).
-//   alpha = 0 with with_d = 0: P[u][b][j]            (q_half tables)
-//   with_d = 1: Pa[u][b][j][alpha], alpha = blockIdx.x (q_obs tables)
+// Stand-alone bra of psi on tensor cores, one cluster per unit.
+//   with_d = 0: P[u][b][j] from the q_half tables
+//   with_d = 1: Pa[u][b][j][alpha], alpha = 0..3 (plain and d_x, d_y, d_z
+//               weighted rows) from the q_obs tables, in one pass over psi
 // ----------------------------------------------------------------------------
-__global__ void __launch_bounds__(TC_THREADS, 2) k_bra_tc(LaunchSet L, const float2* __restrict__ psi,
-                                                          float2* __restrict__ out, int with_d) {
+__global__ void __cluster_dims__(TC_CL, 1, 1) __launch_bounds__(TC_THREADS, 3)
+    k_bra_tc(LaunchSet L, const float2* __restrict__ psi, float2* __restrict__ out, int with_d) {
+  extern __shared__ __align__(16) unsigned char tc_raw[];
+  TcSmem& sm = *reinterpret_cast<TcSmem*>(tc_raw);
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const CellDev& c = L.cell;
+  const int rank = (int)cluster.block_rank();
+  const int u = L.unit_ids[blockIdx.x / TC_CL];
+  const UnitDev U = L.units[u];
+  const float2* ph = (const float2*)(with_d ? L.ph_obs : L.ph_half) + (long long)u * L.ph_stride;
+  const int na = with_d ? 4 : 1;
+  const int n_tiles = (c.npts + TC_PT - 1) / TC_PT;
+  const int tpc = (n_tiles + TC_CL - 1) / TC_CL;
+  const int t_begin = rank * tpc, t_end = min(n_tiles, t_begin + tpc);
+  tc_load_tables(sm, c, ph);
+  float acc[4][2][4];
+#pragma unroll
+  for (int al = 0; al < 4; ++al)
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[al][j][e] = 0.f;
+  // Each thread carries 8 values (TC_PT x 16 / TC_THREADS) of the next tile
+  // in registers while the current tile's products run.
+  float2 nxt[8];
+  const float2* src = psi + U.psi_off;
+  auto fetch = [&](int p0) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int i = threadIdx.x + k * TC_THREADS;
+      const int pt = i % TC_PT, b = i / TC_PT;
+      const int p = p0 + pt;
+      nxt[k] = (p < c.npts && b < c.n_bands) ? src[(long long)b * c.npts + p] : make_float2(0.f, 0.f);
+    }
+  };
+  if (t_begin < t_end) fetch(t_begin * TC_PT);
+  for (int tile = t_begin; tile < t_end; ++tile) {
+    const int p0 = tile * TC_PT;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int i = threadIdx.x + k * TC_THREADS;
+      const int pt = i % TC_PT, b = i / TC_PT;
+      uint32_t hi, lo;
+      tc_split2(nxt[k].x, nxt[k].y, hi, lo);
+      tc_st16(sm.ts_hi + b * TC_TS_PITCH + pt, hi);
+      tc_st16(sm.ts_lo + b * TC_TS_PITCH + pt, lo);
+      tc_st16(sm.ts_hi + (16 + b) * TC_TS_PITCH + pt, hi >> 16);
+      tc_st16(sm.ts_lo + (16 + b) * TC_TS_PITCH + pt, lo >> 16);
+    }
+    if (tile + 1 < t_end) fetch(p0 + TC_PT);
+#pragma unroll
+    for (int al = 0; al < 4; ++al) {
+      if (al < na) {
+        if (al > 0) __syncthreads();
+        tc_gen_c(sm, c, p0, al);
+        __syncthreads();
+        tc_bra_tile(sm, acc[al]);
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int al = 0; al < 4; ++al)
+    if (al < na) tc_bra_partial(sm, acc[al], al);
+  cluster.sync();
+#pragma unroll
+  for (int al = 0; al < 4; ++al) {
+    if (al < na) {
+      if (with_d)
+        tc_bra_reduce(sm, c, (float2*)out + U.pa_off, 4 * c.n_proj, 4, al, al);
+      else
+        tc_bra_reduce(sm, c, (float2*)out + U.p_off, c.n_proj, 1, 0, al);
+    }
+  }
+  cluster.sync();   // peers stay resident until every CTA has read their partials
+}
+
+// ----------------------------------------------------------------------------
+// Tensor-core ket: V[u][b][r] = sum_j beta~_j(r) E_j P[u][b][j] (the non-local
+// term of h t), for a chunk of TC_KET_TILES point tiles per CTA.
+// grid (chunks, units), 256 threads; warp w computes points 16w..16w+15 of
+// a tile and writes its results straight from the MMA registers.
+// ----------------------------------------------------------------------------
+#define TC_KET_TILES 4
+__global__ void __launch_bounds__(TC_THREADS, 3) k_ket_tc(LaunchSet L, const float2* __restrict__ P,
+                                                          float2* __restrict__ V) {
   extern __shared__ __align__(16) unsigned char tc_raw[];
   TcSmem& sm = *reinterpret_cast<TcSmem*>(tc_raw);
   const CellDev& c = L.cell;
   const int u = L.unit_ids[blockIdx.y];
   const UnitDev U = L.units[u];
-  const int alpha = with_d ? blockIdx.x : 0;
-  const float2* ph = (const float2*)(with_d ? L.ph_obs : L.ph_half) + (long long)u * L.ph_stride;
-  float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-  for (int p0 = 0; p0 < c.npts; p0 += TC_PT) {
-    __syncthreads();
-    tc_gen_c(sm, c, ph, p0, alpha);
-    tc_load_ts(sm, c, psi + U.psi_off, p0);
-    __syncthreads();
-    tc_bra_tile(sm, acc);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, t4 = lane & 3;
+  tc_load_tables(sm, c, (const float2*)L.ph_half + (long long)u * L.ph_stride);
+  // Wt[b][j] = Wr, Wt[16+b][j] = Wi, Wt[b][32+j] = Wi, Wt[16+b][32+j] = -Wr, W = E P
+  for (int i = threadIdx.x; i < 32 * 16; i += TC_THREADS) {
+    const int j = i % 32, b = i / 32;
+    float wr = 0.f, wi = 0.f;
+    if (j < c.n_proj && b < c.n_bands) {
+      const float2 p = P[U.p_off + (long long)b * c.n_proj + j];
+      const float e = (float)c.ekb[j];
+      wr = e * p.x;
+      wi = e * p.y;
+    }
+    uint32_t hi, lo, nhi, nlo;
+    tc_split2(wr, wi, hi, lo);
+    tc_split2(-wr, wi, nhi, nlo);
+    tc_st16(sm.w_hi + b * TC_W_PITCH + j, hi);
+    tc_st16(sm.w_lo + b * TC_W_PITCH + j, lo);
+    tc_st16(sm.w_hi + (16 + b) * TC_W_PITCH + j, hi >> 16);
+    tc_st16(sm.w_lo + (16 + b) * TC_W_PITCH + j, lo >> 16);
+    tc_st16(sm.w_hi + b * TC_W_PITCH + 32 + j, nhi >> 16);
+    tc_st16(sm.w_lo + b * TC_W_PITCH + 32 + j, nlo >> 16);
+    tc_st16(sm.w_hi + (16 + b) * TC_W_PITCH + 32 + j, nhi);
+    tc_st16(sm.w_lo + (16 + b) * TC_W_PITCH + 32 + j, nlo);
   }
-  if (with_d)
-    tc_bra_store(sm, acc, c, (float2*)out + U.pa_off, 4 * c.n_proj, 4, alpha);
-  else
-    tc_bra_store(sm, acc, c, (float2*)out + U.p_off, c.n_proj, 1, 0);
+  const int n_tiles = (c.npts + TC_PT - 1) / TC_PT;
+  const int t_begin = blockIdx.x * TC_KET_TILES, t_end = min(n_tiles, t_begin + TC_KET_TILES);
+  for (int tile = t_begin; tile < t_end; ++tile) {
+    const int p0 = tile * TC_PT;
+    __syncthreads();
+    tc_gen_c(sm, c, p0, 0);
+    __syncthreads();
+    float d[4][4];
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) d[nt][e] = 0.f;
+    const int row = 16 * warp + g;
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) {
+      const int col = 16 * ks + 2 * t4;
+      uint32_t ahi[4], alo[4];
+      ahi[0] = tc_ld32(sm.cs_hi + row * TC_CS_PITCH + col);
+      ahi[1] = tc_ld32(sm.cs_hi + (row + 8) * TC_CS_PITCH + col);
+      ahi[2] = tc_ld32(sm.cs_hi + row * TC_CS_PITCH + col + 8);
+      ahi[3] = tc_ld32(sm.cs_hi + (row + 8) * TC_CS_PITCH + col + 8);
+      alo[0] = tc_ld32(sm.cs_lo + row * TC_CS_PITCH + col);
+      alo[1] = tc_ld32(sm.cs_lo + (row + 8) * TC_CS_PITCH + col);
+      alo[2] = tc_ld32(sm.cs_lo + row * TC_CS_PITCH + col + 8);
+      alo[3] = tc_ld32(sm.cs_lo + (row + 8) * TC_CS_PITCH + col + 8);
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        const int n = 8 * nt + g;
+        const uint32_t bh0 = tc_ld32(sm.w_hi + n * TC_W_PITCH + col), bh1 = tc_ld32(sm.w_hi + n * TC_W_PITCH + col + 8);
+        const uint32_t bl0 = tc_ld32(sm.w_lo + n * TC_W_PITCH + col), bl1 = tc_ld32(sm.w_lo + n * TC_W_PITCH + col + 8);
+        tc_mma(d[nt], alo, bh0, bh1);
+        tc_mma(d[nt], ahi, bl0, bl1);
+        tc_mma(d[nt], ahi, bh0, bh1);
+      }
+    }
+    // lane owns points row, row + 8 and bands 2t4, 2t4+1, 8+2t4, 9+2t4
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int p = p0 + row + 8 * r;
+      if (p >= c.npts) continue;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int b = 2 * t4 + (k & 1) + 8 * (k >> 1);
+        if (b < c.n_bands)
+          V[U.psi_off + (long long)b * c.npts + p] =
+              make_float2(d[k >> 1][2 * r + (k & 1)], d[2 + (k >> 1)][2 * r + (k & 1)]);
+      }
+    }
+  }
 }
 
 // ----------------------------------------------------------------------------
 // Fused Taylor stage m on tensor cores, one CTA per unit.
 //   t_m = (-i dt/m)[ -1/2 lap t - i q.grad t + (|q|^2/2 + v_eff) t + V_NL t ]
 //   psi accumulation as in k_stage; for m < 4 also P_m = <beta~|t_m> -> Pout.
+// Warp w owns tile points 16w .. 16w+15 for the ket; lane (g, t4) then owns
+// points 16w+g, 16w+g+8 and bands 2t4, 2t4+1, 8+2t4, 9+2t4 of the ket
+// result, and does the stencil and update for exactly those eight pairs.
 // ----------------------------------------------------------------------------
-__global__ void __launch_bounds__(TC_THREADS, 2) k_stage_tc(LaunchSet L, const float2* __restrict__ tin,
-                                                            float2* __restrict__ tout, float2* __restrict__ psi,
-                                                            const float2* __restrict__ Pin, float2* __restrict__ Pout,
-                                                            int m) {
+__global__ void __cluster_dims__(TC_CL, 1, 1) __launch_bounds__(TC_THREADS, 3)
+    k_stage_tc(LaunchSet L, const float2* __restrict__ tin, float2* __restrict__ tout, float2* __restrict__ psi,
+               const float2* __restrict__ Pin, float2* __restrict__ Pout, int m) {
   extern __shared__ __align__(16) unsigned char tc_raw[];
   TcSmem& sm = *reinterpret_cast<TcSmem*>(tc_raw);
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
   const CellDev& c = L.cell;
-  const int u = L.unit_ids[blockIdx.x];
+  const int u = L.unit_ids[blockIdx.x / TC_CL];
   const UnitDev U = L.units[u];
   const SubDev S = L.subs[U.sub];
-  const float2* ph = (const float2*)L.ph_half + (long long)u * L.ph_stride;
   const float* qt = reinterpret_cast<const float*>(L.qt_half) + 4 * u;
-  const float q0 = qt[0], q1 = qt[1], q2 = qt[2], q2h = qt[3];
+  const float q0 = qt[0], q1 = qt[1], q2 = qt[2];
   const float hdt = (float)S.dt / (float)m;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, t4 = lane & 3;
   const bool do_bra = m < 4;
+  const float* veff = reinterpret_cast<const float*>(S.veff);
+  const float diag0 = c.hlapf[0][0] + c.hlapf[1][0] + c.hlapf[2][0] + qt[3];
 
+  tc_load_tables(sm, c, (const float2*)L.ph_half + (long long)u * L.ph_stride);
   // Wt (ket operand) from W = E_j P_jb:
   //   Wt[b][j] = Wr, Wt[16+b][j] = Wi, Wt[b][32+j] = Wi, Wt[16+b][32+j] = -Wr
   for (int i = threadIdx.x; i < 32 * 16; i += TC_THREADS) {
@@ -249,8 +444,8 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_stage_tc(LaunchSet L, const f
       wi = e * p.y;
     }
     uint32_t hi, lo, nhi, nlo;
-    tc_split2(wr, wi, hi, lo);        // (Wr, Wi)
-    tc_split2(-wr, wi, nhi, nlo);     // (-Wr, Wi)
+    tc_split2(wr, wi, hi, lo);
+    tc_split2(-wr, wi, nhi, nlo);
     tc_st16(sm.w_hi + b * TC_W_PITCH + j, hi);
     tc_st16(sm.w_lo + b * TC_W_PITCH + j, lo);
     tc_st16(sm.w_hi + (16 + b) * TC_W_PITCH + j, hi >> 16);
@@ -260,32 +455,24 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_stage_tc(LaunchSet L, const f
     tc_st16(sm.w_hi + (16 + b) * TC_W_PITCH + 32 + j, nhi);
     tc_st16(sm.w_lo + (16 + b) * TC_W_PITCH + 32 + j, nlo);
   }
-  // per-thread stencil constants (packed float2 pairs)
-  float lw[3][TC_ND], gq[3][TC_ND];
-  const float qa[3] = {q0, q1, q2};
-#pragma unroll
-  for (int ax = 0; ax < 3; ++ax)
-#pragma unroll
-    for (int mm = 1; mm <= TC_ND; ++mm) {
-      lw[ax][mm - 1] = (float)(-0.5 * c.lapw[ax][mm]);
-      gq[ax][mm - 1] = qa[ax] * (float)c.gradw[ax][mm];
-    }
-  const float diag0 = (float)(-0.5 * (c.lapw[0][0] + c.lapw[1][0] + c.lapw[2][0])) + q2h;
   const int n12 = c.n1 * c.n2;
-  const int pt = threadIdx.x % TC_PT, bh = threadIdx.x / TC_PT;  // point, band half (8 bands)
   float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+  const int n_tiles = (c.npts + TC_PT - 1) / TC_PT;
+  const int tpc = (n_tiles + TC_CL - 1) / TC_CL;
+  const int t_begin = rank * tpc, t_end = min(n_tiles, t_begin + tpc);
 
-  for (int p0 = 0; p0 < c.npts; p0 += TC_PT) {
+  for (int tile = t_begin; tile < t_end; ++tile) {
+    const int p0 = tile * TC_PT;
     __syncthreads();
-    tc_gen_c(sm, c, ph, p0, 0);
+    tc_gen_c(sm, c, p0, 0);
     __syncthreads();
-    // ket: warp w -> points 16w..16w+15, all 32 n'
+    // ket: V for points 16w+g (+8) and all 32 n' in registers
+    float d[4][4];
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) d[nt][e] = 0.f;
     {
-      float d[4][4];
-#pragma unroll
-      for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) d[nt][e] = 0.f;
       const int row = 16 * warp + g;
 #pragma unroll
       for (int ks = 0; ks < 4; ++ks) {
@@ -309,18 +496,11 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_stage_tc(LaunchSet L, const f
           tc_mma(d[nt], ahi, bh0, bh1);
         }
       }
-#pragma unroll
-      for (int nt = 0; nt < 4; ++nt) {
-        const int n = 8 * nt + 2 * t4;
-        sm.vs[row * TC_V_PITCH + n] = d[nt][0];
-        sm.vs[row * TC_V_PITCH + n + 1] = d[nt][1];
-        sm.vs[(row + 8) * TC_V_PITCH + n] = d[nt][2];
-        sm.vs[(row + 8) * TC_V_PITCH + n + 1] = d[nt][3];
-      }
     }
-    __syncthreads();
-    // stencil + ket + Taylor update for (point pt, bands 8 bh .. 8 bh + 7)
-    {
+    // stencil + ket + Taylor update for this lane's 2 points x 4 bands
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int pt = 16 * warp + g + 8 * r;
       const int p = p0 + pt;
       const bool valid = p < c.npts;
       const int pp = valid ? p : 0;
@@ -335,37 +515,42 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_stage_tc(LaunchSet L, const f
         oz[2 * mm - 2] = (wrap_idx(iz + mm, c.n3) - iz) * n12;
         oz[2 * mm - 1] = (wrap_idx(iz - mm, c.n3) - iz) * n12;
       }
-      const float v = valid ? reinterpret_cast<const float*>(S.veff)[pp] : 0.f;
-      const float dg = diag0 + v;
-      for (int bl = 0; bl < 8; ++bl) {
-        const int b = 8 * bh + bl;
+      const float dg = diag0 + (valid ? veff[pp] : 0.f);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int b = 2 * t4 + (k & 1) + 8 * (k >> 1);
+        const float vre = d[k >> 1][2 * r + (k & 1)];
+        const float vim = d[2 + (k >> 1)][2 * r + (k & 1)];
         float tr = 0.f, ti = 0.f;
         if (valid && b < c.n_bands) {
           const long long base = U.psi_off + (long long)b * c.npts + pp;
           const float2* tb = tin + base;
           const float2 ce = tb[0];
-          float hx = dg * ce.x, hy = dg * ce.y, gx = 0.f, gy = 0.f;
+          float hx = dg * ce.x, hy = dg * ce.y;
+          float gxr = 0.f, gxi = 0.f, gyr = 0.f, gyi = 0.f, gzr = 0.f, gzi = 0.f;
 #pragma unroll
           for (int mm = 1; mm <= TC_ND; ++mm) {
             const float2 xu = tb[ox[2 * mm - 2]], xd = tb[ox[2 * mm - 1]];
             const float2 yu = tb[oy[2 * mm - 2]], yd = tb[oy[2 * mm - 1]];
             const float2 zu = tb[oz[2 * mm - 2]], zd = tb[oz[2 * mm - 1]];
-            hx = fmaf(lw[0][mm - 1], xu.x + xd.x, hx);
-            hy = fmaf(lw[0][mm - 1], xu.y + xd.y, hy);
-            hx = fmaf(lw[1][mm - 1], yu.x + yd.x, hx);
-            hy = fmaf(lw[1][mm - 1], yu.y + yd.y, hy);
-            hx = fmaf(lw[2][mm - 1], zu.x + zd.x, hx);
-            hy = fmaf(lw[2][mm - 1], zu.y + zd.y, hy);
-            gx = fmaf(gq[0][mm - 1], xu.x - xd.x, gx);
-            gy = fmaf(gq[0][mm - 1], xu.y - xd.y, gy);
-            gx = fmaf(gq[1][mm - 1], yu.x - yd.x, gx);
-            gy = fmaf(gq[1][mm - 1], yu.y - yd.y, gy);
-            gx = fmaf(gq[2][mm - 1], zu.x - zd.x, gx);
-            gy = fmaf(gq[2][mm - 1], zu.y - zd.y, gy);
+            hx = fmaf(c.hlapf[0][mm], xu.x + xd.x, hx);
+            hy = fmaf(c.hlapf[0][mm], xu.y + xd.y, hy);
+            hx = fmaf(c.hlapf[1][mm], yu.x + yd.x, hx);
+            hy = fmaf(c.hlapf[1][mm], yu.y + yd.y, hy);
+            hx = fmaf(c.hlapf[2][mm], zu.x + zd.x, hx);
+            hy = fmaf(c.hlapf[2][mm], zu.y + zd.y, hy);
+            gxr = fmaf(c.gradwf[0][mm], xu.x - xd.x, gxr);
+            gxi = fmaf(c.gradwf[0][mm], xu.y - xd.y, gxi);
+            gyr = fmaf(c.gradwf[1][mm], yu.x - yd.x, gyr);
+            gyi = fmaf(c.gradwf[1][mm], yu.y - yd.y, gyi);
+            gzr = fmaf(c.gradwf[2][mm], zu.x - zd.x, gzr);
+            gzi = fmaf(c.gradwf[2][mm], zu.y - zd.y, gzi);
           }
-          // -i q.grad t, ket
-          const float hr = hx + gy + sm.vs[pt * TC_V_PITCH + b];
-          const float hi = hy - gx + sm.vs[pt * TC_V_PITCH + 16 + b];
+          // q.grad t, then h += -i q.grad t + V_NL t
+          const float qgr = fmaf(q0, gxr, fmaf(q1, gyr, q2 * gzr));
+          const float qgi = fmaf(q0, gxi, fmaf(q1, gyi, q2 * gzi));
+          const float hr = hx + qgi + vre;
+          const float hi = hy - qgr + vim;
           tr = hdt * hi;
           ti = -hdt * hr;
           if (m < 4) tout[base] = make_float2(tr, ti);
@@ -378,12 +563,12 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_stage_tc(LaunchSet L, const f
           }
         }
         if (do_bra) {
-          uint32_t hi, lo;
-          tc_split2(tr, ti, hi, lo);
-          tc_st16(sm.ts_hi + b * TC_TS_PITCH + pt, hi);
-          tc_st16(sm.ts_lo + b * TC_TS_PITCH + pt, lo);
-          tc_st16(sm.ts_hi + (16 + b) * TC_TS_PITCH + pt, hi >> 16);
-          tc_st16(sm.ts_lo + (16 + b) * TC_TS_PITCH + pt, lo >> 16);
+          uint32_t hi2, lo2;
+          tc_split2(tr, ti, hi2, lo2);
+          tc_st16(sm.ts_hi + b * TC_TS_PITCH + pt, hi2);
+          tc_st16(sm.ts_lo + b * TC_TS_PITCH + pt, lo2);
+          tc_st16(sm.ts_hi + (16 + b) * TC_TS_PITCH + pt, hi2 >> 16);
+          tc_st16(sm.ts_lo + (16 + b) * TC_TS_PITCH + pt, lo2 >> 16);
         }
       }
     }
@@ -392,5 +577,11 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_stage_tc(LaunchSet L, const f
       tc_bra_tile(sm, acc);
     }
   }
-  if (do_bra) tc_bra_store(sm, acc, c, Pout + U.p_off, c.n_proj, 1, 0);
+  if (do_bra) {
+    __syncthreads();
+    tc_bra_partial(sm, acc, 0);
+    cluster.sync();
+    tc_bra_reduce(sm, c, Pout + U.p_off, c.n_proj, 1, 0, 0);
+    cluster.sync();   // peers stay resident until every CTA has read their partials
+  }
 }
