@@ -7,6 +7,8 @@ static bool tc_attr_set = false;
 
 static void tc_set_attributes() {
   if (tc_attr_set) return;
+  cudaFuncSetAttribute(k_bra_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TwSmem));
+  cudaFuncSetAttribute(k_ket_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TwSmem));
   cudaFuncSetAttribute(k_bra_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TcSmem));
   cudaFuncSetAttribute(k_stage_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TcSmem));
   cudaFuncSetAttribute(k_ket_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TcSmem));
@@ -16,9 +18,8 @@ static void tc_set_attributes() {
 void launch_bra_tc(const LaunchSet& L, const void* psi, void* out, int with_d, void* stream) {
   if (L.n_units == 0 || !L.cell.use_proj) return;
   tc_set_attributes();
-  // one cluster of TC_CL CTAs per unit (all four current weightings in one pass when with_d)
-  k_bra_tc<<<L.n_units * TC_CL, TC_THREADS, sizeof(TcSmem), (cudaStream_t)stream>>>(L, (const float2*)psi,
-                                                                                      (float2*)out, with_d);
+  // one CTA per unit (all four current weightings in one pass when with_d)
+  k_bra_w<<<L.n_units, 256, sizeof(TwSmem), (cudaStream_t)stream>>>(L, (const float2*)psi, (float2*)out, with_d);
 }
 
 void launch_stage_tc(const LaunchSet& L, const void* tin, void* tout, void* psi, void* P, int m, void* stream) {
@@ -31,9 +32,9 @@ void launch_stage_tc(const LaunchSet& L, const void* tin, void* tout, void* psi,
 void launch_ket_tc(const LaunchSet& L, const void* P, void* V, void* stream) {
   if (L.n_units == 0) return;
   tc_set_attributes();
-  const int n_tiles = (L.cell.npts + TC_PT - 1) / TC_PT;
-  dim3 grid((n_tiles + TC_KET_TILES - 1) / TC_KET_TILES, L.n_units);
-  k_ket_tc<<<grid, TC_THREADS, sizeof(TcSmem), (cudaStream_t)stream>>>(L, (const float2*)P, (float2*)V);
+  const int n_steps = (L.cell.npts + TW_PTS - 1) / TW_PTS;
+  dim3 grid((n_steps + 8 * TW_KET_STEPS - 1) / (8 * TW_KET_STEPS), L.n_units);
+  k_ket_w<<<grid, 256, sizeof(TwSmem), (cudaStream_t)stream>>>(L, (const float2*)P, (float2*)V);
 }
 
 void launch_stage_v(const LaunchSet& L, const void* tin, void* tout, void* psi, const void* V, int m, void* stream) {

@@ -585,3 +585,316 @@ __global__ void __cluster_dims__(TC_CL, 1, 1) __launch_bounds__(TC_THREADS, 3)
     cluster.sync();   // peers stay resident until every CTA has read their partials
   }
 }
+
+// ============================================================================
+// Warp-independent forms of the bra and the ket.  Each warp owns 16-point
+// slices: it generates its own projector rows and orbital values into a
+// private shared-memory tile and runs its products with warp-level
+// synchronisation only; CTA barriers occur once, in the final reduction.
+// ============================================================================
+#define TW_PTS 16          // points per warp step
+#define TW_CPITCH 72       // bf16 per projector row (64 + 8)
+#define TW_TPITCH 24       // bf16 per orbital row (16 + 8)
+
+struct TwTile {
+  __nv_bfloat16 c_hi[TW_PTS * TW_CPITCH];
+  __nv_bfloat16 c_lo[TW_PTS * TW_CPITCH];
+  __nv_bfloat16 t_hi[32 * TW_TPITCH];
+  __nv_bfloat16 t_lo[32 * TW_TPITCH];
+};
+
+struct TwSmem {
+  TwTile w[8];
+  float2 fac[TC_NA * 3 * TC_NMAX];
+  float dis[TC_NA * 3 * TC_NMAX];
+  float pn[TC_NA * 4];
+  __nv_bfloat16 wk_hi[32 * TC_W_PITCH];
+  __nv_bfloat16 wk_lo[32 * TC_W_PITCH];
+};
+
+__device__ __forceinline__ void tw_load_tables(TwSmem& sm, const CellDev& c, const float2* ph) {
+  const int nm = c.nmax;
+  const int n = c.n_atoms * 3 * nm;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int a = i / (3 * nm), r = i % (3 * nm);
+    const int ax = r / nm, ii = r % nm;
+    const float g = c.g1f[i];
+    const float2 p = ph[i];
+    sm.fac[(a * 3 + ax) * TC_NMAX + ii] = make_float2(g * p.x, g * p.y);
+    sm.dis[(a * 3 + ax) * TC_NMAX + ii] = c.d1f[i];
+  }
+  for (int i = threadIdx.x; i < 4 * c.n_atoms; i += blockDim.x) sm.pn[i] = c.pnormf[i];
+}
+
+// projector rows of 16 points (p0 .. p0+15) into the warp's tile
+__device__ __forceinline__ void tw_gen_c(TwTile& wt, const TwSmem& sm, const CellDev& c, int p0, int alpha,
+                                         int lane) {
+  // lane -> point pt = lane % 16 and atoms lane / 16 + 2k
+  const int pt = lane & (TW_PTS - 1);
+  const int p = p0 + pt;
+  const bool pv = p < c.npts;
+  const int pp = pv ? p : 0;
+  const int n12 = c.n1 * c.n2;
+  const int iz = pp / n12, rem = pp - iz * n12;
+  const int iy = rem / c.n1, ix = rem - iy * c.n1;
+#pragma unroll
+  for (int k = 0; k < (TW_PTS * TC_NA) / 32; ++k) {
+    const int a = (lane >> 4) + 2 * k;
+    float cr[4] = {0.f, 0.f, 0.f, 0.f}, ci[4] = {0.f, 0.f, 0.f, 0.f};
+    if (pv && a < c.n_atoms) {
+      const float2* fa = sm.fac + a * 3 * TC_NMAX;
+      const float* da = sm.dis + a * 3 * TC_NMAX;
+      const float2 fx = fa[ix], fy = fa[TC_NMAX + iy], fz = fa[2 * TC_NMAX + iz];
+      const float d[3] = {da[ix], da[TC_NMAX + iy], da[2 * TC_NMAX + iz]};
+      const float2 fxy = make_float2(fx.x * fy.x - fx.y * fy.y, fx.x * fy.y + fx.y * fy.x);
+      float fr = fxy.x * fz.x - fxy.y * fz.y, fi = fxy.x * fz.y + fxy.y * fz.x;
+      if (alpha > 0) {
+        fr *= d[alpha - 1];
+        fi *= d[alpha - 1];
+      }
+      const float* pn = sm.pn + 4 * a;
+      const float w[4] = {pn[0], pn[1] * d[0], pn[2] * d[1], pn[3] * d[2]};
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        cr[t] = fr * w[t];
+        ci[t] = fi * w[t];
+      }
+    }
+    uint2 hr, lr, hc, lc;
+    tc_split2(cr[0], cr[1], hr.x, lr.x);
+    tc_split2(cr[2], cr[3], hr.y, lr.y);
+    tc_split2(ci[0], ci[1], hc.x, lc.x);
+    tc_split2(ci[2], ci[3], hc.y, lc.y);
+    *reinterpret_cast<uint2*>(wt.c_hi + pt * TW_CPITCH + 4 * a) = hr;
+    *reinterpret_cast<uint2*>(wt.c_lo + pt * TW_CPITCH + 4 * a) = lr;
+    *reinterpret_cast<uint2*>(wt.c_hi + pt * TW_CPITCH + 32 + 4 * a) = hc;
+    *reinterpret_cast<uint2*>(wt.c_lo + pt * TW_CPITCH + 32 + 4 * a) = lc;
+  }
+}
+
+// 8 orbital values per lane of a 16-point step: v[k] = t_b(p0 + pt), i = lane + 32k, pt = i % 16, b = i / 16
+__device__ __forceinline__ void tw_fetch(float2 (&v)[8], const float2* src, const CellDev& c, int p0, int lane) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int i = lane + 32 * k;
+    const int pt = i % TW_PTS, b = i / TW_PTS;
+    const int p = p0 + pt;
+    v[k] = (p < c.npts && b < c.n_bands) ? src[(long long)b * c.npts + p] : make_float2(0.f, 0.f);
+  }
+}
+
+__device__ __forceinline__ void tw_store_t(TwTile& wt, const float2 (&v)[8], int lane) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int i = lane + 32 * k;
+    const int pt = i % TW_PTS, b = i / TW_PTS;
+    uint32_t hi, lo;
+    tc_split2(v[k].x, v[k].y, hi, lo);
+    tc_st16(wt.t_hi + b * TW_TPITCH + pt, hi);
+    tc_st16(wt.t_lo + b * TW_TPITCH + pt, lo);
+    tc_st16(wt.t_hi + (16 + b) * TW_TPITCH + pt, hi >> 16);
+    tc_st16(wt.t_lo + (16 + b) * TW_TPITCH + pt, lo >> 16);
+  }
+}
+
+// acc[mt][nt] += C^T T over the 16 points of the warp's tile
+__device__ __forceinline__ void tw_bra_step(const TwTile& wt, float (&acc)[4][4][4], int lane) {
+  const int g = lane >> 2, t = lane & 3;
+  const int q = lane >> 3, r = lane & 7;
+  uint32_t bh[4][2], bl[4][2];
+#pragma unroll
+  for (int nt = 0; nt < 4; ++nt) {
+    const __nv_bfloat16* ph = wt.t_hi + (8 * nt + g) * TW_TPITCH + 2 * t;
+    const __nv_bfloat16* pl = wt.t_lo + (8 * nt + g) * TW_TPITCH + 2 * t;
+    bh[nt][0] = tc_ld32(ph);
+    bh[nt][1] = tc_ld32(ph + 8);
+    bl[nt][0] = tc_ld32(pl);
+    bl[nt][1] = tc_ld32(pl + 8);
+  }
+  const int prow = ((q >> 1) << 3) + r;
+#pragma unroll
+  for (int mt = 0; mt < 4; ++mt) {
+    const int jcol = 16 * mt + ((q & 1) << 3);
+    uint32_t ahi[4], alo[4];
+    tc_ldsm_x4_trans(ahi, wt.c_hi + prow * TW_CPITCH + jcol);
+    tc_ldsm_x4_trans(alo, wt.c_lo + prow * TW_CPITCH + jcol);
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+      tc_mma(acc[mt][nt], alo, bh[nt][0], bh[nt][1]);
+      tc_mma(acc[mt][nt], ahi, bl[nt][0], bl[nt][1]);
+      tc_mma(acc[mt][nt], ahi, bh[nt][0], bh[nt][1]);
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Bra of orbitals on tensor cores, one 8-CTA cluster per unit, warp-independent
+// main loop.  with_d = 0: P[u][b][j] (q_half tables), every warp one slice
+// sequence; with_d = 1: Pa[u][b][j][alpha] (q_obs tables), warp w takes
+// weighting alpha = w % 4 and every other slice.
+// ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(256, 2) k_bra_w(LaunchSet L, const float2* __restrict__ src,
+                                                  float2* __restrict__ out, int with_d) {
+  extern __shared__ __align__(16) unsigned char tw_raw[];
+  TwSmem& sm = *reinterpret_cast<TwSmem*>(tw_raw);
+  const CellDev& c = L.cell;
+  const int u = L.unit_ids[blockIdx.x];
+  const UnitDev U = L.units[u];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const float2* ph = (const float2*)(with_d ? L.ph_obs : L.ph_half) + (long long)u * L.ph_stride;
+  tw_load_tables(sm, c, ph);
+  __syncthreads();
+  const int n_steps_all = (c.npts + TW_PTS - 1) / TW_PTS;
+  const int alpha = with_d ? (warp & 3) : 0;
+  const int s_first = with_d ? (warp >> 2) : warp;
+  const int s_stride = with_d ? 2 : 8;
+  TwTile& wt = sm.w[warp];
+  const float2* s0 = src + U.psi_off;
+  float acc[4][4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[a][b][e] = 0.f;
+  float2 v[8];
+  if (s_first < n_steps_all) tw_fetch(v, s0, c, s_first * TW_PTS, lane);
+  for (int s = s_first; s < n_steps_all; s += s_stride) {
+    const int p0 = s * TW_PTS;
+    __syncwarp();
+    tw_store_t(wt, v, lane);
+    if (s + s_stride < n_steps_all) tw_fetch(v, s0, c, (s + s_stride) * TW_PTS, lane);
+    tw_gen_c(wt, sm, c, p0, alpha, lane);
+    __syncwarp();
+    tw_bra_step(wt, acc, lane);
+  }
+  // reduce the warps in a fixed order into D[slot][64][33] (tile area)
+  float* D = reinterpret_cast<float*>(sm.w);
+  const int slot = with_d ? (warp & 3) : 0;
+  const int order = with_d ? (warp >> 2) : warp;
+  const int n_order = with_d ? 2 : 8;
+  const int g = lane >> 2, t = lane & 3;
+  for (int pass = 0; pass < n_order; ++pass) {
+    __syncthreads();
+    if (order == pass) {
+      float* Ds = D + slot * 64 * TC_D_PITCH;
+#pragma unroll
+      for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int row = 16 * mt + g + ((e >> 1) << 3);
+            const int col = 8 * nt + 2 * t + (e & 1);
+            float* dst = Ds + row * TC_D_PITCH + col;
+            *dst = (pass == 0) ? acc[mt][nt][e] : *dst + acc[mt][nt][e];
+          }
+    }
+  }
+  __syncthreads();
+  const int n_slots = with_d ? 4 : 1;
+  const float dv = (float)c.dv;
+  for (int i = threadIdx.x; i < n_slots * 32 * 16; i += blockDim.x) {
+    const int sl = i / 512, o = i % 512;
+    const int j = o % 32, b = o / 32;
+    if (j < c.n_proj && b < c.n_bands) {
+      const float* Dl = D + sl * 64 * TC_D_PITCH;
+      const float pr = Dl[j * TC_D_PITCH + b] - Dl[(32 + j) * TC_D_PITCH + 16 + b];
+      const float pi = Dl[j * TC_D_PITCH + 16 + b] + Dl[(32 + j) * TC_D_PITCH + b];
+      const float2 val = make_float2(dv * pr, dv * pi);
+      if (with_d)
+        out[U.pa_off + (long long)b * 4 * c.n_proj + 4 * j + sl] = val;
+      else
+        out[U.p_off + (long long)b * c.n_proj + j] = val;
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Ket on tensor cores, warp-independent: V[u][b][r] = sum_j beta~_j(r) E_j P_jb.
+// grid (chunks of 8 x TW_KET_STEPS slices, units); warp w takes slices
+// w, w + 8, ... of the chunk and writes V from its MMA registers.
+// ----------------------------------------------------------------------------
+#define TW_KET_STEPS 4
+__global__ void __launch_bounds__(256, 2) k_ket_w(LaunchSet L, const float2* __restrict__ P,
+                                                  float2* __restrict__ V) {
+  extern __shared__ __align__(16) unsigned char tw_raw[];
+  TwSmem& sm = *reinterpret_cast<TwSmem*>(tw_raw);
+  const CellDev& c = L.cell;
+  const int u = L.unit_ids[blockIdx.y];
+  const UnitDev U = L.units[u];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, t4 = lane & 3;
+  tw_load_tables(sm, c, (const float2*)L.ph_half + (long long)u * L.ph_stride);
+  for (int i = threadIdx.x; i < 32 * 16; i += blockDim.x) {
+    const int j = i % 32, b = i / 32;
+    float wr = 0.f, wi = 0.f;
+    if (j < c.n_proj && b < c.n_bands) {
+      const float2 p = P[U.p_off + (long long)b * c.n_proj + j];
+      const float e = (float)c.ekb[j];
+      wr = e * p.x;
+      wi = e * p.y;
+    }
+    uint32_t hi, lo, nhi, nlo;
+    tc_split2(wr, wi, hi, lo);
+    tc_split2(-wr, wi, nhi, nlo);
+    tc_st16(sm.wk_hi + b * TC_W_PITCH + j, hi);
+    tc_st16(sm.wk_lo + b * TC_W_PITCH + j, lo);
+    tc_st16(sm.wk_hi + (16 + b) * TC_W_PITCH + j, hi >> 16);
+    tc_st16(sm.wk_lo + (16 + b) * TC_W_PITCH + j, lo >> 16);
+    tc_st16(sm.wk_hi + b * TC_W_PITCH + 32 + j, nhi >> 16);
+    tc_st16(sm.wk_lo + b * TC_W_PITCH + 32 + j, nlo >> 16);
+    tc_st16(sm.wk_hi + (16 + b) * TC_W_PITCH + 32 + j, nhi);
+    tc_st16(sm.wk_lo + (16 + b) * TC_W_PITCH + 32 + j, nlo);
+  }
+  __syncthreads();
+  TwTile& wt = sm.w[warp];
+  const int n_steps_all = (c.npts + TW_PTS - 1) / TW_PTS;
+  const int s_begin = blockIdx.x * 8 * TW_KET_STEPS;
+  const int s_end = min(n_steps_all, s_begin + 8 * TW_KET_STEPS);
+  for (int s = s_begin + warp; s < s_end; s += 8) {
+    const int p0 = s * TW_PTS;
+    __syncwarp();
+    tw_gen_c(wt, sm, c, p0, 0, lane);
+    __syncwarp();
+    float d[4][4];
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) d[nt][e] = 0.f;
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) {
+      const int col = 16 * ks + 2 * t4;
+      uint32_t ahi[4], alo[4];
+      ahi[0] = tc_ld32(wt.c_hi + g * TW_CPITCH + col);
+      ahi[1] = tc_ld32(wt.c_hi + (g + 8) * TW_CPITCH + col);
+      ahi[2] = tc_ld32(wt.c_hi + g * TW_CPITCH + col + 8);
+      ahi[3] = tc_ld32(wt.c_hi + (g + 8) * TW_CPITCH + col + 8);
+      alo[0] = tc_ld32(wt.c_lo + g * TW_CPITCH + col);
+      alo[1] = tc_ld32(wt.c_lo + (g + 8) * TW_CPITCH + col);
+      alo[2] = tc_ld32(wt.c_lo + g * TW_CPITCH + col + 8);
+      alo[3] = tc_ld32(wt.c_lo + (g + 8) * TW_CPITCH + col + 8);
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        const int n = 8 * nt + g;
+        const uint32_t bh0 = tc_ld32(sm.wk_hi + n * TC_W_PITCH + col), bh1 = tc_ld32(sm.wk_hi + n * TC_W_PITCH + col + 8);
+        const uint32_t bl0 = tc_ld32(sm.wk_lo + n * TC_W_PITCH + col), bl1 = tc_ld32(sm.wk_lo + n * TC_W_PITCH + col + 8);
+        tc_mma(d[nt], alo, bh0, bh1);
+        tc_mma(d[nt], ahi, bl0, bl1);
+        tc_mma(d[nt], ahi, bh0, bh1);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int p = p0 + g + 8 * r;
+      if (p >= c.npts) continue;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int b = 2 * t4 + (k & 1) + 8 * (k >> 1);
+        if (b < c.n_bands)
+          V[U.psi_off + (long long)b * c.npts + p] =
+              make_float2(d[k >> 1][2 * r + (k & 1)], d[2 + (k >> 1)][2 * r + (k & 1)]);
+      }
+    }
+  }
+}
