@@ -596,6 +596,8 @@ int tsbz_init_cell(tsbz_ctx* ctx, const tsbz_cell_desc* d, int* cell_id) {
       c.gradw[ax][m] = dw[m] / h;
       c.hlapf[ax][m] = (float)(-0.5 * cw[m] / (h * h));
       c.gradwf[ax][m] = (float)(dw[m] / h);
+      c.hlap2[ax][m] = make_float2(c.hlapf[ax][m], c.hlapf[ax][m]);
+      c.gradw2[ax][m] = make_float2(c.gradwf[ax][m], c.gradwf[ax][m]);
     }
     c.gsq_scale[ax] = 2.0 * 3.14159265358979323846 / d->a[ax];
   }

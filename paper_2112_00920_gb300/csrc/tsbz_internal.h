@@ -30,6 +30,8 @@ struct CellDev {
   double gradw[3][TSBZ_MAX_ND + 1];  // d_m / h_ax   (m = 1..nd)
   float hlapf[3][TSBZ_MAX_ND + 1];   // -1/2 c_m / h_ax^2 in float
   float gradwf[3][TSBZ_MAX_ND + 1];  // d_m / h_ax in float
+  float2 hlap2[3][TSBZ_MAX_ND + 1];  // (w, w) pairs of hlapf for packed FP32x2 arithmetic
+  float2 gradw2[3][TSBZ_MAX_ND + 1]; // (w, w) pairs of gradwf
   double gsq_scale[3];               // (2 pi / a_ax)
   const double* g1;     // [n_atoms][3][nmax] Gaussian factor exp(-d^2/(2 rc^2)), 0 outside the box
   const double* d1;     // [n_atoms][3][nmax] minimum-image displacement, 0 outside the box

@@ -467,17 +467,26 @@ __global__ void __launch_bounds__(256, 4) k_stage_z(LaunchSet L, const typename 
     const int zz = wrap_idx(k - ND, n3);
     qv[k] = act ? tb[(long long)zz * n12] : zero;
   }
+  // values of the current plane loaded one step ahead: V, psi (m >= 2), v_eff
+  VT v_cur = act ? V[base0] : zero;
+  VT p_cur = (act && m >= 2) ? psi[base0] : zero;
+  T e_cur = act ? veff[col] : (T)0;
   for (int z = 0; z < n3; ++z) {
-    // prefetch t(z + ND + 1)
+    // prefetch t(z + ND + 1) and V, psi, v_eff of plane z + 1
     const int zn = wrap_idx(wrap_idx(z + ND + 1, n3), n3);
     const VT nxt = act ? tb[(long long)zn * n12] : zero;
+    const bool more = act && z + 1 < n3;
+    const long long idx_n = base0 + (long long)(z + 1) * n12;
+    const VT v_nxt = more ? V[idx_n] : zero;
+    const VT p_nxt = (more && m >= 2) ? psi[idx_n] : zero;
+    const T e_nxt = more ? veff[(z + 1) * n12 + col] : (T)0;
     __syncthreads();
     if (act) plane[col] = qv[ND];
     __syncthreads();
     if (act) {
       const VT ce = qv[ND];
       const long long idx = base0 + (long long)z * n12;
-      const T dg = dg0 + veff[z * n12 + col];
+      const T dg = dg0 + e_cur;
       T hx = dg * ce.x, hy = dg * ce.y;
       T gxr = 0, gxi = 0, gyr = 0, gyi = 0, gzr = 0, gzi = 0;
 #pragma unroll
@@ -498,23 +507,25 @@ __global__ void __launch_bounds__(256, 4) k_stage_z(LaunchSet L, const typename 
         gzr = fma((T)c.gradwf[2][mm], zu.x - zd.x, gzr);
         gzi = fma((T)c.gradwf[2][mm], zu.y - zd.y, gzi);
       }
-      const VT v = V[idx];
       const T qgr = fma(q0, gxr, fma(q1, gyr, q2 * gzr));
       const T qgi = fma(q0, gxi, fma(q1, gyi, q2 * gzi));
-      const T hr = hx + qgi + v.x;
-      const T hi = hy - qgr + v.y;
+      const T hr = hx + qgi + v_cur.x;
+      const T hi = hy - qgr + v_cur.y;
       const VT t = cmk<VT>(hdt * hi, -hdt * hr);
       if (m < 4) tout[idx] = t;
       if (m == 2) {
-        psi[idx] = cadd(psi[idx], cadd(ce, t));
+        psi[idx] = cadd(p_cur, cadd(ce, t));
       } else if (m >= 3) {
-        psi[idx] = cadd(psi[idx], t);
+        psi[idx] = cadd(p_cur, t);
       }
     }
     // advance the queue
 #pragma unroll
     for (int k = 0; k < 2 * ND; ++k) qv[k] = qv[k + 1];
     qv[2 * ND] = nxt;
+    v_cur = v_nxt;
+    p_cur = p_nxt;
+    e_cur = e_nxt;
   }
 }
 

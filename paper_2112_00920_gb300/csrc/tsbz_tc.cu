@@ -40,6 +40,14 @@ void launch_ket_tc(const LaunchSet& L, const void* P, void* V, void* stream) {
 void launch_stage_v(const LaunchSet& L, const void* tin, void* tout, void* psi, const void* V, int m, void* stream) {
   if (L.n_units == 0) return;
   const int n12 = L.cell.n1 * L.cell.n2;
+  if (n12 <= 256 && L.cell.n3 == 16) {
+    // 2.5-D z-march, depth 16 unrolled, packed arithmetic
+    const int threads = ((n12 + 31) / 32) * 32;
+    dim3 grid(L.cell.n_bands, L.n_units);
+    k_stage_zf<16><<<grid, threads, n12 * sizeof(float2), (cudaStream_t)stream>>>(
+        L, (const float2*)tin, (float2*)tout, (float2*)psi, (const float2*)V, m);
+    return;
+  }
   if (n12 <= 256) {
     // 2.5-D z-march: one CTA per (band, unit), one thread per (x, y) column
     const int threads = ((n12 + 31) / 32) * 32;

@@ -898,3 +898,97 @@ __global__ void __launch_bounds__(256, 2) k_ket_w(LaunchSet L, const float2* __r
     }
   }
 }
+
+// ----------------------------------------------------------------------------
+// Taylor stage m, 2.5-D z-march for float orbitals with a compile-time grid
+// depth NZ (the z loop is fully unrolled, so the register queue of the 2 ND + 1
+// column values rotates by renaming) and packed FP32x2 complex arithmetic.
+// One CTA per (band, unit), one thread per (x, y) column (n1 n2 <= 256).
+//   t_m = (-i dt/m)[h_loc t + V], psi accumulation as in k_stage.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+template <int NZ>
+__global__ void __launch_bounds__(256, 4) k_stage_zf(LaunchSet L, const float2* __restrict__ tin,
+                                                     float2* __restrict__ tout, float2* __restrict__ psi,
+                                                     const float2* __restrict__ V, int m) {
+  constexpr int ND = TC_ND;
+  extern __shared__ __align__(16) unsigned char zraw[];
+  float2* plane = reinterpret_cast<float2*>(zraw);
+  const CellDev& c = L.cell;
+  const int b = blockIdx.x;
+  const int u = L.unit_ids[blockIdx.y];
+  const UnitDev U = L.units[u];
+  const SubDev S = L.subs[U.sub];
+  const int n1 = c.n1, n2 = c.n2, n12 = n1 * n2;
+  const int col = threadIdx.x;
+  const bool act = col < n12;
+  const int ix = act ? col % n1 : 0, iy = act ? col / n1 : 0;
+  const int rowb = iy * n1;
+  const float* qt = reinterpret_cast<const float*>(L.qt_half) + 4 * u;
+  const float q0 = qt[0], q1 = qt[1], q2 = qt[2];
+  const float dg0 = c.hlapf[0][0] + c.hlapf[1][0] + c.hlapf[2][0] + qt[3];
+  const float hdt = (float)S.dt / (float)m;
+  const float* veff = reinterpret_cast<const float*>(S.veff);
+  const long long base0 = U.psi_off + (long long)b * c.npts + col;
+  const float2* tb = tin + base0;
+  const float2 zero = make_float2(0.f, 0.f);
+  const float2 neg1 = make_float2(-1.f, -1.f);
+  float2 qv[NZ + 2 * ND];   // t(z) for z = -ND .. NZ - 1 + ND (periodic)
+#pragma unroll
+  for (int k = 0; k < 2 * ND; ++k) qv[k] = act ? tb[(long long)((k - ND + NZ) % NZ) * n12] : zero;
+  float2 v_cur = act ? V[base0] : zero;
+  float2 p_cur = (act && m >= 2) ? psi[base0] : zero;
+  float e_cur = act ? veff[col] : 0.f;
+#pragma unroll
+  for (int z = 0; z < NZ; ++z) {
+    // t(z + ND) enters the queue (periodic), V, psi, v_eff of plane z + 1 prefetched
+    qv[z + 2 * ND] = act ? tb[(long long)((z + ND) % NZ) * n12] : zero;
+    float2 v_nxt = zero, p_nxt = zero;
+    float e_nxt = 0.f;
+    if (act && z + 1 < NZ) {
+      const long long idx_n = base0 + (long long)(z + 1) * n12;
+      v_nxt = V[idx_n];
+      if (m >= 2) p_nxt = psi[idx_n];
+      e_nxt = veff[(z + 1) * n12 + col];
+    }
+    __syncthreads();
+    if (act) plane[col] = qv[z + ND];
+    __syncthreads();
+    if (act) {
+      const float2 ce = qv[z + ND];
+      const long long idx = base0 + (long long)z * n12;
+      const float dg = dg0 + e_cur;
+      float2 h = __fmul2_rn(make_float2(dg, dg), ce);
+      float2 gx = zero, gy = zero, gz = zero;
+#pragma unroll
+      for (int mm = 1; mm <= ND; ++mm) {
+        const float2 xu = plane[rowb + wrap_idx(ix + mm, n1)], xd = plane[rowb + wrap_idx(ix - mm, n1)];
+        const float2 yu = plane[wrap_idx(iy + mm, n2) * n1 + ix], yd = plane[wrap_idx(iy - mm, n2) * n1 + ix];
+        const float2 zu = qv[z + ND + mm], zd = qv[z + ND - mm];
+        h = f2fma(c.hlap2[0][mm], __fadd2_rn(xu, xd), h);
+        h = f2fma(c.hlap2[1][mm], __fadd2_rn(yu, yd), h);
+        h = f2fma(c.hlap2[2][mm], __fadd2_rn(zu, zd), h);
+        gx = f2fma(c.gradw2[0][mm], f2fma(neg1, xd, xu), gx);
+        gy = f2fma(c.gradw2[1][mm], f2fma(neg1, yd, yu), gy);
+        gz = f2fma(c.gradw2[2][mm], f2fma(neg1, zd, zu), gz);
+      }
+      // q.grad t = q0 gx + q1 gy + q2 gz;  h += -i q.grad t + V
+      float2 qg = __fmul2_rn(make_float2(q0, q0), gx);
+      qg = f2fma(make_float2(q1, q1), gy, qg);
+      qg = f2fma(make_float2(q2, q2), gz, qg);
+      const float hr = h.x + qg.y + v_cur.x;
+      const float hi = h.y - qg.x + v_cur.y;
+      const float2 t = make_float2(hdt * hi, -hdt * hr);
+      if (m < 4) tout[idx] = t;
+      if (m == 2) {
+        psi[idx] = __fadd2_rn(p_cur, __fadd2_rn(ce, t));
+      } else if (m >= 3) {
+        psi[idx] = __fadd2_rn(p_cur, t);
+      }
+    }
+    v_cur = v_nxt;
+    p_cur = p_nxt;
+    e_cur = e_nxt;
+  }
+}
