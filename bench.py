@@ -158,6 +158,58 @@ def build_propagator(precision, n_steps_cap, device=0, n_subsims=64):
     return P, sids, run
 
 
+# DRAM traffic of the stage kernel from an ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum), per launch averaged over m = 1..4, measured on the
+# reduced workload (8 of the 64 subgrids, 8192 orbitals) and scaled by the
+# orbital count to the full workload.  Valid only for the kernel source it
+# was taken on: the SHA-1 of the kernel text is checked at run time.
+STAGE_TRAFFIC = {"kernel": "k_stage_zf", "sha1": None, "bytes_per_launch_full": None,
+                 "profile": "profiles/k_stage_zf_fp32tc_reduced8.md"}
+
+
+def _kernel_sha1(path: str, name: str) -> str | None:
+    import hashlib
+    try:
+        src = open(path).read()
+    except OSError:
+        return None
+    i = src.find(f" {name}(")
+    if i < 0:
+        return None
+    j = src.find("\n}\n", i)
+    return hashlib.sha1(src[i:j].encode()).hexdigest()
+
+
+def eps_check(precision, device):
+    """Relative eps(omega) error of `precision` against the FP64 GPU path on a
+    small linear-response run (see the call site)."""
+    import workloads as W
+    from paper_2112_00920_gb300 import Propagator, shifted_kpoints
+    cell = W.cell_a_coarse(n=8)
+    n, dt, k0 = 600, 0.08, 0.005
+    k = shifted_kpoints(cell.a, (2, 2, 2), (0.0, 0.0, 0.0))
+    psi = W.plane_wave_orbitals(cell.a, cell.n, W.plane_wave_set(cell.n_bands), 8)
+    om = np.linspace(0.1, 20.0, 400) / 27.211386245988
+    t = np.arange(n + 1) * dt
+    win = 1.0 - 3.0 * (t / t[-1]) ** 2 + 2.0 * (t / t[-1]) ** 3
+    wts = np.ones(n + 1)
+    wts[0] = wts[-1] = 0.5
+    out = {}
+    for prec in ("fp64", precision):
+        P = Propagator(prec, device=device)
+        cid = P.add_cell_spec(cell)
+        sid = P.add_subsim(cid, k, dt, n)
+        P.load_ground_state(sid, psi)
+        P.set_kick(sid, k0, (1.0, 0.0, 0.0))
+        P.propagate(n)
+        J, j0 = P.current(sid)
+        P.close()
+        dj = (J - j0[None, :])[:, 0]
+        sig = dt * np.exp(1j * np.outer(om, t)) @ (wts * win * dj) / k0
+        out[prec] = 1.0 + 4.0j * np.pi * sig / om
+    return float(np.max(np.abs(out[precision] - out["fp64"])) / np.max(np.abs(out["fp64"])))
+
+
 def stage_bytes_per_launch(elem: int, n_orb: int, npts: int) -> float:
     """Algorithmic DRAM bytes of the Taylor stage kernel, averaged over its
     four launches per step: m=1 reads t0 and writes t1 (2 arrays), m=2 and
@@ -208,7 +260,7 @@ def main():
     from paper_2112_00920_gb300 import build_library
     build_library()
 
-    cap = args.warmup + args.steps
+    cap = args.warmup + 2 * args.steps + 1
     P, sids, run = build_propagator(args.precision, cap, device=local_rank, n_subsims=args.subsims)
     cell = run.subsims[0].cell
     n_orb = run.n_orbitals
@@ -257,12 +309,30 @@ def main():
     stage_ms = fam["stage"] / n_stage
     bytes_launch = stage_bytes_per_launch(elem, n_orb, cell.n_pts)
     achieved = bytes_launch / (stage_ms / 1e3) / 1e9
-    kname = ("k_stage_tc (stencil + tensor-core ket + Taylor accumulate + tensor-core bra of t_m)"
+    kname = ("k_stage_zf (2.5-D stencil + non-local term + Taylor accumulate)"
              if args.precision == "fp32_tc" else "k_stage (stencil + ket + Taylor accumulate)")
+    traffic = None
+    if args.precision == "fp32_tc" and args.subsims == 64 and STAGE_TRAFFIC["sha1"]:
+        sha = _kernel_sha1(os.path.join(ROOT, "paper_2112_00920_gb300", "csrc", "tsbz_tc.cuh"), "k_stage_zf")
+        if sha == STAGE_TRAFFIC["sha1"]:
+            traffic = STAGE_TRAFFIC["bytes_per_launch_full"]
     roof = {"kernel": kname, "bound": "hbm", "achieved": achieved,
-            "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+            "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
+            "algorithmic_bytes_per_launch": bytes_launch,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)" if peaks else "fallback 6.8 TB/s",
             "family_ms_per_step": {k: v / args.steps for k, v in fam.items()}}
+
+    # the same steps replayed from the captured CUDA graph (no per-kernel events)
+    P.set_graphs(True)
+    P.propagate(1)
+    torch.cuda.synchronize()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n_graph = max(1, min(args.steps, cap - args.warmup - args.steps - 1))
+    g0.record(stream)
+    P.propagate(n_graph)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    graph_value = n_orb * n_graph * world / (g0.elapsed_time(g1) / 1e3)
 
     # end-to-end through the C ABI with host buffers
     P.close()
@@ -282,6 +352,13 @@ def main():
            "d2h_bytes_per_step": int(J_e2e.nbytes / max(args.steps, 1)),
            "includes": "context set-up, 64 ground-state uploads (complex128 host), kick, propagation, "
                        "two-step current download"}
+
+    # eps(omega) error of this path against the FP64 GPU path (itself pinned to
+    # the oracle at err_J <= 1e-10): cell A on an 8^3 grid, MP 2^3, plane-wave
+    # start, kick 0.005 x, 600 steps, eps over 0.1-20 eV (Eqs. 12-14)
+    eps_err = None
+    if args.precision != "fp64":
+        eps_err = eps_check(args.precision, local_rank)
 
     # plain FP64 GPU path on the same workload (comparison)
     fp64 = None
@@ -317,8 +394,12 @@ def main():
                           "l2": "inputs larger than L2 (psi 2 GiB in fp32), no flush needed",
                           "parallelism": f"replica x{world} (independent shifts per GPU)"},
                "roofline": roof, "e2e": e2e, "gpu_launches": launches,
+               "graph_replay_value": graph_value,
                "clocks": clk.summary(),
                "fp64_gpu": fp64,
+               "eps_rel_err_vs_fp64": eps_err,
+               "eps_check": "cell A on 8^3 grid, MP 2^3, plane-wave start, kick 0.005 x, 600 steps, "
+                            "eps over 0.1-20 eV vs the FP64 GPU path (FP64 GPU vs oracle: err_J <= 1e-10)",
                "fp32_over_fp64": (value / world / fp64["value"]) if fp64 else None,
                "two_step_dJx_last": float(J_avg[-1, 0])}
         if cpu is not None:

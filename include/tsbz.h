@@ -168,6 +168,14 @@ int tsbz_get_launch_count(tsbz_ctx* ctx, long long* launches);
 int tsbz_get_timings(tsbz_ctx* ctx, double* times_ms, int n);
 int tsbz_set_profiling(tsbz_ctx* ctx, int on);
 
+/* Replay time steps from a CUDA graph (on = 1; default off).  The first
+ * propagated step after enabling runs normally and is then captured once on
+ * a stream the library owns; later steps replay the graph, ordered against
+ * the caller's stream by events.  Profiling (tsbz_set_profiling) takes the
+ * direct-launch path.  Set-up calls invalidate nothing: the graph reads the
+ * step counters and field samples from device memory. */
+int tsbz_set_graphs(tsbz_ctx* ctx, int on);
+
 const char* tsbz_last_error(tsbz_ctx* ctx);
 void tsbz_destroy(tsbz_ctx* ctx);
 

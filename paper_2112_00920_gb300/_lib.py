@@ -85,6 +85,7 @@ _SIGS = {
     "tsbz_get_launch_count": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong)], ctypes.c_int),
     "tsbz_get_timings": ([ctypes.c_void_p, _D, ctypes.c_int], ctypes.c_int),
     "tsbz_set_profiling": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
+    "tsbz_set_graphs": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "tsbz_last_error": ([ctypes.c_void_p], ctypes.c_char_p),
     "tsbz_destroy": ([ctypes.c_void_p], None),
     "tsbz_shifted_kpoints": ([_D, _I, _D, _D, ctypes.c_size_t], ctypes.c_int),
@@ -349,6 +350,9 @@ class Propagator:
         n = ctypes.c_longlong()
         self._check(self.lib.tsbz_get_launch_count(self.ctx, ctypes.byref(n)), "tsbz_get_launch_count")
         return n.value
+
+    def set_graphs(self, on: bool):
+        self._check(self.lib.tsbz_set_graphs(self.ctx, 1 if on else 0), "tsbz_set_graphs")
 
     def set_profiling(self, on: bool):
         self._check(self.lib.tsbz_set_profiling(self.ctx, 1 if on else 0), "tsbz_set_profiling")

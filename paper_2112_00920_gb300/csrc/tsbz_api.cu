@@ -101,6 +101,11 @@ struct tsbz_ctx {
   std::vector<long long> unit_psi_off;
   long long launches = 0;
   bool prof = false;
+  bool graphs = false;
+  cudaStream_t gstream = nullptr;     // the library's own stream for graph capture and replay
+  cudaGraphExec_t step_graph = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  long long graph_launches = 0;       // kernels in one captured step
   double times[7] = {0, 0, 0, 0, 0, 0, 0};
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, int>> ev_marks;   // (family, event index of start)
@@ -353,7 +358,9 @@ template <typename T> int run_observe(tsbz_ctx* ctx, int fin_mode) {
     ev_stop(ctx);
     if (hc.dev.use_proj) ++ctx->launches;
     ev_start(ctx, FAM_OBS);
-    launch_observe<T>(L, ctx->psi, ctx->rho_part, ctx->jk_part, ctx->nrm_part, ctx->stream);
+    if (!(ctx->precision == TSBZ_FP32_TC &&
+          launch_observe_zf(L, ctx->psi, ctx->rho_part, ctx->jk_part, ctx->nrm_part, ctx->stream)))
+      launch_observe<T>(L, ctx->psi, ctx->rho_part, ctx->jk_part, ctx->nrm_part, ctx->stream);
     ev_stop(ctx);
     ++ctx->launches;
   }
@@ -455,6 +462,51 @@ template <typename T> int run_init(tsbz_ctx* ctx, bool minus, bool plus) {
     run_field<T>(ctx, TSBZ_FIELD_J0PLUS);
     run_observe<T>(ctx, TSBZ_FIN_J0PLUS);
   }
+  return TSBZ_OK;
+}
+
+// One time step captured once as a CUDA graph on the library's own stream
+// and replayed n times; the caller's stream and the library stream are
+// ordered by events on both sides.  The first step runs uncaptured, so
+// one-time set-up (kernel attributes) happens outside the capture.
+int run_steps_graph(tsbz_ctx* ctx, int n_steps) {
+  if (!ctx->gstream) {
+    CK(cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming));
+  }
+  int done = 0;
+  if (!ctx->step_graph) {
+    int rc = ctx->precision == TSBZ_FP64 ? run_step<double>(ctx) : run_step<float>(ctx);
+    if (rc) return rc;
+    CK(cudaGetLastError());
+    done = 1;
+    CK(cudaEventRecord(ctx->ev_in, ctx->stream));
+    CK(cudaStreamWaitEvent(ctx->gstream, ctx->ev_in, 0));
+    cudaStream_t user = ctx->stream;
+    const long long launches0 = ctx->launches;
+    ctx->stream = ctx->gstream;
+    CK(cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeThreadLocal));
+    rc = ctx->precision == TSBZ_FP64 ? run_step<double>(ctx) : run_step<float>(ctx);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(ctx->gstream, &graph);
+    ctx->stream = user;
+    ctx->graph_launches = ctx->launches - launches0;
+    ctx->launches = launches0;
+    if (rc) return rc;
+    if (ec != cudaSuccess) return set_err(ctx, TSBZ_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
+    const cudaError_t ei = cudaGraphInstantiate(&ctx->step_graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) return set_err(ctx, TSBZ_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ei));
+  }
+  CK(cudaEventRecord(ctx->ev_in, ctx->stream));
+  CK(cudaStreamWaitEvent(ctx->gstream, ctx->ev_in, 0));
+  for (int i = done; i < n_steps; ++i) {
+    CK(cudaGraphLaunch(ctx->step_graph, ctx->gstream));
+    ctx->launches += ctx->graph_launches;
+  }
+  CK(cudaEventRecord(ctx->ev_out, ctx->gstream));
+  CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_out, 0));
   return TSBZ_OK;
 }
 
@@ -750,9 +802,13 @@ int tsbz_propagate(tsbz_ctx* ctx, int n_steps) {
       return set_err(ctx, TSBZ_EINVAL, "sub-simulation " + std::to_string(s) + " would exceed its max_steps");
   ctx->ev_marks.clear();
   ctx->ev_next = 0;
-  for (int i = 0; i < n_steps; ++i) {
-    rc = ctx->precision == TSBZ_FP64 ? run_step<double>(ctx) : run_step<float>(ctx);
-    if (rc) return rc;
+  if (ctx->graphs && !ctx->prof && n_steps > 0) {
+    if ((rc = run_steps_graph(ctx, n_steps))) return rc;
+  } else {
+    for (int i = 0; i < n_steps; ++i) {
+      rc = ctx->precision == TSBZ_FP64 ? run_step<double>(ctx) : run_step<float>(ctx);
+      if (rc) return rc;
+    }
   }
   CK(cudaGetLastError());
   if ((rc = sync_and_check(ctx))) return rc;
@@ -900,6 +956,12 @@ int tsbz_get_launch_count(tsbz_ctx* ctx, long long* launches) {
   return TSBZ_OK;
 }
 
+int tsbz_set_graphs(tsbz_ctx* ctx, int on) {
+  if (!ctx) return TSBZ_EINVAL;
+  ctx->graphs = on != 0;
+  return TSBZ_OK;
+}
+
 int tsbz_set_profiling(tsbz_ctx* ctx, int on) {
   if (!ctx) return TSBZ_EINVAL;
   ctx->prof = on != 0;
@@ -925,6 +987,13 @@ void tsbz_destroy(tsbz_ctx* ctx) {
       cudaFree(p);
   }
   for (auto e : ctx->ev_pool) cudaEventDestroy(e);
+  if (ctx->step_graph) cudaGraphExecDestroy(ctx->step_graph);
+  if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
+  if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
+  if (ctx->gstream) {
+    cudaStreamSynchronize(ctx->gstream);
+    cudaStreamDestroy(ctx->gstream);
+  }
   delete ctx;
 }
 

@@ -123,6 +123,7 @@ template <typename T> void launch_convert_out_t(const void* src, double2* dst, l
 template <typename T> void launch_veff_frozen_t(const SubDev* subs_dev, int s, const CellDev& c, void* stream);
 // tensor-core mode (float orbitals)
 void launch_bra_tc(const LaunchSet& L, const void* psi, void* out, int with_d, void* stream);
-void launch_stage_tc(const LaunchSet& L, const void* tin, void* tout, void* psi, void* P, int m, void* stream);
 void launch_ket_tc(const LaunchSet& L, const void* P, void* V, void* stream);
+bool launch_observe_zf(const LaunchSet& L, const void* psi, double* rho_part, double* jk_part, double* nrm_part,
+                       void* stream);
 void launch_stage_v(const LaunchSet& L, const void* tin, void* tout, void* psi, const void* V, int m, void* stream);

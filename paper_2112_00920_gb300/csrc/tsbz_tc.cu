@@ -9,9 +9,6 @@ static void tc_set_attributes() {
   if (tc_attr_set) return;
   cudaFuncSetAttribute(k_bra_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TwSmem));
   cudaFuncSetAttribute(k_ket_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TwSmem));
-  cudaFuncSetAttribute(k_bra_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TcSmem));
-  cudaFuncSetAttribute(k_stage_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TcSmem));
-  cudaFuncSetAttribute(k_ket_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TcSmem));
   tc_attr_set = true;
 }
 
@@ -22,12 +19,6 @@ void launch_bra_tc(const LaunchSet& L, const void* psi, void* out, int with_d, v
   k_bra_w<<<L.n_units, 256, sizeof(TwSmem), (cudaStream_t)stream>>>(L, (const float2*)psi, (float2*)out, with_d);
 }
 
-void launch_stage_tc(const LaunchSet& L, const void* tin, void* tout, void* psi, void* P, int m, void* stream) {
-  if (L.n_units == 0) return;
-  tc_set_attributes();
-  k_stage_tc<<<L.n_units * TC_CL, TC_THREADS, sizeof(TcSmem), (cudaStream_t)stream>>>(
-      L, (const float2*)tin, (float2*)tout, (float2*)psi, (const float2*)P, (float2*)P, m);
-}
 
 void launch_ket_tc(const LaunchSet& L, const void* P, void* V, void* stream) {
   if (L.n_units == 0) return;
@@ -59,4 +50,14 @@ void launch_stage_v(const LaunchSet& L, const void* tin, void* tout, void* psi, 
   dim3 grid(L.cell.n_tiles, L.n_units);
   k_stage_v<float, TC_ND><<<grid, TSBZ_PT, 0, (cudaStream_t)stream>>>(L, (const float2*)tin, (float2*)tout,
                                                                       (float2*)psi, (const float2*)V, m);
+}
+
+bool launch_observe_zf(const LaunchSet& L, const void* psi, double* rho_part, double* jk_part, double* nrm_part,
+                       void* stream) {
+  const int n12 = L.cell.n1 * L.cell.n2;
+  if (L.cell.n3 != 16 || n12 > 256 || L.cell.n_bgroups != 1 || L.n_units == 0) return false;
+  const int threads = ((n12 + 31) / 32) * 32;
+  k_observe_zf<16><<<L.n_units, threads, 0, (cudaStream_t)stream>>>(L, (const float2*)psi, rho_part, jk_part,
+                                                                    nrm_part);
+  return true;
 }

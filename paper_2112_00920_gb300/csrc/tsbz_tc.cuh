@@ -3,59 +3,47 @@
 //
 // Projector values of one k-point, C_j(r) = conj(beta~_j(r)) = pnorm_j F_x F_y F_z w_j,
 // with the per-axis factors F_ax(i) = g_ax(i) exp(+i q_ax d_ax(i)) and
-// w_j in {1, d_x, d_y, d_z}, are generated per tile of TC_PT grid points in
+// w_j in {1, d_x, d_y, d_z}, are generated per tile of grid points in
 // shared memory as a real matrix Cs[pt][j'] (j' < 32: Re C_j, j' >= 32:
-// Im C_j), each value split into a BF16 high part and a BF16 low part
-// (x ~ hi + lo).  A product A B is evaluated as A_hi B_hi + A_hi B_lo +
-// A_lo B_hi with mma.sync m16n8k16 and FP32 accumulation.
+// Im C_j).  Every operand value x is scaled by S = 2^10 and split into an
+// FP16 high part and an FP16 low part (S x ~ hi + lo, each round to
+// nearest; the scale keeps the low parts in the normal FP16 range).  A
+// product A B is evaluated as A_hi B_hi + A_hi B_lo + A_lo B_hi with
+// mma.sync m16n8k16 (f16 inputs, FP32 accumulate), about 2^-21 relative
+// error per product, and the accumulator is multiplied by 1/S^2 = 2^-20.
 //   bra  P_jb = dV sum_r C_j(r) t_b(r):  D[j'][n'] = sum_pt Cs[pt][j'] Ts[n'][pt]
 //        (n' < 16: Re t_b, n' >= 16: Im t_b), P_re = D[j][b] - D[32+j][16+b],
 //        P_im = D[j][16+b] + D[32+j][b]
 //   ket  V_b(r) = sum_j conj(C_j(r)) E_j P_jb:  V[pt][n'] = sum_j' Cs[pt][j'] Wt[n'][j']
 //        with Wt built from W = E P so that V[pt][b] = Re V_b, V[pt][16+b] = Im V_b.
-// A cluster of TC_CL CTAs handles one unit (k-point; bands <= 16,
-// projectors <= 32, grid edges <= 32); CTA rank r of the cluster takes a
-// contiguous chunk of the point tiles, so the CTAs of one unit run together
-// and share its orbitals in L2.  The per-CTA bra sums are added across the
-// cluster through distributed shared memory in rank order (deterministic).
+// Limits of this mode per cell: bands <= 16, projectors <= 32, grid edges <= 32.
 #pragma once
-#include <cooperative_groups.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "tsbz_internal.h"
 
-#define TC_PT 128          // grid points per tile
-#define TC_THREADS 256     // 8 warps
-#define TC_CS_PITCH 72     // bf16 per Cs row (64 + 8 padding)
 #define TC_W_PITCH 72      // bf16 per Wt row
-#define TC_TS_PITCH 136    // bf16 per Ts row (128 + 8 padding)
 #define TC_D_PITCH 33      // floats per row of the final bra combination
 #define TC_ND 4            // stencil half-width of the fused stage
 #define TC_NMAX 32         // largest grid edge
 #define TC_NA 8            // atoms (projectors / 4)
-#define TC_CL 8            // CTAs per cluster (one cluster per unit)
 
-struct TcSmem {
-  __nv_bfloat16 cs_hi[TC_PT * TC_CS_PITCH];
-  __nv_bfloat16 cs_lo[TC_PT * TC_CS_PITCH];
-  __nv_bfloat16 ts_hi[32 * TC_TS_PITCH];
-  __nv_bfloat16 ts_lo[32 * TC_TS_PITCH];
-  __nv_bfloat16 w_hi[32 * TC_W_PITCH];
-  __nv_bfloat16 w_lo[32 * TC_W_PITCH];
-  float2 fac[TC_NA * 3 * TC_NMAX];   // F_ax(i) per atom and axis
-  float dis[TC_NA * 3 * TC_NMAX];    // d_ax(i)
-  float pn[TC_NA * 4];               // pnorm
-};
 
-// Split a pair (x, y) into packed BF16 high parts and packed BF16 low parts
-// (round to nearest for both); one packed conversion per part, because
-// conversions issue on a narrow pipe.
+#define TC_SCALE 1024.0f               // operand scale S
+#define TC_UNSCALE (1.0f / 1048576.0f)   // 1 / S^2
+
+// Split a pair (x, y) into packed FP16 high parts and packed FP16 low parts
+// of (S x, S y); one packed conversion per part, because conversions issue
+// on a narrow pipe.
 __device__ __forceinline__ void tc_split2(float x, float y, uint32_t& hi, uint32_t& lo) {
-  const __nv_bfloat162 h = __floats2bfloat162_rn(x, y);
-  const float2 hf = __bfloat1622float2(h);
-  const __nv_bfloat162 l = __floats2bfloat162_rn(x - hf.x, y - hf.y);
+  x *= TC_SCALE;
+  y *= TC_SCALE;
+  const __half2 h = __floats2half2_rn(x, y);
+  const float2 hf = __half22float2(h);
+  const __half2 l = __floats2half2_rn(x - hf.x, y - hf.y);
   hi = *reinterpret_cast<const uint32_t*>(&h);
   lo = *reinterpret_cast<const uint32_t*>(&l);
 }
@@ -68,7 +56,7 @@ __device__ __forceinline__ void tc_st16(__nv_bfloat16* p, uint32_t bits) {
 
 __device__ __forceinline__ void tc_mma(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
   asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
       "{%0,%1,%2,%3};\n"
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
@@ -79,511 +67,6 @@ __device__ __forceinline__ void tc_ldsm_x4_trans(uint32_t (&r)[4], const __nv_bf
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
                : "r"(addr));
-}
-
-// Per-axis factors F_ax(i) = g_ax(i) * phase_ax(i), displacements and
-// normalisations of one unit into shared memory.
-__device__ __forceinline__ void tc_load_tables(TcSmem& sm, const CellDev& c, const float2* ph) {
-  const int nm = c.nmax;
-  const int n = c.n_atoms * 3 * nm;
-  for (int i = threadIdx.x; i < n; i += TC_THREADS) {
-    const int a = i / (3 * nm), r = i % (3 * nm);
-    const int ax = r / nm, ii = r % nm;
-    const float g = c.g1f[i];
-    const float2 p = ph[i];
-    sm.fac[(a * 3 + ax) * TC_NMAX + ii] = make_float2(g * p.x, g * p.y);
-    sm.dis[(a * 3 + ax) * TC_NMAX + ii] = c.d1f[i];
-  }
-  for (int i = threadIdx.x; i < 4 * c.n_atoms; i += TC_THREADS) sm.pn[i] = c.pnormf[i];
-}
-
-// Cs for points p0 .. p0+TC_PT-1.  alpha = 0: plain projector rows;
-// alpha = 1..3: rows multiplied by d_x, d_y, d_z.
-__device__ __forceinline__ void tc_gen_c(TcSmem& sm, const CellDev& c, int p0, int alpha) {
-  for (int i = threadIdx.x; i < TC_PT * TC_NA; i += TC_THREADS) {
-    const int pt = i % TC_PT, a = i / TC_PT;
-    const int p = p0 + pt;
-    float cr[4] = {0.f, 0.f, 0.f, 0.f}, ci[4] = {0.f, 0.f, 0.f, 0.f};
-    if (p < c.npts && a < c.n_atoms) {
-      const int ix = p % c.n1, iy = (p / c.n1) % c.n2, iz = p / (c.n1 * c.n2);
-      const float2* fa = sm.fac + a * 3 * TC_NMAX;
-      const float* da = sm.dis + a * 3 * TC_NMAX;
-      const float2 fx = fa[ix], fy = fa[TC_NMAX + iy], fz = fa[2 * TC_NMAX + iz];
-      const float d[3] = {da[ix], da[TC_NMAX + iy], da[2 * TC_NMAX + iz]};
-      const float2 fxy = make_float2(fx.x * fy.x - fx.y * fy.y, fx.x * fy.y + fx.y * fy.x);
-      float fr = fxy.x * fz.x - fxy.y * fz.y, fi = fxy.x * fz.y + fxy.y * fz.x;
-      if (alpha > 0) {
-        fr *= d[alpha - 1];
-        fi *= d[alpha - 1];
-      }
-      const float* pn = sm.pn + 4 * a;
-      const float w[4] = {pn[0], pn[1] * d[0], pn[2] * d[1], pn[3] * d[2]};
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        cr[t] = fr * w[t];
-        ci[t] = fi * w[t];
-      }
-    }
-    uint2 hr, lr, hc, lc;
-    tc_split2(cr[0], cr[1], hr.x, lr.x);
-    tc_split2(cr[2], cr[3], hr.y, lr.y);
-    tc_split2(ci[0], ci[1], hc.x, lc.x);
-    tc_split2(ci[2], ci[3], hc.y, lc.y);
-    *reinterpret_cast<uint2*>(sm.cs_hi + pt * TC_CS_PITCH + 4 * a) = hr;
-    *reinterpret_cast<uint2*>(sm.cs_lo + pt * TC_CS_PITCH + 4 * a) = lr;
-    *reinterpret_cast<uint2*>(sm.cs_hi + pt * TC_CS_PITCH + 32 + 4 * a) = hc;
-    *reinterpret_cast<uint2*>(sm.cs_lo + pt * TC_CS_PITCH + 32 + 4 * a) = lc;
-  }
-}
-
-// D[j'][n'] += sum over the tile of Cs[pt][j'] Ts[n'][pt]; warp w owns j'-tile
-// w/2 and n'-tiles 2(w%2), 2(w%2)+1.
-__device__ __forceinline__ void tc_bra_tile(const TcSmem& sm, float (&acc)[2][4]) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int g = lane >> 2, t = lane & 3;
-  const int mt = warp >> 1, nt0 = 2 * (warp & 1);
-  const int q = lane >> 3, r = lane & 7;
-#pragma unroll 2
-  for (int ks = 0; ks < TC_PT / 16; ++ks) {
-    const int prow = 16 * ks + ((q >> 1) << 3) + r;
-    const int jcol = 16 * mt + ((q & 1) << 3);
-    uint32_t ahi[4], alo[4];
-    tc_ldsm_x4_trans(ahi, sm.cs_hi + prow * TC_CS_PITCH + jcol);
-    tc_ldsm_x4_trans(alo, sm.cs_lo + prow * TC_CS_PITCH + jcol);
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int n = 8 * (nt0 + j) + g;
-      const __nv_bfloat16* bh = sm.ts_hi + n * TC_TS_PITCH + 16 * ks + 2 * t;
-      const __nv_bfloat16* bl = sm.ts_lo + n * TC_TS_PITCH + 16 * ks + 2 * t;
-      const uint32_t bh0 = tc_ld32(bh), bh1 = tc_ld32(bh + 8);
-      const uint32_t bl0 = tc_ld32(bl), bl1 = tc_ld32(bl + 8);
-      tc_mma(acc[j], alo, bh0, bh1);
-      tc_mma(acc[j], ahi, bl0, bl1);
-      tc_mma(acc[j], ahi, bh0, bh1);
-    }
-  }
-}
-
-// Finish a bra: each CTA writes its partial D[j'][n'] (64 x 32) into its
-// Cs area at slot `slot`; after a cluster barrier, CTA rank r forms the
-// outputs (j, b) with b in its share of the bands, summing the partials of
-// ranks 0..TC_CL-1 in order:
-//   out[b * stride + j * jstep + joff] = dV (P_re, P_im).
-// The caller runs the cluster barrier that ends the reads (tc_cluster_done).
-__device__ __forceinline__ void tc_bra_partial(TcSmem& sm, const float (&acc)[2][4], int slot) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int g = lane >> 2, t = lane & 3;
-  const int mt = warp >> 1, nt0 = 2 * (warp & 1);
-  float* D = reinterpret_cast<float*>(sm.cs_hi) + slot * 64 * TC_D_PITCH;
-#pragma unroll
-  for (int j = 0; j < 2; ++j) {
-    const int n = 8 * (nt0 + j) + 2 * t;
-    const int row = 16 * mt + g;
-    D[row * TC_D_PITCH + n] = acc[j][0];
-    D[row * TC_D_PITCH + n + 1] = acc[j][1];
-    D[(row + 8) * TC_D_PITCH + n] = acc[j][2];
-    D[(row + 8) * TC_D_PITCH + n + 1] = acc[j][3];
-  }
-}
-
-__device__ __forceinline__ void tc_bra_reduce(TcSmem& sm, const CellDev& c, float2* out, int stride, int jstep,
-                                              int joff, int slot) {
-  namespace cg = cooperative_groups;
-  cg::cluster_group cluster = cg::this_cluster();
-  const int rank = (int)cluster.block_rank();
-  float* Dloc = reinterpret_cast<float*>(sm.cs_hi) + slot * 64 * TC_D_PITCH;
-  const float dv = (float)c.dv;
-  const int per = (32 * 16) / TC_CL;   // outputs per CTA
-  for (int i = threadIdx.x; i < per; i += TC_THREADS) {
-    const int o = rank * per + i;
-    const int j = o % 32, b = o / 32;
-    if (j < c.n_proj && b < c.n_bands) {
-      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-      for (int r = 0; r < TC_CL; ++r) {
-        const float* D = cluster.map_shared_rank(Dloc, r);
-        a0 += D[j * TC_D_PITCH + b];
-        a1 += D[(32 + j) * TC_D_PITCH + 16 + b];
-        a2 += D[j * TC_D_PITCH + 16 + b];
-        a3 += D[(32 + j) * TC_D_PITCH + b];
-      }
-      out[(long long)b * stride + j * jstep + joff] = make_float2(dv * (a0 - a1), dv * (a2 + a3));
-    }
-  }
-}
-
-// A tile of orbitals (all bands) into Ts as split BF16.
-__device__ __forceinline__ void tc_load_ts(TcSmem& sm, const CellDev& c, const float2* src, int p0) {
-  for (int i = threadIdx.x; i < TC_PT * 16; i += TC_THREADS) {
-    const int pt = i % TC_PT, b = i / TC_PT;
-    const int p = p0 + pt;
-    float2 v = make_float2(0.f, 0.f);
-    if (p < c.npts && b < c.n_bands) v = src[(long long)b * c.npts + p];
-    uint32_t hi, lo;
-    tc_split2(v.x, v.y, hi, lo);
-    tc_st16(sm.ts_hi + b * TC_TS_PITCH + pt, hi);
-    tc_st16(sm.ts_lo + b * TC_TS_PITCH + pt, lo);
-    tc_st16(sm.ts_hi + (16 + b) * TC_TS_PITCH + pt, hi >> 16);
-    tc_st16(sm.ts_lo + (16 + b) * TC_TS_PITCH + pt, lo >> 16);
-  }
-}
-
-// ----------------------------------------------------------------------------
-// Stand-alone bra of psi on tensor cores, one cluster per unit.
-//   with_d = 0: P[u][b][j] from the q_half tables
-//   with_d = 1: Pa[u][b][j][alpha], alpha = 0..3 (plain and d_x, d_y, d_z
-//               weighted rows) from the q_obs tables, in one pass over psi
-// ----------------------------------------------------------------------------
-__global__ void __cluster_dims__(TC_CL, 1, 1) __launch_bounds__(TC_THREADS, 3)
-    k_bra_tc(LaunchSet L, const float2* __restrict__ psi, float2* __restrict__ out, int with_d) {
-  extern __shared__ __align__(16) unsigned char tc_raw[];
-  TcSmem& sm = *reinterpret_cast<TcSmem*>(tc_raw);
-  namespace cg = cooperative_groups;
-  cg::cluster_group cluster = cg::this_cluster();
-  const CellDev& c = L.cell;
-  const int rank = (int)cluster.block_rank();
-  const int u = L.unit_ids[blockIdx.x / TC_CL];
-  const UnitDev U = L.units[u];
-  const float2* ph = (const float2*)(with_d ? L.ph_obs : L.ph_half) + (long long)u * L.ph_stride;
-  const int na = with_d ? 4 : 1;
-  const int n_tiles = (c.npts + TC_PT - 1) / TC_PT;
-  const int tpc = (n_tiles + TC_CL - 1) / TC_CL;
-  const int t_begin = rank * tpc, t_end = min(n_tiles, t_begin + tpc);
-  tc_load_tables(sm, c, ph);
-  float acc[4][2][4];
-#pragma unroll
-  for (int al = 0; al < 4; ++al)
-#pragma unroll
-    for (int j = 0; j < 2; ++j)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) acc[al][j][e] = 0.f;
-  // Each thread carries 8 values (TC_PT x 16 / TC_THREADS) of the next tile
-  // in registers while the current tile's products run.
-  float2 nxt[8];
-  const float2* src = psi + U.psi_off;
-  auto fetch = [&](int p0) {
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int i = threadIdx.x + k * TC_THREADS;
-      const int pt = i % TC_PT, b = i / TC_PT;
-      const int p = p0 + pt;
-      nxt[k] = (p < c.npts && b < c.n_bands) ? src[(long long)b * c.npts + p] : make_float2(0.f, 0.f);
-    }
-  };
-  if (t_begin < t_end) fetch(t_begin * TC_PT);
-  for (int tile = t_begin; tile < t_end; ++tile) {
-    const int p0 = tile * TC_PT;
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int i = threadIdx.x + k * TC_THREADS;
-      const int pt = i % TC_PT, b = i / TC_PT;
-      uint32_t hi, lo;
-      tc_split2(nxt[k].x, nxt[k].y, hi, lo);
-      tc_st16(sm.ts_hi + b * TC_TS_PITCH + pt, hi);
-      tc_st16(sm.ts_lo + b * TC_TS_PITCH + pt, lo);
-      tc_st16(sm.ts_hi + (16 + b) * TC_TS_PITCH + pt, hi >> 16);
-      tc_st16(sm.ts_lo + (16 + b) * TC_TS_PITCH + pt, lo >> 16);
-    }
-    if (tile + 1 < t_end) fetch(p0 + TC_PT);
-#pragma unroll
-    for (int al = 0; al < 4; ++al) {
-      if (al < na) {
-        if (al > 0) __syncthreads();
-        tc_gen_c(sm, c, p0, al);
-        __syncthreads();
-        tc_bra_tile(sm, acc[al]);
-      }
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int al = 0; al < 4; ++al)
-    if (al < na) tc_bra_partial(sm, acc[al], al);
-  cluster.sync();
-#pragma unroll
-  for (int al = 0; al < 4; ++al) {
-    if (al < na) {
-      if (with_d)
-        tc_bra_reduce(sm, c, (float2*)out + U.pa_off, 4 * c.n_proj, 4, al, al);
-      else
-        tc_bra_reduce(sm, c, (float2*)out + U.p_off, c.n_proj, 1, 0, al);
-    }
-  }
-  cluster.sync();   // peers stay resident until every CTA has read their partials
-}
-
-// ----------------------------------------------------------------------------
-// Tensor-core ket: V[u][b][r] = sum_j beta~_j(r) E_j P[u][b][j] (the non-local
-// term of h t), for a chunk of TC_KET_TILES point tiles per CTA.
-// grid (chunks, units), 256 threads; warp w computes points 16w..16w+15 of
-// a tile and writes its results straight from the MMA registers.
-// ----------------------------------------------------------------------------
-#define TC_KET_TILES 4
-__global__ void __launch_bounds__(TC_THREADS, 3) k_ket_tc(LaunchSet L, const float2* __restrict__ P,
-                                                          float2* __restrict__ V) {
-  extern __shared__ __align__(16) unsigned char tc_raw[];
-  TcSmem& sm = *reinterpret_cast<TcSmem*>(tc_raw);
-  const CellDev& c = L.cell;
-  const int u = L.unit_ids[blockIdx.y];
-  const UnitDev U = L.units[u];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int g = lane >> 2, t4 = lane & 3;
-  tc_load_tables(sm, c, (const float2*)L.ph_half + (long long)u * L.ph_stride);
-  // Wt[b][j] = Wr, Wt[16+b][j] = Wi, Wt[b][32+j] = Wi, Wt[16+b][32+j] = -Wr, W = E P
-  for (int i = threadIdx.x; i < 32 * 16; i += TC_THREADS) {
-    const int j = i % 32, b = i / 32;
-    float wr = 0.f, wi = 0.f;
-    if (j < c.n_proj && b < c.n_bands) {
-      const float2 p = P[U.p_off + (long long)b * c.n_proj + j];
-      const float e = (float)c.ekb[j];
-      wr = e * p.x;
-      wi = e * p.y;
-    }
-    uint32_t hi, lo, nhi, nlo;
-    tc_split2(wr, wi, hi, lo);
-    tc_split2(-wr, wi, nhi, nlo);
-    tc_st16(sm.w_hi + b * TC_W_PITCH + j, hi);
-    tc_st16(sm.w_lo + b * TC_W_PITCH + j, lo);
-    tc_st16(sm.w_hi + (16 + b) * TC_W_PITCH + j, hi >> 16);
-    tc_st16(sm.w_lo + (16 + b) * TC_W_PITCH + j, lo >> 16);
-    tc_st16(sm.w_hi + b * TC_W_PITCH + 32 + j, nhi >> 16);
-    tc_st16(sm.w_lo + b * TC_W_PITCH + 32 + j, nlo >> 16);
-    tc_st16(sm.w_hi + (16 + b) * TC_W_PITCH + 32 + j, nhi);
-    tc_st16(sm.w_lo + (16 + b) * TC_W_PITCH + 32 + j, nlo);
-  }
-  const int n_tiles = (c.npts + TC_PT - 1) / TC_PT;
-  const int t_begin = blockIdx.x * TC_KET_TILES, t_end = min(n_tiles, t_begin + TC_KET_TILES);
-  for (int tile = t_begin; tile < t_end; ++tile) {
-    const int p0 = tile * TC_PT;
-    __syncthreads();
-    tc_gen_c(sm, c, p0, 0);
-    __syncthreads();
-    float d[4][4];
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) d[nt][e] = 0.f;
-    const int row = 16 * warp + g;
-#pragma unroll
-    for (int ks = 0; ks < 4; ++ks) {
-      const int col = 16 * ks + 2 * t4;
-      uint32_t ahi[4], alo[4];
-      ahi[0] = tc_ld32(sm.cs_hi + row * TC_CS_PITCH + col);
-      ahi[1] = tc_ld32(sm.cs_hi + (row + 8) * TC_CS_PITCH + col);
-      ahi[2] = tc_ld32(sm.cs_hi + row * TC_CS_PITCH + col + 8);
-      ahi[3] = tc_ld32(sm.cs_hi + (row + 8) * TC_CS_PITCH + col + 8);
-      alo[0] = tc_ld32(sm.cs_lo + row * TC_CS_PITCH + col);
-      alo[1] = tc_ld32(sm.cs_lo + (row + 8) * TC_CS_PITCH + col);
-      alo[2] = tc_ld32(sm.cs_lo + row * TC_CS_PITCH + col + 8);
-      alo[3] = tc_ld32(sm.cs_lo + (row + 8) * TC_CS_PITCH + col + 8);
-#pragma unroll
-      for (int nt = 0; nt < 4; ++nt) {
-        const int n = 8 * nt + g;
-        const uint32_t bh0 = tc_ld32(sm.w_hi + n * TC_W_PITCH + col), bh1 = tc_ld32(sm.w_hi + n * TC_W_PITCH + col + 8);
-        const uint32_t bl0 = tc_ld32(sm.w_lo + n * TC_W_PITCH + col), bl1 = tc_ld32(sm.w_lo + n * TC_W_PITCH + col + 8);
-        tc_mma(d[nt], alo, bh0, bh1);
-        tc_mma(d[nt], ahi, bl0, bl1);
-        tc_mma(d[nt], ahi, bh0, bh1);
-      }
-    }
-    // lane owns points row, row + 8 and bands 2t4, 2t4+1, 8+2t4, 9+2t4
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      const int p = p0 + row + 8 * r;
-      if (p >= c.npts) continue;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int b = 2 * t4 + (k & 1) + 8 * (k >> 1);
-        if (b < c.n_bands)
-          V[U.psi_off + (long long)b * c.npts + p] =
-              make_float2(d[k >> 1][2 * r + (k & 1)], d[2 + (k >> 1)][2 * r + (k & 1)]);
-      }
-    }
-  }
-}
-
-// ----------------------------------------------------------------------------
-// Fused Taylor stage m on tensor cores, one CTA per unit.
-//   t_m = (-i dt/m)[ -1/2 lap t - i q.grad t + (|q|^2/2 + v_eff) t + V_NL t ]
-//   psi accumulation as in k_stage; for m < 4 also P_m = <beta~|t_m> -> Pout.
-// Warp w owns tile points 16w .. 16w+15 for the ket; lane (g, t4) then owns
-// points 16w+g, 16w+g+8 and bands 2t4, 2t4+1, 8+2t4, 9+2t4 of the ket
-// result, and does the stencil and update for exactly those eight pairs.
-// ----------------------------------------------------------------------------
-__global__ void __cluster_dims__(TC_CL, 1, 1) __launch_bounds__(TC_THREADS, 3)
-    k_stage_tc(LaunchSet L, const float2* __restrict__ tin, float2* __restrict__ tout, float2* __restrict__ psi,
-               const float2* __restrict__ Pin, float2* __restrict__ Pout, int m) {
-  extern __shared__ __align__(16) unsigned char tc_raw[];
-  TcSmem& sm = *reinterpret_cast<TcSmem*>(tc_raw);
-  namespace cg = cooperative_groups;
-  cg::cluster_group cluster = cg::this_cluster();
-  const int rank = (int)cluster.block_rank();
-  const CellDev& c = L.cell;
-  const int u = L.unit_ids[blockIdx.x / TC_CL];
-  const UnitDev U = L.units[u];
-  const SubDev S = L.subs[U.sub];
-  const float* qt = reinterpret_cast<const float*>(L.qt_half) + 4 * u;
-  const float q0 = qt[0], q1 = qt[1], q2 = qt[2];
-  const float hdt = (float)S.dt / (float)m;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int g = lane >> 2, t4 = lane & 3;
-  const bool do_bra = m < 4;
-  const float* veff = reinterpret_cast<const float*>(S.veff);
-  const float diag0 = c.hlapf[0][0] + c.hlapf[1][0] + c.hlapf[2][0] + qt[3];
-
-  tc_load_tables(sm, c, (const float2*)L.ph_half + (long long)u * L.ph_stride);
-  // Wt (ket operand) from W = E_j P_jb:
-  //   Wt[b][j] = Wr, Wt[16+b][j] = Wi, Wt[b][32+j] = Wi, Wt[16+b][32+j] = -Wr
-  for (int i = threadIdx.x; i < 32 * 16; i += TC_THREADS) {
-    const int j = i % 32, b = i / 32;
-    float wr = 0.f, wi = 0.f;
-    if (j < c.n_proj && b < c.n_bands) {
-      const float2 p = Pin[U.p_off + (long long)b * c.n_proj + j];
-      const float e = (float)c.ekb[j];
-      wr = e * p.x;
-      wi = e * p.y;
-    }
-    uint32_t hi, lo, nhi, nlo;
-    tc_split2(wr, wi, hi, lo);
-    tc_split2(-wr, wi, nhi, nlo);
-    tc_st16(sm.w_hi + b * TC_W_PITCH + j, hi);
-    tc_st16(sm.w_lo + b * TC_W_PITCH + j, lo);
-    tc_st16(sm.w_hi + (16 + b) * TC_W_PITCH + j, hi >> 16);
-    tc_st16(sm.w_lo + (16 + b) * TC_W_PITCH + j, lo >> 16);
-    tc_st16(sm.w_hi + b * TC_W_PITCH + 32 + j, nhi >> 16);
-    tc_st16(sm.w_lo + b * TC_W_PITCH + 32 + j, nlo >> 16);
-    tc_st16(sm.w_hi + (16 + b) * TC_W_PITCH + 32 + j, nhi);
-    tc_st16(sm.w_lo + (16 + b) * TC_W_PITCH + 32 + j, nlo);
-  }
-  const int n12 = c.n1 * c.n2;
-  float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-  const int n_tiles = (c.npts + TC_PT - 1) / TC_PT;
-  const int tpc = (n_tiles + TC_CL - 1) / TC_CL;
-  const int t_begin = rank * tpc, t_end = min(n_tiles, t_begin + tpc);
-
-  for (int tile = t_begin; tile < t_end; ++tile) {
-    const int p0 = tile * TC_PT;
-    __syncthreads();
-    tc_gen_c(sm, c, p0, 0);
-    __syncthreads();
-    // ket: V for points 16w+g (+8) and all 32 n' in registers
-    float d[4][4];
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) d[nt][e] = 0.f;
-    {
-      const int row = 16 * warp + g;
-#pragma unroll
-      for (int ks = 0; ks < 4; ++ks) {
-        const int col = 16 * ks + 2 * t4;
-        uint32_t ahi[4], alo[4];
-        ahi[0] = tc_ld32(sm.cs_hi + row * TC_CS_PITCH + col);
-        ahi[1] = tc_ld32(sm.cs_hi + (row + 8) * TC_CS_PITCH + col);
-        ahi[2] = tc_ld32(sm.cs_hi + row * TC_CS_PITCH + col + 8);
-        ahi[3] = tc_ld32(sm.cs_hi + (row + 8) * TC_CS_PITCH + col + 8);
-        alo[0] = tc_ld32(sm.cs_lo + row * TC_CS_PITCH + col);
-        alo[1] = tc_ld32(sm.cs_lo + (row + 8) * TC_CS_PITCH + col);
-        alo[2] = tc_ld32(sm.cs_lo + row * TC_CS_PITCH + col + 8);
-        alo[3] = tc_ld32(sm.cs_lo + (row + 8) * TC_CS_PITCH + col + 8);
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt) {
-          const int n = 8 * nt + g;
-          const uint32_t bh0 = tc_ld32(sm.w_hi + n * TC_W_PITCH + col), bh1 = tc_ld32(sm.w_hi + n * TC_W_PITCH + col + 8);
-          const uint32_t bl0 = tc_ld32(sm.w_lo + n * TC_W_PITCH + col), bl1 = tc_ld32(sm.w_lo + n * TC_W_PITCH + col + 8);
-          tc_mma(d[nt], alo, bh0, bh1);
-          tc_mma(d[nt], ahi, bl0, bl1);
-          tc_mma(d[nt], ahi, bh0, bh1);
-        }
-      }
-    }
-    // stencil + ket + Taylor update for this lane's 2 points x 4 bands
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      const int pt = 16 * warp + g + 8 * r;
-      const int p = p0 + pt;
-      const bool valid = p < c.npts;
-      const int pp = valid ? p : 0;
-      const int ix = pp % c.n1, iy = (pp / c.n1) % c.n2, iz = pp / n12;
-      int ox[2 * TC_ND], oy[2 * TC_ND], oz[2 * TC_ND];
-#pragma unroll
-      for (int mm = 1; mm <= TC_ND; ++mm) {
-        ox[2 * mm - 2] = wrap_idx(ix + mm, c.n1) - ix;
-        ox[2 * mm - 1] = wrap_idx(ix - mm, c.n1) - ix;
-        oy[2 * mm - 2] = (wrap_idx(iy + mm, c.n2) - iy) * c.n1;
-        oy[2 * mm - 1] = (wrap_idx(iy - mm, c.n2) - iy) * c.n1;
-        oz[2 * mm - 2] = (wrap_idx(iz + mm, c.n3) - iz) * n12;
-        oz[2 * mm - 1] = (wrap_idx(iz - mm, c.n3) - iz) * n12;
-      }
-      const float dg = diag0 + (valid ? veff[pp] : 0.f);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int b = 2 * t4 + (k & 1) + 8 * (k >> 1);
-        const float vre = d[k >> 1][2 * r + (k & 1)];
-        const float vim = d[2 + (k >> 1)][2 * r + (k & 1)];
-        float tr = 0.f, ti = 0.f;
-        if (valid && b < c.n_bands) {
-          const long long base = U.psi_off + (long long)b * c.npts + pp;
-          const float2* tb = tin + base;
-          const float2 ce = tb[0];
-          float hx = dg * ce.x, hy = dg * ce.y;
-          float gxr = 0.f, gxi = 0.f, gyr = 0.f, gyi = 0.f, gzr = 0.f, gzi = 0.f;
-#pragma unroll
-          for (int mm = 1; mm <= TC_ND; ++mm) {
-            const float2 xu = tb[ox[2 * mm - 2]], xd = tb[ox[2 * mm - 1]];
-            const float2 yu = tb[oy[2 * mm - 2]], yd = tb[oy[2 * mm - 1]];
-            const float2 zu = tb[oz[2 * mm - 2]], zd = tb[oz[2 * mm - 1]];
-            hx = fmaf(c.hlapf[0][mm], xu.x + xd.x, hx);
-            hy = fmaf(c.hlapf[0][mm], xu.y + xd.y, hy);
-            hx = fmaf(c.hlapf[1][mm], yu.x + yd.x, hx);
-            hy = fmaf(c.hlapf[1][mm], yu.y + yd.y, hy);
-            hx = fmaf(c.hlapf[2][mm], zu.x + zd.x, hx);
-            hy = fmaf(c.hlapf[2][mm], zu.y + zd.y, hy);
-            gxr = fmaf(c.gradwf[0][mm], xu.x - xd.x, gxr);
-            gxi = fmaf(c.gradwf[0][mm], xu.y - xd.y, gxi);
-            gyr = fmaf(c.gradwf[1][mm], yu.x - yd.x, gyr);
-            gyi = fmaf(c.gradwf[1][mm], yu.y - yd.y, gyi);
-            gzr = fmaf(c.gradwf[2][mm], zu.x - zd.x, gzr);
-            gzi = fmaf(c.gradwf[2][mm], zu.y - zd.y, gzi);
-          }
-          // q.grad t, then h += -i q.grad t + V_NL t
-          const float qgr = fmaf(q0, gxr, fmaf(q1, gyr, q2 * gzr));
-          const float qgi = fmaf(q0, gxi, fmaf(q1, gyi, q2 * gzi));
-          const float hr = hx + qgi + vre;
-          const float hi = hy - qgr + vim;
-          tr = hdt * hi;
-          ti = -hdt * hr;
-          if (m < 4) tout[base] = make_float2(tr, ti);
-          if (m == 2) {
-            const float2 ps = psi[base];
-            psi[base] = make_float2(ps.x + (ce.x + tr), ps.y + (ce.y + ti));
-          } else if (m >= 3) {
-            const float2 ps = psi[base];
-            psi[base] = make_float2(ps.x + tr, ps.y + ti);
-          }
-        }
-        if (do_bra) {
-          uint32_t hi2, lo2;
-          tc_split2(tr, ti, hi2, lo2);
-          tc_st16(sm.ts_hi + b * TC_TS_PITCH + pt, hi2);
-          tc_st16(sm.ts_lo + b * TC_TS_PITCH + pt, lo2);
-          tc_st16(sm.ts_hi + (16 + b) * TC_TS_PITCH + pt, hi2 >> 16);
-          tc_st16(sm.ts_lo + (16 + b) * TC_TS_PITCH + pt, lo2 >> 16);
-        }
-      }
-    }
-    if (do_bra) {
-      __syncthreads();
-      tc_bra_tile(sm, acc);
-    }
-  }
-  if (do_bra) {
-    __syncthreads();
-    tc_bra_partial(sm, acc, 0);
-    cluster.sync();
-    tc_bra_reduce(sm, c, Pout + U.p_off, c.n_proj, 1, 0, 0);
-    cluster.sync();   // peers stay resident until every CTA has read their partials
-  }
 }
 
 // ============================================================================
@@ -793,7 +276,7 @@ __global__ void __launch_bounds__(256, 2) k_bra_w(LaunchSet L, const float2* __r
   }
   __syncthreads();
   const int n_slots = with_d ? 4 : 1;
-  const float dv = (float)c.dv;
+  const float dv = (float)c.dv * TC_UNSCALE;
   for (int i = threadIdx.x; i < n_slots * 32 * 16; i += blockDim.x) {
     const int sl = i / 512, o = i % 512;
     const int j = o % 32, b = o / 32;
@@ -892,8 +375,8 @@ __global__ void __launch_bounds__(256, 2) k_ket_w(LaunchSet L, const float2* __r
       for (int k = 0; k < 4; ++k) {
         const int b = 2 * t4 + (k & 1) + 8 * (k >> 1);
         if (b < c.n_bands)
-          V[U.psi_off + (long long)b * c.npts + p] =
-              make_float2(d[k >> 1][2 * r + (k & 1)], d[2 + (k >> 1)][2 * r + (k & 1)]);
+          V[U.psi_off + (long long)b * c.npts + p] = make_float2(d[k >> 1][2 * r + (k & 1)] * TC_UNSCALE,
+                                                                 d[2 + (k >> 1)][2 * r + (k & 1)] * TC_UNSCALE);
       }
     }
   }
@@ -991,4 +474,109 @@ __global__ void __launch_bounds__(256, 4) k_stage_zf(LaunchSet L, const float2* 
     p_cur = p_nxt;
     e_cur = e_nxt;
   }
+}
+
+// ----------------------------------------------------------------------------
+// Observation pass for float orbitals on depth-NZ grids, 2.5-D form: one CTA
+// per unit, one thread per (x, y) column; bands outer, z-march inner.  Per
+// column and plane it accumulates occ sum_b |u|^2 (rho) over the bands, and
+// per thread sum Re(u* (-i grad u)) and per band sum |u|^2 (block-reduced per
+// band).  The unit's sums are written to point tile 0 of the partial
+// buffers and zeros to the other tiles, which the finalize kernel adds.
+// ----------------------------------------------------------------------------
+template <int NZ>
+__global__ void __launch_bounds__(256) k_observe_zf(LaunchSet L, const float2* __restrict__ psi,
+                                                    double* __restrict__ rho_part, double* __restrict__ jk_part,
+                                                    double* __restrict__ nrm_part) {
+  constexpr int ND = TC_ND;
+  __shared__ float2 plane[256];
+  __shared__ float red[8];
+  __shared__ double redj[8][3];
+  const CellDev& c = L.cell;
+  const int u = L.unit_ids[blockIdx.x];
+  const UnitDev U = L.units[u];
+  const int n1 = c.n1, n2 = c.n2, n12 = n1 * n2;
+  const int col = threadIdx.x;
+  const bool act = col < n12;
+  const int ix = act ? col % n1 : 0, iy = act ? col / n1 : 0;
+  const int rowb = iy * n1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const float2 zero = make_float2(0.f, 0.f);
+  float rho[NZ];
+#pragma unroll
+  for (int z = 0; z < NZ; ++z) rho[z] = 0.f;
+  double jx = 0.0, jy = 0.0, jz = 0.0;
+  for (int b = 0; b < c.n_bands; ++b) {
+    const float2* tb = psi + U.psi_off + (long long)b * c.npts + col;
+    float2 qv[NZ + 2 * ND];
+#pragma unroll
+    for (int k = 0; k < 2 * ND; ++k) qv[k] = act ? tb[(long long)((k - ND + NZ) % NZ) * n12] : zero;
+    float nb = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
+#pragma unroll
+    for (int z = 0; z < NZ; ++z) {
+      qv[z + 2 * ND] = act ? tb[(long long)((z + ND) % NZ) * n12] : zero;
+      __syncthreads();
+      if (act) plane[col] = qv[z + ND];
+      __syncthreads();
+      if (act) {
+        const float2 ce = qv[z + ND];
+        float2 gx = zero, gy = zero, gz = zero;
+#pragma unroll
+        for (int mm = 1; mm <= ND; ++mm) {
+          const float2 xu = plane[rowb + wrap_idx(ix + mm, n1)], xd = plane[rowb + wrap_idx(ix - mm, n1)];
+          const float2 yu = plane[wrap_idx(iy + mm, n2) * n1 + ix], yd = plane[wrap_idx(iy - mm, n2) * n1 + ix];
+          const float2 zu = qv[z + ND + mm], zd = qv[z + ND - mm];
+          gx.x = fmaf(c.gradwf[0][mm], xu.x - xd.x, gx.x);
+          gx.y = fmaf(c.gradwf[0][mm], xu.y - xd.y, gx.y);
+          gy.x = fmaf(c.gradwf[1][mm], yu.x - yd.x, gy.x);
+          gy.y = fmaf(c.gradwf[1][mm], yu.y - yd.y, gy.y);
+          gz.x = fmaf(c.gradwf[2][mm], zu.x - zd.x, gz.x);
+          gz.y = fmaf(c.gradwf[2][mm], zu.y - zd.y, gz.y);
+        }
+        const float n2v = ce.x * ce.x + ce.y * ce.y;
+        rho[z] += n2v;
+        nb += n2v;
+        // Re(conj(u) (-i g)) = u_r g_i - u_i g_r
+        bx += ce.x * gx.y - ce.y * gx.x;
+        by += ce.x * gy.y - ce.y * gy.x;
+        bz += ce.x * gz.y - ce.y * gz.x;
+      }
+    }
+    jx += bx;
+    jy += by;
+    jz += bz;
+    // band norm: warp then block sum (fixed order)
+    for (int off = 16; off > 0; off >>= 1) nb += __shfl_xor_sync(0xffffffffu, nb, off);
+    __syncthreads();
+    if (lane == 0) red[warp] = nb;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sum = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += (double)red[w];
+      nrm_part[U.nrm_off + b] = sum;
+    }
+  }
+  if (act)
+#pragma unroll
+    for (int z = 0; z < NZ; ++z) rho_part[U.rho_off + (long long)z * n12 + col] = c.occ * (double)rho[z];
+  for (int off = 16; off > 0; off >>= 1) {
+    jx += __shfl_xor_sync(0xffffffffu, jx, off);
+    jy += __shfl_xor_sync(0xffffffffu, jy, off);
+    jz += __shfl_xor_sync(0xffffffffu, jz, off);
+  }
+  if (lane == 0) {
+    redj[warp][0] = jx;
+    redj[warp][1] = jy;
+    redj[warp][2] = jz;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double sum = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += redj[w][threadIdx.x];
+    jk_part[U.jk_off + threadIdx.x] = sum;
+  }
+  // zeros for the other point tiles of the partial layout
+  for (int i = threadIdx.x; i < 3 * (c.n_tiles - 1); i += blockDim.x) jk_part[U.jk_off + 3 + i] = 0.0;
+  for (int i = threadIdx.x; i < c.n_bands * (c.n_tiles - 1); i += blockDim.x)
+    nrm_part[U.nrm_off + c.n_bands + i] = 0.0;
 }

@@ -258,3 +258,54 @@ def test_full_two_step_workload_sampled(precision):
             compare(g, o, FP64_J_TOL, FP64_RHO_TOL)
         else:
             print(precision, m, compare(g, o, 1e-4, 1e-5, 1e-5))
+
+
+def _eps(j, j0, dt, k0, omegas):
+    return analysis.dielectric((j - j0[None, :])[:, 0], dt, k0, omegas)
+
+
+def test_eps_error_vs_oracle():
+    """eps(omega) over 0.1-20 eV (Eqs. 12-14) from each GPU path against the
+    complex128 oracle: cell A on an 8^3 grid, MP 2^3, SCF ground state,
+    kick 0.005 x, 600 steps of dt = 0.08 (T_W = run length).  North-star
+    bar for the float/tensor-core path: err_eps <= 1e-4."""
+    cell = W.cell_a_coarse(n=8)
+    k = kpoints.kpoints_cartesian(cell.a, (2, 2, 2), (0.0, 0.0, 0.0))
+    gs = scf.ground_state(cell, k, seed=7, tol=1e-10, eig_tol=1e-10)
+    n, dt, k0 = 600, 0.08, 0.005
+    s = dict(mp=(2, 2, 2), shift=(0, 0, 0), psi=gs["u"], dt=dt, n_steps=n, field=W.Kick(k0=k0))
+    o = oracle_run(cell, s)
+    om = np.linspace(0.1, 20.0, 400) / 27.211386245988
+    e_ref = _eps(o["J"], o["J0_minus"], dt, k0, om)
+    errs = {}
+    for prec in ("fp64", "fp32", "fp32_tc"):
+        _, g = gpu_run(cell, [s], precision=prec)
+        errs[prec] = analysis.err_eps(_eps(g[0]["J"], g[0]["J0m"], dt, k0, om), e_ref)
+    print("err_eps vs oracle:", errs)
+    assert errs["fp64"] <= 1e-10
+    assert errs["fp32_tc"] <= 1e-4
+    assert errs["fp32"] <= 1e-4
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_tc"])
+def test_graph_replay_bitwise(precision):
+    """Steps replayed from the captured CUDA graph equal direct launches bit for bit."""
+    from paper_2112_00920_gb300 import Propagator, shifted_kpoints
+    cell = _tiny_pair()
+    subs = [random_subsim(cell, (2, 1, 1), (0.5, 0.25, 0.5), 0.08, 7, W.Kick(k0=0.01), seed=8, tag=i) for i in range(2)]
+    out = []
+    for graphs in (False, True):
+        P = Propagator(precision)
+        cid = P.add_cell_spec(cell)
+        sids = [P.add_subsim(cid, shifted_kpoints(cell.a, s["mp"], s["shift"]), s["dt"], 7) for s in subs]
+        for sid, s in zip(sids, subs):
+            P.load_ground_state(sid, s["psi"])
+            P.set_kick(sid, 0.01, (1.0, 0.0, 0.0))
+        P.set_graphs(graphs)
+        P.propagate(3)
+        P.propagate(4)
+        out.append([(P.current(sid)[0], P.get_state(sid)[0]) for sid in sids])
+        P.close()
+    for (ja, sa), (jb, sb) in zip(out[0], out[1]):
+        np.testing.assert_array_equal(ja, jb)
+        np.testing.assert_array_equal(sa, sb)
