@@ -163,8 +163,8 @@ def build_propagator(precision, n_steps_cap, device=0, n_subsims=64):
 # reduced workload (8 of the 64 subgrids, 8192 orbitals) and scaled by the
 # orbital count to the full workload.  Valid only for the kernel source it
 # was taken on: the SHA-1 of the kernel text is checked at run time.
-STAGE_TRAFFIC = {"kernel": "k_stage_zf", "sha1": None, "bytes_per_launch_full": None,
-                 "profile": "profiles/k_stage_zf_fp32tc_reduced8.md"}
+STAGE_TRAFFIC = {"kernel": "k_stage_zf", "sha1": "2afbe1ff13073b336cf76b75f65936eec571d70b",
+                 "bytes_per_launch_full": 8.87e9, "profile": "profiles/k_stage_zf_fp32tc_reduced8.md"}
 
 
 def _kernel_sha1(path: str, name: str) -> str | None:

@@ -35,7 +35,8 @@ void launch_stage_v(const LaunchSet& L, const void* tin, void* tout, void* psi, 
     // 2.5-D z-march, depth 16 unrolled, packed arithmetic
     const int threads = ((n12 + 31) / 32) * 32;
     dim3 grid(L.cell.n_bands, L.n_units);
-    k_stage_zf<16><<<grid, threads, n12 * sizeof(float2), (cudaStream_t)stream>>>(
+    const size_t pad = (size_t)(L.cell.n1 + 2 * TC_ND) * (L.cell.n2 + 2 * TC_ND) * sizeof(float2);
+    k_stage_zf<16><<<grid, threads, pad, (cudaStream_t)stream>>>(
         L, (const float2*)tin, (float2*)tout, (float2*)psi, (const float2*)V, m);
     return;
   }
@@ -55,7 +56,7 @@ void launch_stage_v(const LaunchSet& L, const void* tin, void* tout, void* psi, 
 bool launch_observe_zf(const LaunchSet& L, const void* psi, double* rho_part, double* jk_part, double* nrm_part,
                        void* stream) {
   const int n12 = L.cell.n1 * L.cell.n2;
-  if (L.cell.n3 != 16 || n12 > 256 || L.cell.n_bgroups != 1 || L.n_units == 0) return false;
+  if (L.cell.n3 != 16 || L.cell.n1 > 16 || L.cell.n2 > 16 || L.cell.n_bgroups != 1 || L.n_units == 0) return false;
   const int threads = ((n12 + 31) / 32) * 32;
   k_observe_zf<16><<<L.n_units, threads, 0, (cudaStream_t)stream>>>(L, (const float2*)psi, rho_part, jk_part,
                                                                     nrm_part);

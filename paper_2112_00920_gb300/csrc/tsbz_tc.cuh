@@ -382,6 +382,20 @@ __global__ void __launch_bounds__(256, 2) k_ket_w(LaunchSet L, const float2* __r
   }
 }
 
+
+// Periodic plane with a halo of ND points on each side in x and y: entry
+// (iy + ND) * (n1 + 2 ND) + ix + ND holds t(ix, iy); the halo holds the
+// periodic images, so every in-plane neighbour of the star stencil is a
+// load at a constant offset from the thread's own entry.
+__device__ __forceinline__ void zpad_store(float2* pl, int n1, int n2, int ix, int iy, float2 v) {
+  constexpr int ND = TC_ND;
+  const int W = n1 + 2 * ND;
+  pl[(iy + ND) * W + ix + ND] = v;
+  if (ix < ND) pl[(iy + ND) * W + ix + n1 + ND] = v;
+  if (ix >= n1 - ND) pl[(iy + ND) * W + ix - n1 + ND] = v;
+  if (iy < ND) pl[(iy + n2 + ND) * W + ix + ND] = v;
+  if (iy >= n2 - ND) pl[(iy - n2 + ND) * W + ix + ND] = v;
+}
 // ----------------------------------------------------------------------------
 // Taylor stage m, 2.5-D z-march for float orbitals with a compile-time grid
 // depth NZ (the z loop is fully unrolled, so the register queue of the 2 ND + 1
@@ -407,7 +421,8 @@ __global__ void __launch_bounds__(256, 4) k_stage_zf(LaunchSet L, const float2* 
   const int col = threadIdx.x;
   const bool act = col < n12;
   const int ix = act ? col % n1 : 0, iy = act ? col / n1 : 0;
-  const int rowb = iy * n1;
+  const int W = n1 + 2 * ND;
+  const float2* me = plane + (iy + ND) * W + ix + ND;
   const float* qt = reinterpret_cast<const float*>(L.qt_half) + 4 * u;
   const float q0 = qt[0], q1 = qt[1], q2 = qt[2];
   const float dg0 = c.hlapf[0][0] + c.hlapf[1][0] + c.hlapf[2][0] + qt[3];
@@ -436,7 +451,7 @@ __global__ void __launch_bounds__(256, 4) k_stage_zf(LaunchSet L, const float2* 
       e_nxt = veff[(z + 1) * n12 + col];
     }
     __syncthreads();
-    if (act) plane[col] = qv[z + ND];
+    if (act) zpad_store(plane, n1, n2, ix, iy, qv[z + ND]);
     __syncthreads();
     if (act) {
       const float2 ce = qv[z + ND];
@@ -446,8 +461,8 @@ __global__ void __launch_bounds__(256, 4) k_stage_zf(LaunchSet L, const float2* 
       float2 gx = zero, gy = zero, gz = zero;
 #pragma unroll
       for (int mm = 1; mm <= ND; ++mm) {
-        const float2 xu = plane[rowb + wrap_idx(ix + mm, n1)], xd = plane[rowb + wrap_idx(ix - mm, n1)];
-        const float2 yu = plane[wrap_idx(iy + mm, n2) * n1 + ix], yd = plane[wrap_idx(iy - mm, n2) * n1 + ix];
+        const float2 xu = me[mm], xd = me[-mm];
+        const float2 yu = me[mm * W], yd = me[-mm * W];
         const float2 zu = qv[z + ND + mm], zd = qv[z + ND - mm];
         h = f2fma(c.hlap2[0][mm], __fadd2_rn(xu, xd), h);
         h = f2fma(c.hlap2[1][mm], __fadd2_rn(yu, yd), h);
@@ -489,7 +504,7 @@ __global__ void __launch_bounds__(256) k_observe_zf(LaunchSet L, const float2* _
                                                     double* __restrict__ rho_part, double* __restrict__ jk_part,
                                                     double* __restrict__ nrm_part) {
   constexpr int ND = TC_ND;
-  __shared__ float2 plane[256];
+  __shared__ float2 plane[(16 + 2 * TC_ND) * (16 + 2 * TC_ND)];
   __shared__ float red[8];
   __shared__ double redj[8][3];
   const CellDev& c = L.cell;
@@ -499,7 +514,8 @@ __global__ void __launch_bounds__(256) k_observe_zf(LaunchSet L, const float2* _
   const int col = threadIdx.x;
   const bool act = col < n12;
   const int ix = act ? col % n1 : 0, iy = act ? col / n1 : 0;
-  const int rowb = iy * n1;
+  const int W = n1 + 2 * ND;
+  const float2* me = plane + (iy + ND) * W + ix + ND;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const float2 zero = make_float2(0.f, 0.f);
   float rho[NZ];
@@ -516,15 +532,15 @@ __global__ void __launch_bounds__(256) k_observe_zf(LaunchSet L, const float2* _
     for (int z = 0; z < NZ; ++z) {
       qv[z + 2 * ND] = act ? tb[(long long)((z + ND) % NZ) * n12] : zero;
       __syncthreads();
-      if (act) plane[col] = qv[z + ND];
+      if (act) zpad_store(plane, n1, n2, ix, iy, qv[z + ND]);
       __syncthreads();
       if (act) {
         const float2 ce = qv[z + ND];
         float2 gx = zero, gy = zero, gz = zero;
 #pragma unroll
         for (int mm = 1; mm <= ND; ++mm) {
-          const float2 xu = plane[rowb + wrap_idx(ix + mm, n1)], xd = plane[rowb + wrap_idx(ix - mm, n1)];
-          const float2 yu = plane[wrap_idx(iy + mm, n2) * n1 + ix], yd = plane[wrap_idx(iy - mm, n2) * n1 + ix];
+          const float2 xu = me[mm], xd = me[-mm];
+          const float2 yu = me[mm * W], yd = me[-mm * W];
           const float2 zu = qv[z + ND + mm], zd = qv[z + ND - mm];
           gx.x = fmaf(c.gradwf[0][mm], xu.x - xd.x, gx.x);
           gx.y = fmaf(c.gradwf[0][mm], xu.y - xd.y, gx.y);
