@@ -21,6 +21,7 @@
 #include "tsbz.h"
 #include "tsbz_host.h"
 #include "tsbz_internal.h"
+#include "tsbz_bulk.cuh"
 
 namespace {
 
@@ -34,6 +35,7 @@ struct HostCell {
   int* d_unit_ids = nullptr;
   std::vector<int> hxc_subs;   // non-frozen sub-simulations of this cell
   int* d_hxc_subs = nullptr;
+  bool pa_by_stage = false;    // the last stage 4 also wrote P (next step) and Pa
 };
 
 struct HostSub {
@@ -79,7 +81,9 @@ struct tsbz_ctx {
   void* vnl = nullptr;     // non-local term of the tensor-core mode
   void* ph_half = nullptr;
   void* ph_obs = nullptr;
+  void* ph_next = nullptr;   // tables of the next step (single-precision mode)
   long long ph_stride = 1;
+  bool p_next_valid = false; // P holds the projections of psi for the coming step
   double* rho_part = nullptr;
   double* jk_part = nullptr;
   double* nrm_part = nullptr;
@@ -184,6 +188,7 @@ LaunchSet make_set(tsbz_ctx* ctx, HostCell& hc) {
   L.q_obs = ctx->q_obs;
   L.ph_half = ctx->ph_half;
   L.ph_obs = ctx->ph_obs;
+  L.ph_next = ctx->ph_next;
   L.ph_stride = ctx->ph_stride;
   L.qt_half = ctx->qt_half;
   return L;
@@ -243,6 +248,7 @@ int layout(tsbz_ctx* ctx) {
   if ((rc = dalloc(ctx, std::max<long long>(pa_e, 1) * es, &ctx->Pa))) return rc;
   if ((rc = dalloc(ctx, ctx->n_units * ph_stride * es, &ctx->ph_half))) return rc;
   if ((rc = dalloc(ctx, ctx->n_units * ph_stride * es, &ctx->ph_obs))) return rc;
+  if (ctx->precision == TSBZ_FP32 && (rc = dalloc(ctx, ctx->n_units * ph_stride * es, &ctx->ph_next))) return rc;
   if ((rc = dalloc_t(ctx, rho_e, &ctx->rho_part))) return rc;
   if ((rc = dalloc_t(ctx, std::max<long long>(jk_e, 1), &ctx->jk_part))) return rc;
   if ((rc = dalloc_t(ctx, std::max<long long>(nrm_e, 1), &ctx->nrm_part))) return rc;
@@ -350,15 +356,20 @@ template <typename T> int run_observe(tsbz_ctx* ctx, int fin_mode) {
   for (auto& hc : ctx->cells) {
     if (hc.unit_ids.empty()) continue;
     LaunchSet L = make_set(ctx, hc);
-    ev_start(ctx, FAM_BRA);
-    if (ctx->precision == TSBZ_FP32_TC)
-      launch_bra_tc(L, ctx->psi, ctx->Pa, 1, ctx->stream);
-    else
-      launch_bra<T>(L, ctx->psi, ctx->Pa, 1, 1, ctx->stream);
-    ev_stop(ctx);
-    if (hc.dev.use_proj) ++ctx->launches;
+    const bool sep = ctx->precision == TSBZ_FP32 && sep_supported(hc.dev);
+    if (!(fin_mode == TSBZ_FIN_STEP && hc.pa_by_stage)) {
+      ev_start(ctx, FAM_BRA);
+      if (ctx->precision == TSBZ_FP32_TC)
+        launch_bra_tc(L, ctx->psi, ctx->Pa, 1, ctx->stream);
+      else if (sep)
+        launch_bra_sep(L, ctx->psi, ctx->Pa, 1, 1, ctx->stream);
+      else
+        launch_bra<T>(L, ctx->psi, ctx->Pa, 1, 1, ctx->stream);
+      ev_stop(ctx);
+      if (hc.dev.use_proj) ++ctx->launches;
+    }
     ev_start(ctx, FAM_OBS);
-    if (!(ctx->precision == TSBZ_FP32_TC &&
+    if (!(ctx->precision != TSBZ_FP64 &&
           launch_observe_zf(L, ctx->psi, ctx->rho_part, ctx->jk_part, ctx->nrm_part, ctx->stream)))
       launch_observe<T>(L, ctx->psi, ctx->rho_part, ctx->jk_part, ctx->nrm_part, ctx->stream);
     ev_stop(ctx);
@@ -420,10 +431,30 @@ template <typename T> int run_step(tsbz_ctx* ctx) {
   run_field<T>(ctx, TSBZ_FIELD_STEP);
   void* srcs[4] = {ctx->psi, ctx->tA, ctx->tB, ctx->tA};
   void* dsts[4] = {ctx->tA, ctx->tB, ctx->tA, nullptr};
-  for (int m = 1; m <= 4; ++m) {
-    for (auto& hc : ctx->cells) {
-      if (hc.unit_ids.empty()) continue;
-      LaunchSet L = make_set(ctx, hc);
+  for (auto& hc : ctx->cells) {
+    if (hc.unit_ids.empty()) continue;
+    LaunchSet L = make_set(ctx, hc);
+    if (ctx->precision == TSBZ_FP32 && sep_supported(hc.dev)) {
+      // Four fused stages; each leaves the projections of its t_m in P, and the
+      // bulk-staged stage 4 those of psi(t_{n+1}) for the next step and of the
+      // current (Pa).  The projections of psi are computed here only when P does
+      // not hold them already (first step, or after the state or field changed).
+      if (!ctx->p_next_valid || !hc.pa_by_stage) {
+        ev_start(ctx, FAM_BRA);
+        launch_bra_sep(L, ctx->psi, ctx->P, 0, 0, ctx->stream);
+        ev_stop(ctx);
+        if (hc.dev.use_proj) ++ctx->launches;
+      }
+      for (int m = 1; m <= 4; ++m) {
+        ev_start(ctx, FAM_STAGE);
+        const bool fused4 = launch_stage_sep(L, srcs[m - 1], dsts[m - 1], ctx->psi, ctx->P, ctx->Pa, m, ctx->stream);
+        if (m == 4) hc.pa_by_stage = fused4;
+        ev_stop(ctx);
+        ++ctx->launches;
+      }
+      continue;
+    }
+    for (int m = 1; m <= 4; ++m) {
       ev_start(ctx, FAM_BRA);
       launch_bra<T>(L, srcs[m - 1], ctx->P, 0, 0, ctx->stream);
       ev_stop(ctx);
@@ -436,10 +467,12 @@ template <typename T> int run_step(tsbz_ctx* ctx) {
   }
   run_observe<T>(ctx, TSBZ_FIN_STEP);
   run_hxc<T>(ctx);
+  ctx->p_next_valid = true;
   return TSBZ_OK;
 }
 
 template <typename T> int run_init(tsbz_ctx* ctx, bool minus, bool plus) {
+  ctx->p_next_valid = false;
   std::vector<int> mask(ctx->subs.size(), 0);
   if (minus) {
     for (size_t s = 0; s < ctx->subs.size(); ++s) mask[s] = ctx->subs[s].need_init ? 1 : 0;
@@ -476,6 +509,12 @@ int run_steps_graph(tsbz_ctx* ctx, int n_steps) {
     CK(cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming));
   }
   int done = 0;
+  if (ctx->step_graph && !ctx->p_next_valid) {
+    // the captured step assumes P already holds the projections of psi
+    int rc = ctx->precision == TSBZ_FP64 ? run_step<double>(ctx) : run_step<float>(ctx);
+    if (rc) return rc;
+    done = 1;
+  }
   if (!ctx->step_graph) {
     int rc = ctx->precision == TSBZ_FP64 ? run_step<double>(ctx) : run_step<float>(ctx);
     if (rc) return rc;
@@ -824,6 +863,9 @@ int tsbz_propagate(tsbz_ctx* ctx, int n_steps) {
   std::vector<int> st(ctx->subs.size(), 0);
   CK(cudaMemcpy(st.data(), ctx->d_status, sizeof(int) * st.size(), cudaMemcpyDeviceToHost));
   for (size_t s = 0; s < st.size(); ++s)
+    if (st[s] & BK_STATUS_TIMEOUT)
+      return set_err(ctx, TSBZ_ETIMEOUT, "a bounded device wait gave up in sub-simulation " + std::to_string(s));
+  for (size_t s = 0; s < st.size(); ++s)
     if (st[s]) return set_err(ctx, TSBZ_ENONFINITE, "non-finite current in sub-simulation " + std::to_string(s));
   return TSBZ_OK;
 }
@@ -918,6 +960,7 @@ int tsbz_load_state(tsbz_ctx* ctx, int s, const double* psi, size_t n_elems, int
   if (step < 0 || step > hs.max_steps) return set_err(ctx, TSBZ_EINVAL, "bad step");
   if ((rc = ensure_ready(ctx))) return rc;
   if ((rc = copy_state_in(ctx, s, psi, n_elems, 0))) return rc;
+  ctx->p_next_valid = false;
   CK(cudaMemcpyAsync(ctx->d_steps + s, &step, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
   hs.steps = step;
   // rho, norms and v_Hxc from the restored orbitals (no current is written)

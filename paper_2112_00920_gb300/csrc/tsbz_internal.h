@@ -98,6 +98,7 @@ struct LaunchSet {
   double* q_obs;          // [unit][3]
   void* ph_half;          // [unit][n_atoms*3*nmax] complex T
   void* ph_obs;
+  void* ph_next;          // q = k + A(t_{n+1} + dt/2): tables of the next step (null if unused)
   long long ph_stride;    // complex elements per unit
   void* qt_half;          // [unit][4] in T: q_x, q_y, q_z, |q|^2 / 2 at t_n + dt/2
 };
@@ -127,3 +128,9 @@ void launch_ket_tc(const LaunchSet& L, const void* P, void* V, void* stream);
 bool launch_observe_zf(const LaunchSet& L, const void* psi, double* rho_part, double* jk_part, double* nrm_part,
                        void* stream);
 void launch_stage_v(const LaunchSet& L, const void* tin, void* tout, void* psi, const void* V, int m, void* stream);
+// single-precision fused stage and projections (cells with at most 8 atoms, depth 8 or 16, n1 n2 <= 256)
+bool sep_supported(const CellDev& c);
+void launch_bra_sep(const LaunchSet& L, const void* src, void* out, int with_d, int use_obs, void* stream);
+// stage 4 on the bulk-staged path also writes P (next step) and Pa; returns whether it did
+bool launch_stage_sep(const LaunchSet& L, const void* tin, void* tout, void* psi, void* P, void* Pa, int m,
+                      void* stream);

@@ -114,6 +114,20 @@ __global__ void k_field(LaunchSet L, int mode) {
     sincos(qo[ax] * d, &s, &co);
     pho[i] = cmk<V>((T)co, (T)s);
   }
+  if (L.ph_next != nullptr && mode == TSBZ_FIELD_STEP) {
+    // q_half of step n + 1, evaluated exactly as that step's field launch will
+    const int step = *S.step;
+    const int jh = 2 * step + 3, jo = 2 * step + 4;
+    double qn[3];
+    for (int ax = 0; ax < 3; ++ax) qn[ax] = L.kcart[3 * u + ax] + (jo < S.n_field ? S.A[3 * jh + ax] : 0.0);
+    V* phn = (V*)L.ph_next + (long long)u * L.ph_stride;
+    for (int i = threadIdx.x; i < tab; i += blockDim.x) {
+      const int ax = (i / c.nmax) % 3;
+      double s, co;
+      sincos(qn[ax] * c.d1[i], &s, &co);
+      phn[i] = cmk<V>((T)co, (T)s);
+    }
+  }
 }
 
 // ----------------------------------------------------------------------------
@@ -690,7 +704,7 @@ __global__ void __launch_bounds__(256) k_finalize(const SubDev* subs, const Unit
       J[ax] = -t / (c.omega * S.n_k);
       finite = finite && isfinite(J[ax]);
     }
-    if (!finite) *S.status = 1;
+    if (!finite) *S.status |= 1;
     if (write_j) {
       double* dst = (mode == TSBZ_FIN_J0MINUS) ? S.J0m : (mode == TSBZ_FIN_J0PLUS ? S.J : S.J + 3LL * (step + 1));
       for (int ax = 0; ax < 3; ++ax) dst[ax] = J[ax];

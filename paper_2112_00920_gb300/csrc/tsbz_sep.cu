@@ -1,0 +1,70 @@
+// Launchers of the single-precision fused stage and projection kernels.
+#include "tsbz_internal.h"
+#include "tsbz_sep.cuh"
+
+bool sep_supported(const CellDev& c) {
+  const int n12 = c.n1 * c.n2;
+  return c.nd == ZM_ND && n12 <= 256 && (c.n3 == 8 || c.n3 == 16) && c.n_atoms <= SEP_NA;
+}
+
+static inline unsigned sep_threads(const CellDev& c) { return (unsigned)(((c.n1 * c.n2 + 31) / 32) * 32); }
+
+void launch_bra_sep(const LaunchSet& L, const void* src, void* out, int with_d, int use_obs, void* stream) {
+  if (L.n_units == 0 || !L.cell.use_proj) return;
+  const unsigned grid = (unsigned)L.n_units * (unsigned)L.cell.n_bands;
+  const unsigned thr = sep_threads(L.cell);
+  cudaStream_t st = (cudaStream_t)stream;
+  const float2* s = (const float2*)src;
+  float2* o = (float2*)out;
+  if (L.cell.n3 == 16) {
+    if (with_d)
+      k_bra_sep<16, 1><<<grid, thr, 0, st>>>(L, s, o, use_obs);
+    else
+      k_bra_sep<16, 0><<<grid, thr, 0, st>>>(L, s, o, use_obs);
+  } else {
+    if (with_d)
+      k_bra_sep<8, 1><<<grid, thr, 0, st>>>(L, s, o, use_obs);
+    else
+      k_bra_sep<8, 0><<<grid, thr, 0, st>>>(L, s, o, use_obs);
+  }
+}
+
+template <int N>
+static void launch_stage_bulk(const LaunchSet& L, const void* tin, void* tout, void* psi, void* P, void* Pa, int m,
+                              cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    size_t most = 0;
+    for (int k = 1; k <= 4; ++k) most = sep_bulk_smem(N, k) > most ? sep_bulk_smem(N, k) : most;
+    cudaFuncSetAttribute(k_stage_bulk<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
+    attr = true;
+  }
+  const unsigned grid = (unsigned)L.n_units * (unsigned)L.cell.n_bands;
+  const size_t dyn = sep_bulk_smem(N, m);
+  k_stage_bulk<N><<<grid, N * N, dyn, st>>>(L, (const float2*)tin, (float2*)tout, (float2*)psi, (float2*)P,
+                                            (float2*)Pa, m);
+}
+
+bool launch_stage_sep(const LaunchSet& L, const void* tin, void* tout, void* psi, void* P, void* Pa, int m,
+                      void* stream) {
+  if (L.n_units == 0) return false;
+  const CellDev& c = L.cell;
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool next = L.ph_next != nullptr;
+  if (next && c.n1 == 16 && c.n2 == 16 && c.n3 == 16) {
+    launch_stage_bulk<16>(L, tin, tout, psi, P, Pa, m, st);
+    return true;
+  }
+  if (next && c.n1 == 8 && c.n2 == 8 && c.n3 == 8) {
+    launch_stage_bulk<8>(L, tin, tout, psi, P, Pa, m, st);
+    return true;
+  }
+  const unsigned grid = (unsigned)L.n_units * (unsigned)c.n_bands;
+  const unsigned thr = sep_threads(c);
+  const size_t pad = (size_t)(c.n1 + 2 * ZM_ND) * (c.n2 + 2 * ZM_ND) * sizeof(float2);
+  if (c.n3 == 16)
+    k_stage_sep<16><<<grid, thr, pad, st>>>(L, (const float2*)tin, (float2*)tout, (float2*)psi, (float2*)P, m);
+  else
+    k_stage_sep<8><<<grid, thr, pad, st>>>(L, (const float2*)tin, (float2*)tout, (float2*)psi, (float2*)P, m);
+  return false;
+}

@@ -24,6 +24,7 @@
 #include <stdint.h>
 
 #include "tsbz_internal.h"
+#include "tsbz_zmarch.cuh"
 
 #define TC_W_PITCH 72      // bf16 per Wt row
 #define TC_D_PITCH 33      // floats per row of the final bra combination
@@ -383,19 +384,8 @@ __global__ void __launch_bounds__(256, 2) k_ket_w(LaunchSet L, const float2* __r
 }
 
 
-// Periodic plane with a halo of ND points on each side in x and y: entry
-// (iy + ND) * (n1 + 2 ND) + ix + ND holds t(ix, iy); the halo holds the
-// periodic images, so every in-plane neighbour of the star stencil is a
-// load at a constant offset from the thread's own entry.
-__device__ __forceinline__ void zpad_store(float2* pl, int n1, int n2, int ix, int iy, float2 v) {
-  constexpr int ND = TC_ND;
-  const int W = n1 + 2 * ND;
-  pl[(iy + ND) * W + ix + ND] = v;
-  if (ix < ND) pl[(iy + ND) * W + ix + n1 + ND] = v;
-  if (ix >= n1 - ND) pl[(iy + ND) * W + ix - n1 + ND] = v;
-  if (iy < ND) pl[(iy + n2 + ND) * W + ix + ND] = v;
-  if (iy >= n2 - ND) pl[(iy - n2 + ND) * W + ix + ND] = v;
-}
+
+
 // ----------------------------------------------------------------------------
 // Taylor stage m, 2.5-D z-march for float orbitals with a compile-time grid
 // depth NZ (the z loop is fully unrolled, so the register queue of the 2 ND + 1
@@ -403,8 +393,6 @@ __device__ __forceinline__ void zpad_store(float2* pl, int n1, int n2, int ix, i
 // One CTA per (band, unit), one thread per (x, y) column (n1 n2 <= 256).
 //   t_m = (-i dt/m)[h_loc t + V], psi accumulation as in k_stage.
 // ----------------------------------------------------------------------------
-__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-
 template <int NZ>
 __global__ void __launch_bounds__(256, 4) k_stage_zf(LaunchSet L, const float2* __restrict__ tin,
                                                      float2* __restrict__ tout, float2* __restrict__ psi,

@@ -63,6 +63,60 @@ def test_parity_fp32_tc_small(case):
     print(f"fp32_tc {case}:", errs)
 
 
+FP32_CASES = {
+    # fused z-march stage, depth 8
+    "tiny8": lambda: (_tiny_pair(), (2, 2, 1), (0.25, 0.5, 0.0), 0.08, W.Kick(k0=0.01)),
+    # fused stage, depth 16, n1 != n2, non-grid atoms, 120 columns (last warp partly idle), pulse
+    "ragged16": lambda: (W.cell_tiny(atoms="offgrid", n=(10, 12, 16), a=(7.0, 8.0, 9.0), n_bands=3), (3, 1, 1),
+                         (0.1, 0.2, 0.3), 0.05,
+                         W.Pulse(e0=0.05, omega0=0.3, t_pulse=0.8, direction=(0.3, 0.4, 0.866))),
+    # fused stage without projectors
+    "free16": lambda: (W.free_electron(W.cell_tiny(n=(12, 12, 16), a=(7.0, 7.0, 9.0), n_bands=2)), (2, 1, 1),
+                       (0.5, 0.0, 0.25), 0.08, W.Kick(k0=0.02)),
+    # generic point-parallel kernels (depth 14)
+    "ragged14": lambda: (W.cell_tiny(atoms="offgrid", n=(10, 12, 14), a=(7.0, 8.0, 9.0), n_bands=3), (5, 1, 1),
+                         (0.1, 0.2, 0.3), 0.05,
+                         W.Pulse(e0=0.05, omega0=0.3, t_pulse=0.8, direction=(0.3, 0.4, 0.866))),
+}
+
+
+@pytest.mark.parametrize("case", sorted(FP32_CASES))
+def test_parity_fp32_small(case):
+    """Single-precision mode against the oracle, 6 steps: the fused stage with the
+    factorised projector contractions (depths 8 and 16, ragged columns, no
+    projectors) and the generic kernels."""
+    cell, mp, shift, dt, field = FP32_CASES[case]()
+    subs = [random_subsim(cell, mp, shift, dt, 6, field, seed=21)]
+    _, g = gpu_run(cell, subs, precision="fp32")
+    o = oracle_run(cell, subs[0])
+    errs = compare(g[0], o, 1e-4, 1e-5, 1e-5)
+    print(f"fp32 {case}:", errs)
+
+
+@pytest.mark.parametrize("precision,n,per_step", [("fp32", (8, 8, 8), 16), ("fp32", (10, 12, 14), 21),
+                                                  ("fp32_tc", (8, 8, 8), 25), ("fp64", (8, 8, 8), 21)])
+def test_kernel_launches_per_step(precision, n, per_step):
+    """Which kernel sequence a step runs (after the first): the fused single-precision
+    stage takes field + 4 stages + observation + finalize + 9 v_Hxc launches (stage 4
+    leaves the projections of the next step and of the current); the generic and
+    FP64 paths take a projection before each of the 4 stages and one for the
+    current; the tensor-core mode adds a ket launch before each stage."""
+    from paper_2112_00920_gb300 import Propagator, shifted_kpoints
+    cell = W.cell_tiny(atoms="pair", n=n, a=(6.0, 6.0, 6.0), n_bands=4)
+    s = random_subsim(cell, (1, 1, 1), (0.25, 0.25, 0.25), 0.08, 4, W.Kick(k0=0.01), seed=5)
+    P = Propagator(precision)
+    cid = P.add_cell_spec(cell)
+    sid = P.add_subsim(cid, shifted_kpoints(cell.a, s["mp"], s["shift"]), s["dt"], 4)
+    P.load_ground_state(sid, s["psi"])
+    P.set_kick(sid, 0.01, (1.0, 0.0, 0.0))
+    P.set_graphs(False)
+    P.propagate(1)
+    before = P.launches()
+    P.propagate(2)
+    assert P.launches() - before == 2 * per_step
+    P.close()
+
+
 def test_tc_mode_rejects_unsupported_cells():
     from paper_2112_00920_gb300 import Propagator, TsbzError
     P = Propagator("fp32_tc")
@@ -287,7 +341,7 @@ def test_eps_error_vs_oracle():
     assert errs["fp32"] <= 1e-4
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32_tc"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_tc"])
 def test_graph_replay_bitwise(precision):
     """Steps replayed from the captured CUDA graph equal direct launches bit for bit."""
     from paper_2112_00920_gb300 import Propagator, shifted_kpoints
