@@ -1,0 +1,518 @@
+// Taylor stage on 16^3 grids with the factorised projector contractions on
+// tensor cores (three-product TF32 mma.sync, FP32 accumulate).
+//
+// Per (unit, band) CTA, with C_{a,t}(r) = pn F^a_x F^a_y F^a_z w_t as in the
+// header of the z-march kernels:
+//   ket   conj(V_NL t)(col, z) = sum_q A[col][q] Z_q(z): the z dependence is a
+//         GEMM over q = (atom, {F_z, d_z F_z}) with the column coefficients
+//         A[col][(a,0)] = F_y (G00 + d_y G10), A[col][(a,1)] = F_y G01,
+//         G00 = F_x (conj W_s + d_x conj W_px), G10 = F_x conj W_py,
+//         G01 = F_x conj W_pz, W = pn E P (x tables first, then y).
+//   bra   monomial sums M_a(i,j,k) = sum_r F_x F_y F_z d_x^i d_y^j d_z^k u(r)
+//         in three contractions: z as a GEMM S[col][(a,k)] = sum_z u Z_{a,k},
+//         then x per (a, k, iy) row, then y per (a, i, j, k) output.
+//         P_{a,t} = dV pn M_a(w_t) with w_t = 000, 100, 010, 001 (s, p_x, p_y,
+//         p_z); the current needs the second-order sums as well.
+// Three-product TF32: x = x_hi + x_lo with x_hi = tf32(x), x_lo = tf32(x -
+// x_hi) (round to nearest); A B ~ A_lo B_hi + A_hi B_lo + A_hi B_hi, an
+// error of order 2^-21 relative per product, accumulated in FP32.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tsbz_sep.cuh"
+
+#define FS_N 16
+#define FS_NP 256          // columns (threads)
+#define FS_NPTS 4096
+#define FS_PU 260          // plane pitch of ubuf in float2 (bank-conflict-free fragment stores)
+#define FS_BKP 36          // row pitch of the ket B matrix in uint2
+
+__device__ __forceinline__ uint32_t fs_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void fs_split(float x, uint32_t& hi, uint32_t& lo) {
+  hi = fs_tf32(x);
+  lo = fs_tf32(x - __uint_as_float(hi));
+}
+
+__device__ __forceinline__ uint2 fs_split2(float x) {
+  uint2 r;
+  fs_split(x, r.x, r.y);
+  return r;
+}
+
+__device__ __forceinline__ void fs_mma(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// d += A B, A = ah + al, B = (b.x hi, b.y lo) for the two B registers
+__device__ __forceinline__ void fs_mma3(float (&d)[4], const uint32_t (&ah)[4], const uint32_t (&al)[4], uint2 b0,
+                                        uint2 b1) {
+  fs_mma(d, al, b0.x, b1.x);
+  fs_mma(d, ah, b0.y, b1.y);
+  fs_mma(d, ah, b0.x, b1.x);
+}
+
+struct FsSmem {
+  float2 tbuf[FS_NPTS];              // band of t_{m-1}; after the march: B_z
+  float2 ubuf[FS_N * FS_PU];         // V_NL per plane (ket), then u; then the z sums S
+  uint2 bk[32 * FS_BKP];             // ket B matrix (hi, lo)
+  float4 zt[SEP_NA * FS_N];          // (Re F_z, Im F_z, d_z, 0) per atom and plane
+  float4 colt[SEP_NA * 2 * FS_N];    // x and y factors (Re F, Im F, d, 0)
+  float2 gt[SEP_NA * 3 * FS_N];      // ket column tables G00, G10, G01 per atom and ix
+  float2 wt[SEP_NP];                 // pn E P of the band
+  float2 mres[SEP_NA * 10];          // monomial sums of one projection pass
+  unsigned long long mbar;
+};
+
+// z factors of one phase table
+__device__ __forceinline__ void fs_load_z(float4* zt, const CellDev& c, const float2* ph) {
+  const int nm = c.nmax;
+  for (int i = threadIdx.x; i < SEP_NA * FS_N; i += blockDim.x) {
+    const int a = i / FS_N, z = i - a * FS_N;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (a < c.n_atoms) {
+      const int idx = (a * 3 + 2) * nm + z;
+      const float g = c.g1f[idx];
+      const float2 p = ph[idx];
+      v = make_float4(g * p.x, g * p.y, c.d1f[idx], 0.f);
+    }
+    zt[i] = v;
+  }
+}
+
+// monomial index of d_x^i d_y^j d_z^k (i + j + k <= 2) in the order
+// 000, 100, 010, 001, 200, 110, 101, 020, 011, 002
+__device__ __forceinline__ int fs_mono(int i, int j, int k) {
+  const int deg = i + j + k;
+  if (deg == 0) return 0;
+  if (deg == 1) return i ? 1 : (j ? 2 : 3);
+  if (i == 2) return 4;
+  if (i == 1) return j ? 5 : 6;
+  if (j == 2) return 7;
+  return j ? 8 : 9;
+}
+
+// ----------------------------------------------------------------------------
+// ket: ubuf[z][col] = conj(V_NL t)(col, z) for the warp's 32 columns
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ void fs_ket(FsSmem& sm, const CellDev& c) {
+  const int tid = threadIdx.x;
+  // column tables G00, G10, G01 (conj W) and the B matrix B[k][n], k < 16: Re rows,
+  // k >= 16: Im rows of q = (a, w); n = 2 z + c
+  for (int i = tid; i < SEP_NA * FS_N; i += blockDim.x) {
+    const int a = i / FS_N, ix = i - a * FS_N;
+    const float4 fx = sm.colt[(2 * a) * FS_N + ix];
+    const float2 F = make_float2(fx.x, fx.y);
+    const float2 ws = sm.wt[4 * a], wx = sm.wt[4 * a + 1], wy = sm.wt[4 * a + 2], wz = sm.wt[4 * a + 3];
+    const float2 q0 = make_float2(ws.x + fx.z * wx.x, -(ws.y + fx.z * wx.y));
+    sm.gt[(a * 3 + 0) * FS_N + ix] = sep_cmul(F, q0);
+    sm.gt[(a * 3 + 1) * FS_N + ix] = sep_cmul(F, make_float2(wy.x, -wy.y));
+    sm.gt[(a * 3 + 2) * FS_N + ix] = sep_cmul(F, make_float2(wz.x, -wz.y));
+  }
+  for (int i = tid; i < 32 * 2 * FS_N; i += blockDim.x) {
+    const int k = i / (2 * FS_N), n = i - k * 2 * FS_N;
+    const int q = k & 15, z = n >> 1, cc = n & 1;
+    const float4 f = sm.zt[(q >> 1) * FS_N + z];
+    const float s = (q & 1) ? f.z : 1.f;
+    const float zr = s * f.x, zi = s * f.y;
+    const float v = (k < 16) ? (cc ? zi : zr) : (cc ? zr : -zi);
+    sm.bk[k * FS_BKP + n] = fs_split2(v);
+  }
+  __syncthreads();
+  const int lane = tid & 31, warp = tid >> 5, g = lane >> 2, t4 = lane & 3;
+  // A fragments of both m-tiles: rows = columns 32 warp + 16 mt + g (+8), k = 8 ks + t4 (+4)
+  uint32_t ah[2][4][4], al[2][4][4];
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt) {
+    const int iyc = 2 * warp + mt;
+    float re[2][4], im[2][4];   // [column A/B][q index i: q = t4 + 4 i]
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int q = t4 + 4 * i, a = q >> 1;
+      const float4 fy = sm.colt[(2 * a + 1) * FS_N + iyc];
+      const float2 F = make_float2(fy.x, fy.y);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int ixc = g + 8 * h;
+        float2 v;
+        if (q & 1) {
+          v = sep_cmul(F, sm.gt[(a * 3 + 2) * FS_N + ixc]);
+        } else {
+          const float2 g0 = sm.gt[(a * 3 + 0) * FS_N + ixc], g1 = sm.gt[(a * 3 + 1) * FS_N + ixc];
+          v = sep_cmul(F, make_float2(g0.x + fy.z * g1.x, g0.y + fy.z * g1.y));
+        }
+        re[h][i] = v.x;
+        im[h][i] = v.y;
+      }
+    }
+    // ks 0, 1: Re of q = t4 + 8 ks (+4); ks 2, 3: Im
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) {
+      const int i0 = 2 * (ks & 1);
+      const float(&src)[2][4] = (ks < 2) ? re : im;
+      fs_split(src[0][i0], ah[mt][ks][0], al[mt][ks][0]);
+      fs_split(src[1][i0], ah[mt][ks][1], al[mt][ks][1]);
+      fs_split(src[0][i0 + 1], ah[mt][ks][2], al[mt][ks][2]);
+      fs_split(src[1][i0 + 1], ah[mt][ks][3], al[mt][ks][3]);
+    }
+  }
+#pragma unroll
+  for (int nt = 0; nt < (2 * FS_N) / 8; ++nt) {
+    float d[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) {
+      const uint2 b0 = sm.bk[(8 * ks + t4) * FS_BKP + 8 * nt + g];
+      const uint2 b1 = sm.bk[(8 * ks + t4 + 4) * FS_BKP + 8 * nt + g];
+      fs_mma3(d[0], ah[0][ks], al[0][ks], b0, b1);
+      fs_mma3(d[1], ah[1][ks], al[1][ks], b0, b1);
+    }
+    const int z = 4 * nt + t4;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+      const int cA = 32 * warp + 16 * mt + g;
+      sm.ubuf[z * FS_PU + cA] = make_float2(d[mt][0], d[mt][1]);
+      sm.ubuf[z * FS_PU + cA + 8] = make_float2(d[mt][2], d[mt][3]);
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Projection pass: monomial sums up to degree D of the atoms covered by the
+// z-weights q' = q0 .. q0 + NQ - 1 (q' = (D + 1) a + k, k = power of d_z),
+// from the split A fragments of u (ah/al) and the tables zt / colt of the
+// pass.  Leaves mres[a_local * NM + mono] (NM = 4 for D = 1, 10 for D = 2).
+// ----------------------------------------------------------------------------
+template <int D, int NQ>
+__device__ __forceinline__ void fs_project_pass(FsSmem& sm, int q0, const uint32_t (&ah)[2][4][4],
+                                                const uint32_t (&al)[2][4][4]) {
+  constexpr int NPR = 2 * NQ;          // real n of the pass
+  constexpr int BZP = NPR + 4;         // B_z row pitch (uint2)
+  constexpr int NM = D == 1 ? 4 : 10;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, g = lane >> 2, t4 = lane & 3;
+  uint2* bz = reinterpret_cast<uint2*>(sm.tbuf);
+  float2* sbuf = sm.ubuf;                                      // [q'][iy][ix ^ iy]
+  // B_z[k][n], k = 2 z + c (component of u), n = 2 q' + c' (component of S)
+  for (int i = tid; i < 32 * NPR; i += blockDim.x) {
+    const int k = i / NPR, n = i - k * NPR;
+    const int z = k >> 1, cu = k & 1, qq = q0 + (n >> 1), cs = n & 1;
+    const int a = qq / (D + 1), kz = qq - a * (D + 1);
+    const float4 f = sm.zt[a * FS_N + z];
+    const float s = kz == 0 ? 1.f : (kz == 1 ? f.z : f.z * f.z);
+    const float zr = s * f.x, zi = s * f.y;
+    const float v = cs == 0 ? (cu == 0 ? zr : -zi) : (cu == 0 ? zi : zr);
+    bz[k * BZP + n] = fs_split2(v);
+  }
+  __syncthreads();
+  // z contraction on tensor cores: S[col][q'] for the warp's columns
+#pragma unroll
+  for (int nt = 0; nt < NPR / 8; ++nt) {
+    float d[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) {
+      const uint2 b0 = bz[(8 * ks + t4) * BZP + 8 * nt + g];
+      const uint2 b1 = bz[(8 * ks + t4 + 4) * BZP + 8 * nt + g];
+      fs_mma3(d[0], ah[0][ks], al[0][ks], b0, b1);
+      fs_mma3(d[1], ah[1][ks], al[1][ks], b0, b1);
+    }
+    const int ql = 4 * nt + t4;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+      const int iyc = 2 * warp + mt;
+      sbuf[ql * FS_NP + iyc * FS_N + (g ^ iyc)] = make_float2(d[mt][0], d[mt][1]);
+      sbuf[ql * FS_NP + iyc * FS_N + ((g + 8) ^ iyc)] = make_float2(d[mt][2], d[mt][3]);
+    }
+  }
+  __syncthreads();
+  // x contraction per row (q', iy): R_i = sum_ix F_x d_x^i S, i <= D - k; then the
+  // y contraction M_a(i, j, k) = sum_iy F_y d_y^j R_i over the 16 lanes of the
+  // half-warp that holds the rows iy = 0..15 of one q' (fixed-order shuffles).
+  constexpr int NR = NQ * FS_N;
+  for (int r0 = 0; r0 < NR; r0 += FS_NP) {
+    const int r = r0 + tid;
+    const bool live = r < NR;
+    const int ql = live ? (r >> 4) : 0, iyr = r & 15;
+    const int qq = q0 + ql, a = qq / (D + 1), kz = qq - a * (D + 1);
+    float2 R0 = make_float2(0.f, 0.f), R1 = R0, R2 = R0;
+    if (live) {
+#pragma unroll 4
+      for (int ixr = 0; ixr < FS_N; ++ixr) {
+        const float2 s = sbuf[ql * FS_NP + iyr * FS_N + (ixr ^ iyr)];
+        const float4 fx = sm.colt[(2 * a) * FS_N + ixr];
+        const float2 p = sep_cmul(make_float2(fx.x, fx.y), s);
+        R0.x += p.x;
+        R0.y += p.y;
+        if (D - kz >= 1) {
+          const float2 pd = make_float2(fx.z * p.x, fx.z * p.y);
+          R1.x += pd.x;
+          R1.y += pd.y;
+          if (D == 2 && kz == 0) {
+            R2.x = fmaf(fx.z, pd.x, R2.x);
+            R2.y = fmaf(fx.z, pd.y, R2.y);
+          }
+        }
+      }
+    }
+    // y weights of this row: F_y d_y^j
+    const float4 fy = sm.colt[(2 * a + 1) * FS_N + iyr];
+    const float2 Fy = make_float2(fy.x, fy.y), Fyd = make_float2(fy.z * fy.x, fy.z * fy.y);
+    // contributions, in the order of the monomials this row feeds:
+    //   D = 1, k = 0: 000 (F R0), 100 (F R1), 010 (F d R0);  k = 1: 001 (F R0)
+    //   D = 2, k = 0: 000, 100, 010, 200 (F R2), 110 (F d R1), 020 (F d^2 R0)
+    //          k = 1: 001, 101 (F R1), 011 (F d R0);  k = 2: 002
+    constexpr int NC = D == 1 ? 3 : 6;
+    float2 v[NC];
+    v[0] = sep_cmul(Fy, R0);
+    v[1] = sep_cmul(Fy, R1);
+    v[2] = sep_cmul(Fyd, R0);
+    if (D == 2) {
+      v[3 % NC] = sep_cmul(Fy, R2);
+      v[4 % NC] = sep_cmul(Fyd, R1);
+      v[5 % NC] = sep_cmul(make_float2(fy.z * Fyd.x, fy.z * Fyd.y), R0);
+    }
+#pragma unroll
+    for (int off = 1; off < 16; off <<= 1)
+#pragma unroll
+      for (int e = 0; e < NC; ++e) {
+        v[e].x += __shfl_xor_sync(0xffffffffu, v[e].x, off);
+        v[e].y += __shfl_xor_sync(0xffffffffu, v[e].y, off);
+      }
+    if (live && iyr == 0) {
+      float2* M = sm.mres + (a - q0 / (D + 1)) * NM;
+      if (D == 1) {
+        if (kz == 0) {
+          M[0] = v[0];
+          M[1] = v[1];
+          M[2] = v[2];
+        } else {
+          M[3] = v[0];
+        }
+      } else {
+        if (kz == 0) {
+          M[0] = v[0];
+          M[1] = v[1];
+          M[2] = v[2];
+          M[4] = v[3 % NC];
+          M[5] = v[4 % NC];
+          M[7] = v[5 % NC];
+        } else if (kz == 1) {
+          M[3] = v[0];
+          M[6] = v[1];
+          M[8] = v[2];
+        } else {
+          M[9] = v[0];
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// A fragments (split) of u = ubuf[z][col] for the warp's columns, k = 2 z + c
+__device__ __forceinline__ void fs_load_u(const FsSmem& sm, uint32_t (&ah)[2][4][4], uint32_t (&al)[2][4][4]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t4 = lane & 3;
+  const float* ub = reinterpret_cast<const float*>(sm.ubuf);
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt) {
+    const int cA = 32 * warp + 16 * mt + g;
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) {
+      const int k0 = 8 * ks + t4, k1 = k0 + 4;
+      const int z0 = k0 >> 1, c0 = k0 & 1, z1 = k1 >> 1, c1 = k1 & 1;
+      fs_split(ub[2 * (z0 * FS_PU + cA) + c0], ah[mt][ks][0], al[mt][ks][0]);
+      fs_split(ub[2 * (z0 * FS_PU + cA + 8) + c0], ah[mt][ks][1], al[mt][ks][1]);
+      fs_split(ub[2 * (z1 * FS_PU + cA) + c1], ah[mt][ks][2], al[mt][ks][2]);
+      fs_split(ub[2 * (z1 * FS_PU + cA + 8) + c1], ah[mt][ks][3], al[mt][ks][3]);
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Taylor stage m on a 16^3 grid, one CTA per (unit, band), one thread per
+// (x, y) column; same arithmetic contract as k_stage_bulk: t_m, the psi
+// accumulation, the projections of t_m (m < 4) or, at m = 4, those of
+// psi(t_{n+1}) for the next step (P) and for the current (Pa).
+// ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(FS_NP, 2) k_stage_fused(LaunchSet L, const float2* __restrict__ tin,
+                                                          float2* __restrict__ tout, float2* __restrict__ psi,
+                                                          float2* __restrict__ P, float2* __restrict__ Pa, int m) {
+  constexpr int ND = ZM_ND, N = FS_N, NP = FS_NP;
+  extern __shared__ __align__(128) unsigned char fs_raw[];
+  FsSmem& sm = *reinterpret_cast<FsSmem*>(fs_raw);
+  const CellDev& c = L.cell;
+  const int b = blockIdx.x % c.n_bands;
+  const int u = L.unit_ids[blockIdx.x / c.n_bands];
+  const UnitDev U = L.units[u];
+  const SubDev S = L.subs[U.sub];
+  const int tid = threadIdx.x, col = tid;
+  const int ix = col & (N - 1), iy = col / N;
+  const bool proj = c.use_proj != 0;
+  const float2* ph = (const float2*)L.ph_half + (long long)u * L.ph_stride;
+  float2* Pu = P + U.p_off + (long long)b * c.n_proj;
+  const long long base = U.psi_off + (long long)b * FS_NPTS;
+  const float2 zero = make_float2(0.f, 0.f);
+  const uint32_t bar = bk_smem(&sm.mbar);
+  if (tid == 0) bk_mbar_init(bar, 1);
+  __syncthreads();
+  if (tid == 0) {
+    bk_mbar_expect_tx(bar, FS_NPTS * (uint32_t)sizeof(float2));
+    bk_copy_g2s(bk_smem(sm.tbuf), tin + base, FS_NPTS * sizeof(float2), bar);
+  }
+  // psi of the column in registers (m >= 2), in flight while the ket runs
+  float2 pq[N];
+#pragma unroll
+  for (int z = 0; z < N; ++z) pq[z] = m >= 2 ? psi[base + z * NP + col] : zero;
+  if (proj) {
+    fs_load_z(sm.zt, c, ph);
+    sep_load_cols<N>(sm.colt, c, ph);
+    for (int j = tid; j < SEP_NP; j += blockDim.x) {
+      float2 w = zero;
+      if (j < c.n_proj) {
+        const float2 p = Pu[j];
+        const float e = c.wkbf[j];
+        w = make_float2(e * p.x, e * p.y);
+      }
+      sm.wt[j] = w;
+    }
+  }
+  __syncthreads();
+  if (proj) {
+    fs_ket(sm, c);
+  } else {
+#pragma unroll
+    for (int z = 0; z < N; ++z) sm.ubuf[z * FS_PU + col] = zero;
+  }
+  const float* qt = reinterpret_cast<const float*>(L.qt_half) + 4 * u;
+  const float q0 = qt[0], q1 = qt[1], q2 = qt[2];
+  const float dg0 = c.hlapf[0][0] + c.hlapf[1][0] + c.hlapf[2][0] + qt[3];
+  const float hdt = (float)S.dt / (float)m;
+  const float* veff = reinterpret_cast<const float*>(S.veff) + col;
+  float e_cur = veff[0];
+  const bool ok = bk_mbar_wait(bar, 0, BK_WAIT_POLLS);
+  if (!__syncthreads_and(ok)) {
+    if (tid == 0) {
+      atomicOr(S.status, BK_STATUS_TIMEOUT);
+      bk_mbar_wait(bar, 0, BK_WAIT_POLLS);
+    }
+    return;
+  }
+  const float2* tb = sm.tbuf;
+  const float2* cz = tb + col;
+  const float2* xp[ND];
+  const float2* xm[ND];
+  const float2* yp[ND];
+  const float2* ym[ND];
+#pragma unroll
+  for (int mm = 1; mm <= ND; ++mm) {
+    xp[mm - 1] = tb + iy * N + ((ix + mm) & (N - 1));
+    xm[mm - 1] = tb + iy * N + ((ix - mm) & (N - 1));
+    yp[mm - 1] = tb + ((iy + mm) & (N - 1)) * N + ix;
+    ym[mm - 1] = tb + ((iy - mm) & (N - 1)) * N + ix;
+  }
+  const float2 neg1 = make_float2(-1.f, -1.f);
+  float2 qv[N + 2 * ND];
+#pragma unroll
+  for (int k = 0; k < 2 * ND; ++k) qv[k] = cz[((k - ND + N) & (N - 1)) * NP];
+#pragma unroll
+  for (int z = 0; z < N; ++z) {
+    qv[z + 2 * ND] = cz[((z + ND) & (N - 1)) * NP];
+    const float e_nxt = (z + 1 < N) ? veff[(z + 1) * NP] : 0.f;
+    const float2 ce = qv[z + ND];
+    const float dg = dg0 + e_cur;
+    float2 h = __fmul2_rn(make_float2(dg, dg), ce);
+    float2 gx = zero, gy = zero, gz = zero;
+#pragma unroll
+    for (int mm = 1; mm <= ND; ++mm) {
+      const float2 xu = xp[mm - 1][z * NP], xd = xm[mm - 1][z * NP];
+      const float2 yu = yp[mm - 1][z * NP], yd = ym[mm - 1][z * NP];
+      const float2 zu = qv[z + ND + mm], zd = qv[z + ND - mm];
+      h = f2fma(c.hlap2[0][mm], __fadd2_rn(xu, xd), h);
+      h = f2fma(c.hlap2[1][mm], __fadd2_rn(yu, yd), h);
+      h = f2fma(c.hlap2[2][mm], __fadd2_rn(zu, zd), h);
+      gx = f2fma(c.gradw2[0][mm], f2fma(neg1, xd, xu), gx);
+      gy = f2fma(c.gradw2[1][mm], f2fma(neg1, yd, yu), gy);
+      gz = f2fma(c.gradw2[2][mm], f2fma(neg1, zd, zu), gz);
+    }
+    float2 qg = __fmul2_rn(make_float2(q0, q0), gx);
+    qg = f2fma(make_float2(q1, q1), gy, qg);
+    qg = f2fma(make_float2(q2, q2), gz, qg);
+    const float2 vq = sm.ubuf[z * FS_PU + col];   // conj(V_NL t)
+    const float hr = h.x + qg.y + vq.x;
+    const float hi = h.y - qg.x - vq.y;
+    const float2 t = make_float2(hdt * hi, -hdt * hr);
+    const long long idx = base + (long long)z * NP + col;
+    float2 uo = t;
+    if (m < 4) tout[idx] = t;
+    if (m == 2) {
+      psi[idx] = __fadd2_rn(pq[z], __fadd2_rn(ce, t));
+    } else if (m == 3) {
+      psi[idx] = __fadd2_rn(pq[z], t);
+    } else if (m == 4) {
+      uo = __fadd2_rn(pq[z], t);   // psi(t_{n+1})
+      psi[idx] = uo;
+    }
+    sm.ubuf[z * FS_PU + col] = uo;
+    e_cur = e_nxt;
+  }
+  if (!proj) return;
+  __syncthreads();
+  uint32_t ah[2][4][4], al[2][4][4];
+  fs_load_u(sm, ah, al);
+  __syncthreads();   // ubuf free for the z sums
+  if (m < 4) {
+    fs_project_pass<1, 2 * SEP_NA>(sm, 0, ah, al);
+    const int j = tid;
+    if (j < c.n_proj) {
+      const float2 M = sm.mres[(j >> 2) * 4 + (j & 3)];
+      const double sc = c.dv * (double)c.pnormf[j];
+      Pu[j] = make_float2((float)(sc * M.x), (float)(sc * M.y));
+    }
+    return;
+  }
+  // m = 4: projections of psi(t_{n+1}) for the next step, then for the current
+  const float2* phn = (const float2*)L.ph_next + (long long)u * L.ph_stride;
+  const float2* pho = (const float2*)L.ph_obs + (long long)u * L.ph_stride;
+  fs_load_z(sm.zt, c, phn);
+  sep_load_cols<N>(sm.colt, c, phn);
+  __syncthreads();
+  fs_project_pass<1, 2 * SEP_NA>(sm, 0, ah, al);
+  {
+    const int j = tid;
+    if (j < c.n_proj) {
+      const float2 M = sm.mres[(j >> 2) * 4 + (j & 3)];
+      const double sc = c.dv * (double)c.pnormf[j];
+      Pu[j] = make_float2((float)(sc * M.x), (float)(sc * M.y));
+    }
+  }
+  fs_load_z(sm.zt, c, pho);
+  sep_load_cols<N>(sm.colt, c, pho);
+  __syncthreads();
+  float2* Pab = Pa + U.pa_off + 4LL * b * c.n_proj;
+#pragma unroll 1
+  for (int half = 0; half < 2; ++half) {
+    fs_project_pass<2, 3 * SEP_NA / 2>(sm, half * (3 * SEP_NA / 2), ah, al);
+    // rows (a, c_x, c_y, c_z) of projector type t: monomials w_t and w_t + e_alpha
+    const int o = tid;
+    if (o < 4 * 4 * (SEP_NA / 2)) {
+      const int al_ = o >> 4, t = (o >> 2) & 3, s = o & 3;
+      const int a = half * (SEP_NA / 2) + al_;
+      const int j = 4 * a + t;
+      if (j < c.n_proj) {
+        int e[3] = {t == 1 ? 1 : 0, t == 2 ? 1 : 0, t == 3 ? 1 : 0};
+        if (s > 0) e[s - 1] += 1;
+        const float2 M = sm.mres[al_ * 10 + fs_mono(e[0], e[1], e[2])];
+        const double sc = c.dv * (double)c.pnormf[j];
+        Pab[4 * j + s] = make_float2((float)(sc * M.x), (float)(sc * M.y));
+      }
+    }
+    __syncthreads();
+  }
+}

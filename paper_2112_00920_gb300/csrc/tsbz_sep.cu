@@ -1,6 +1,7 @@
 // Launchers of the single-precision fused stage and projection kernels.
 #include "tsbz_internal.h"
 #include "tsbz_sep.cuh"
+#include "tsbz_fused.cuh"
 
 bool sep_supported(const CellDev& c) {
   const int n12 = c.n1 * c.n2;
@@ -52,7 +53,14 @@ bool launch_stage_sep(const LaunchSet& L, const void* tin, void* tout, void* psi
   cudaStream_t st = (cudaStream_t)stream;
   const bool next = L.ph_next != nullptr;
   if (next && c.n1 == 16 && c.n2 == 16 && c.n3 == 16) {
-    launch_stage_bulk<16>(L, tin, tout, psi, P, Pa, m, st);
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_stage_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(FsSmem));
+      attr = true;
+    }
+    const unsigned grid = (unsigned)L.n_units * (unsigned)c.n_bands;
+    k_stage_fused<<<grid, FS_NP, sizeof(FsSmem), st>>>(L, (const float2*)tin, (float2*)tout, (float2*)psi,
+                                                        (float2*)P, (float2*)Pa, m);
     return true;
   }
   if (next && c.n1 == 8 && c.n2 == 8 && c.n3 == 8) {

@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(256, 2) k_stage_sep(LaunchSet L, const float2*
                                                       float2* __restrict__ tout, float2* __restrict__ psi,
                                                       float2* __restrict__ P, int m) {
   constexpr int ND = ZM_ND;
-  extern __shared__ __align__(16) unsigned char sraw[];
+  extern __shared__ __align__(128) unsigned char sraw[];
   float2* plane = reinterpret_cast<float2*>(sraw);
   __shared__ float4 fzt[2 * SEP_NA * NZ];
   __shared__ float2 wt[SEP_NP];
@@ -475,7 +475,6 @@ __global__ void __launch_bounds__(256) k_bra_sep(LaunchSet L, const float2* __re
   const int col = threadIdx.x;
   const bool act = col < n12;
   const int ix = act ? col % n1 : 0, iy = act ? col / n1 : 0;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const float2* ph = (const float2*)(use_obs ? L.ph_obs : L.ph_half) + (long long)u * L.ph_stride;
   const float2 zero = make_float2(0.f, 0.f);
   sep_load_z<NZ, NW>(fzt, c, ph);
