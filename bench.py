@@ -163,8 +163,17 @@ def build_propagator(precision, n_steps_cap, device=0, n_subsims=64):
 # reduced workload (8 of the 64 subgrids, 8192 orbitals) and scaled by the
 # orbital count to the full workload.  Valid only for the kernel source it
 # was taken on: the SHA-1 of the kernel text is checked at run time.
-STAGE_TRAFFIC = {"kernel": "k_stage_zf", "sha1": "2afbe1ff13073b336cf76b75f65936eec571d70b",
-                 "bytes_per_launch_full": 8.87e9, "profile": "profiles/k_stage_zf_fp32tc_reduced8.md"}
+STAGE_TRAFFIC = {
+    "fp32": {"kernel": "k_stage_fused", "file": "tsbz_fused.cuh", "sha1": None, "bytes_per_launch_full": None,
+             "profile": "profiles/k_stage_fused_fp32_reduced8.md"},
+    "fp32_tc": {"kernel": "k_stage_zf", "file": "tsbz_tc.cuh", "sha1": "2afbe1ff13073b336cf76b75f65936eec571d70b",
+                "bytes_per_launch_full": 8.87e9, "profile": "profiles/k_stage_zf_fp32tc_reduced8.md"},
+}
+STAGE_KERNEL = {
+    "fp32": "k_stage_fused (z-march stencil + tensor-core projector contractions + Taylor accumulate)",
+    "fp32_tc": "k_stage_zf (z-march stencil + non-local term + Taylor accumulate)",
+    "fp64": "k_stage (stencil + ket + Taylor accumulate)",
+}
 
 
 def _kernel_sha1(path: str, name: str) -> str | None:
@@ -185,7 +194,7 @@ def eps_check(precision, device):
     small linear-response run (see the call site)."""
     import workloads as W
     from paper_2112_00920_gb300 import Propagator, shifted_kpoints
-    cell = W.cell_a_coarse(n=8)
+    cell = W.cell_a()
     n, dt, k0 = 600, 0.08, 0.005
     k = shifted_kpoints(cell.a, (2, 2, 2), (0.0, 0.0, 0.0))
     psi = W.plane_wave_orbitals(cell.a, cell.n, W.plane_wave_set(cell.n_bands), 8)
@@ -224,7 +233,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--precision", default="fp32_tc", choices=["fp32_tc", "fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_tc", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--subsims", type=int, default=64,
@@ -309,13 +318,13 @@ def main():
     stage_ms = fam["stage"] / n_stage
     bytes_launch = stage_bytes_per_launch(elem, n_orb, cell.n_pts)
     achieved = bytes_launch / (stage_ms / 1e3) / 1e9
-    kname = ("k_stage_zf (2.5-D stencil + non-local term + Taylor accumulate)"
-             if args.precision == "fp32_tc" else "k_stage (stencil + ket + Taylor accumulate)")
+    kname = STAGE_KERNEL[args.precision]
     traffic = None
-    if args.precision == "fp32_tc" and args.subsims == 64 and STAGE_TRAFFIC["sha1"]:
-        sha = _kernel_sha1(os.path.join(ROOT, "paper_2112_00920_gb300", "csrc", "tsbz_tc.cuh"), "k_stage_zf")
-        if sha == STAGE_TRAFFIC["sha1"]:
-            traffic = STAGE_TRAFFIC["bytes_per_launch_full"]
+    st = STAGE_TRAFFIC.get(args.precision)
+    if st and args.subsims == 64 and st["sha1"]:
+        sha = _kernel_sha1(os.path.join(ROOT, "paper_2112_00920_gb300", "csrc", st["file"]), st["kernel"])
+        if sha == st["sha1"]:
+            traffic = st["bytes_per_launch_full"]
     roof = {"kernel": kname, "bound": "hbm", "achieved": achieved,
             "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
             "algorithmic_bytes_per_launch": bytes_launch,
@@ -387,9 +396,12 @@ def main():
                "config": {"workload": WORKLOAD if args.subsims == 64 else f"reduced: {args.subsims} of " + WORKLOAD,
                           "n_subsims": len(run.subsims), "k_points": 64 * len(run.subsims),
                           "orbitals_per_gpu": n_orb, "grid": "16^3", "bands": 16, "dt": 0.08,
-                          "precision": {"fp32_tc": "fp32 stencil/Taylor, split-bf16x3 tensor-core projector "
-                                                   "GEMMs with fp32 accumulation, fp64 rho/J/Hartree",
-                                        "fp32": "fp32 stencil/Taylor/projectors (CUDA cores), fp64 rho/J/Hartree",
+                          "precision": {"fp32": "fp32 stencil/Taylor; projector contractions factorised per "
+                                                "axis, the z contractions as three-product TF32 tensor-core "
+                                                "GEMMs (mma.sync) with fp32 accumulation; fp64 rho/J/Hartree",
+                                        "fp32_tc": "fp32 stencil/Taylor; dense projector GEMMs as scaled "
+                                                   "split-FP16 three-product tensor-core products (mma.sync) "
+                                                   "with fp32 accumulation; fp64 rho/J/Hartree",
                                         "fp64": "fp64 throughout"}[args.precision],
                           "l2": "inputs larger than L2 (psi 2 GiB in fp32), no flush needed",
                           "parallelism": f"replica x{world} (independent shifts per GPU)"},
@@ -398,7 +410,7 @@ def main():
                "clocks": clk.summary(),
                "fp64_gpu": fp64,
                "eps_rel_err_vs_fp64": eps_err,
-               "eps_check": "cell A on 8^3 grid, MP 2^3, plane-wave start, kick 0.005 x, 600 steps, "
+               "eps_check": "cell A (16^3 grid), MP 2^3, plane-wave start, kick 0.005 x, 600 steps, "
                             "eps over 0.1-20 eV vs the FP64 GPU path (FP64 GPU vs oracle: err_J <= 1e-10)",
                "fp32_over_fp64": (value / world / fp64["value"]) if fp64 else None,
                "two_step_dJx_last": float(J_avg[-1, 0])}

@@ -516,3 +516,36 @@ __global__ void __launch_bounds__(FS_NP, 2) k_stage_fused(LaunchSet L, const flo
     __syncthreads();
   }
 }
+
+// ----------------------------------------------------------------------------
+// Projections P[u][b][j] of float orbitals on a 16^3 grid (q_half tables),
+// one CTA per (unit, band): the same tensor-core pass as the fused stage, so
+// the projections of a restored state equal those the stage leaves, bit for bit.
+// ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(FS_NP, 2) k_bra_fused(LaunchSet L, const float2* __restrict__ src,
+                                                        float2* __restrict__ P) {
+  extern __shared__ __align__(128) unsigned char fs_raw[];
+  FsSmem& sm = *reinterpret_cast<FsSmem*>(fs_raw);
+  const CellDev& c = L.cell;
+  const int b = blockIdx.x % c.n_bands;
+  const int u = L.unit_ids[blockIdx.x / c.n_bands];
+  const UnitDev U = L.units[u];
+  const int tid = threadIdx.x;
+  const float2* ph = (const float2*)L.ph_half + (long long)u * L.ph_stride;
+  const float2* sb = src + U.psi_off + (long long)b * FS_NPTS + tid;
+#pragma unroll
+  for (int z = 0; z < FS_N; ++z) sm.ubuf[z * FS_PU + tid] = sb[z * FS_NP];
+  fs_load_z(sm.zt, c, ph);
+  sep_load_cols<FS_N>(sm.colt, c, ph);
+  __syncthreads();
+  uint32_t ah[2][4][4], al[2][4][4];
+  fs_load_u(sm, ah, al);
+  __syncthreads();
+  fs_project_pass<1, 2 * SEP_NA>(sm, 0, ah, al);
+  const int j = tid;
+  if (j < c.n_proj) {
+    const float2 M = sm.mres[(j >> 2) * 4 + (j & 3)];
+    const double sc = c.dv * (double)c.pnormf[j];
+    P[U.p_off + (long long)b * c.n_proj + j] = make_float2((float)(sc * M.x), (float)(sc * M.y));
+  }
+}

@@ -13,6 +13,17 @@ static inline unsigned sep_threads(const CellDev& c) { return (unsigned)(((c.n1 
 void launch_bra_sep(const LaunchSet& L, const void* src, void* out, int with_d, int use_obs, void* stream) {
   if (L.n_units == 0 || !L.cell.use_proj) return;
   const unsigned grid = (unsigned)L.n_units * (unsigned)L.cell.n_bands;
+  const CellDev& c = L.cell;
+  if (!with_d && !use_obs && L.ph_next != nullptr && c.n1 == 16 && c.n2 == 16 && c.n3 == 16) {
+    // the projections the 16^3 fused stage leaves are formed by the same pass
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_bra_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(FsSmem));
+      attr = true;
+    }
+    k_bra_fused<<<grid, FS_NP, sizeof(FsSmem), (cudaStream_t)stream>>>(L, (const float2*)src, (float2*)out);
+    return;
+  }
   const unsigned thr = sep_threads(L.cell);
   cudaStream_t st = (cudaStream_t)stream;
   const float2* s = (const float2*)src;

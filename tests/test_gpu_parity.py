@@ -243,10 +243,14 @@ def test_two_step_average_gpu():
         compare(gi, oi, FP64_J_TOL, FP64_RHO_TOL)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_tc"])
-def test_checkpoint_restart_bitwise(precision):
-    """propagate(6) == propagate(3) + get_state/load_state + propagate(3), bit for bit."""
-    cell = _tiny_pair()
+@pytest.mark.parametrize("precision,n", [("fp64", 8), ("fp32", 8), ("fp32", 16), ("fp32_tc", 8), ("fp32_tc", 16)])
+def test_checkpoint_restart_bitwise(precision, n):
+    """propagate(6) == propagate(3) + get_state/load_state + propagate(3), bit for bit
+    (8^3 and 16^3 grids: each shape's own stage and projection kernels; the
+    16^3 cell is 10 bohr wide so that dt E_max of the FD kinetic stays inside
+    the Taylor-4 stability range, about 2.8)."""
+    side = 6.0 if n == 8 else 10.0
+    cell = W.cell_tiny(atoms="pair", n=(n, n, n), a=(side, side, side), n_bands=4)
     subs = [random_subsim(cell, (2, 1, 1), (0.5, 0.5, 0.5), 0.08, 6, W.Kick(k0=0.01), seed=6, tag=i) for i in range(2)]
     P1, g1 = gpu_run(cell, subs, precision=precision)
     P2, _ = gpu_run(cell, subs, precision=precision, steps=3)
@@ -339,6 +343,35 @@ def test_eps_error_vs_oracle():
     assert errs["fp64"] <= 1e-10
     assert errs["fp32_tc"] <= 1e-4
     assert errs["fp32"] <= 1e-4
+
+
+def test_eps_single_vs_fp64_gpu_16():
+    """eps(omega) over 0.1-20 eV of the single-precision paths on the 16^3 cell A
+    (the grid of the two-step workload, where the fused stage and the
+    tensor-core projections run) against the FP64 GPU path, which the tests
+    above pin to the oracle at err_J <= 1e-10.  MP 2^3, plane-wave start,
+    kick 0.005 x, 600 steps of dt = 0.08.  Bar: 1e-4."""
+    from paper_2112_00920_gb300 import Propagator, shifted_kpoints
+    cell = W.cell_a()
+    n, dt, k0 = 600, 0.08, 0.005
+    k = shifted_kpoints(cell.a, (2, 2, 2), (0.0, 0.0, 0.0))
+    psi = W.plane_wave_orbitals(cell.a, cell.n, W.plane_wave_set(cell.n_bands), 8)
+    om = np.linspace(0.1, 20.0, 400) / 27.211386245988
+    eps = {}
+    for prec in ("fp64", "fp32", "fp32_tc"):
+        P = Propagator(prec)
+        cid = P.add_cell_spec(cell)
+        sid = P.add_subsim(cid, k, dt, n)
+        P.load_ground_state(sid, psi)
+        P.set_kick(sid, k0, (1.0, 0.0, 0.0))
+        P.propagate(n)
+        J, j0 = P.current(sid)
+        P.close()
+        eps[prec] = _eps(J, j0, dt, k0, om)
+    errs = {p: analysis.err_eps(eps[p], eps["fp64"]) for p in ("fp32", "fp32_tc")}
+    print("err_eps vs fp64 GPU (16^3):", errs)
+    assert errs["fp32"] <= 1e-4
+    assert errs["fp32_tc"] <= 1e-4
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_tc"])
