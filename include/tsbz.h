@@ -47,9 +47,15 @@ extern "C" {
 /* Arithmetic of the propagation (a2-a5).  Density, current, Hartree and
  * the time integration of the observables are FP64 in every mode. */
 #define TSBZ_FP64 0          /* everything in double                          */
-#define TSBZ_FP32 1          /* stencil, Taylor and projectors in float       */
-#define TSBZ_FP32_TC 2       /* as FP32, projector contractions on tensor cores
-                                (split-BF16, three products, FP32 accumulate) */
+#define TSBZ_FP32 1          /* stencil, Taylor and projectors in float; on
+                                cells of at most 8 atoms with 16^3 grids the
+                                projector contractions are factorised per axis
+                                and their z contractions run on tensor cores
+                                (three-product TF32, FP32 accumulate), fused
+                                with the stencil in one kernel per stage      */
+#define TSBZ_FP32_TC 2       /* as FP32 with dense projector GEMMs on tensor
+                                cores in their own kernels (scaled split-FP16,
+                                three products, FP32 accumulate)              */
 
 #define TSBZ_HXC_SCF 0       /* v_Hxc[rho(t)] updated every step (Eq. 2)      */
 #define TSBZ_HXC_FROZEN 1    /* v_Hxc kept at its loaded value                */
