@@ -89,6 +89,12 @@ __device__ __forceinline__ void fs_load_z(float4* zt, const CellDev& c, const fl
   }
 }
 
+// complex product with explicit round-to-nearest operations (never contracted)
+__device__ __forceinline__ float2 fs_cmul_rn(float2 a, float2 b) {
+  return make_float2(__fsub_rn(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y)),
+                     __fadd_rn(__fmul_rn(a.x, b.y), __fmul_rn(a.y, b.x)));
+}
+
 // monomial index of d_x^i d_y^j d_z^k (i + j + k <= 2) in the order
 // 000, 100, 010, 001, 200, 110, 101, 020, 011, 002
 __device__ __forceinline__ int fs_mono(int i, int j, int k) {
@@ -241,49 +247,51 @@ __device__ __forceinline__ void fs_project_pass(FsSmem& sm, int q0, const uint32
     const bool live = r < NR;
     const int ql = live ? (r >> 4) : 0, iyr = r & 15;
     const int qq = q0 + ql, a = qq / (D + 1), kz = qq - a * (D + 1);
+    // explicit round-to-nearest operations (no contraction), so that the sums a
+    // D = 1 pass and a D = 2 pass have in common come out bit for bit the same
     float2 R0 = make_float2(0.f, 0.f), R1 = R0, R2 = R0;
     if (live) {
 #pragma unroll 4
       for (int ixr = 0; ixr < FS_N; ++ixr) {
         const float2 s = sbuf[ql * FS_NP + iyr * FS_N + (ixr ^ iyr)];
         const float4 fx = sm.colt[(2 * a) * FS_N + ixr];
-        const float2 p = sep_cmul(make_float2(fx.x, fx.y), s);
-        R0.x += p.x;
-        R0.y += p.y;
+        const float2 p = fs_cmul_rn(make_float2(fx.x, fx.y), s);
+        R0.x = __fadd_rn(R0.x, p.x);
+        R0.y = __fadd_rn(R0.y, p.y);
         if (D - kz >= 1) {
-          const float2 pd = make_float2(fx.z * p.x, fx.z * p.y);
-          R1.x += pd.x;
-          R1.y += pd.y;
+          const float2 pd = make_float2(__fmul_rn(fx.z, p.x), __fmul_rn(fx.z, p.y));
+          R1.x = __fadd_rn(R1.x, pd.x);
+          R1.y = __fadd_rn(R1.y, pd.y);
           if (D == 2 && kz == 0) {
-            R2.x = fmaf(fx.z, pd.x, R2.x);
-            R2.y = fmaf(fx.z, pd.y, R2.y);
+            R2.x = __fmaf_rn(fx.z, pd.x, R2.x);
+            R2.y = __fmaf_rn(fx.z, pd.y, R2.y);
           }
         }
       }
     }
     // y weights of this row: F_y d_y^j
     const float4 fy = sm.colt[(2 * a + 1) * FS_N + iyr];
-    const float2 Fy = make_float2(fy.x, fy.y), Fyd = make_float2(fy.z * fy.x, fy.z * fy.y);
+    const float2 Fy = make_float2(fy.x, fy.y), Fyd = make_float2(__fmul_rn(fy.z, fy.x), __fmul_rn(fy.z, fy.y));
     // contributions, in the order of the monomials this row feeds:
     //   D = 1, k = 0: 000 (F R0), 100 (F R1), 010 (F d R0);  k = 1: 001 (F R0)
     //   D = 2, k = 0: 000, 100, 010, 200 (F R2), 110 (F d R1), 020 (F d^2 R0)
     //          k = 1: 001, 101 (F R1), 011 (F d R0);  k = 2: 002
     constexpr int NC = D == 1 ? 3 : 6;
     float2 v[NC];
-    v[0] = sep_cmul(Fy, R0);
-    v[1] = sep_cmul(Fy, R1);
-    v[2] = sep_cmul(Fyd, R0);
+    v[0] = fs_cmul_rn(Fy, R0);
+    v[1] = fs_cmul_rn(Fy, R1);
+    v[2] = fs_cmul_rn(Fyd, R0);
     if (D == 2) {
-      v[3 % NC] = sep_cmul(Fy, R2);
-      v[4 % NC] = sep_cmul(Fyd, R1);
-      v[5 % NC] = sep_cmul(make_float2(fy.z * Fyd.x, fy.z * Fyd.y), R0);
+      v[3 % NC] = fs_cmul_rn(Fy, R2);
+      v[4 % NC] = fs_cmul_rn(Fyd, R1);
+      v[5 % NC] = fs_cmul_rn(make_float2(__fmul_rn(fy.z, Fyd.x), __fmul_rn(fy.z, Fyd.y)), R0);
     }
 #pragma unroll
     for (int off = 1; off < 16; off <<= 1)
 #pragma unroll
       for (int e = 0; e < NC; ++e) {
-        v[e].x += __shfl_xor_sync(0xffffffffu, v[e].x, off);
-        v[e].y += __shfl_xor_sync(0xffffffffu, v[e].y, off);
+        v[e].x = __fadd_rn(v[e].x, __shfl_xor_sync(0xffffffffu, v[e].x, off));
+        v[e].y = __fadd_rn(v[e].y, __shfl_xor_sync(0xffffffffu, v[e].y, off));
       }
     if (live && iyr == 0) {
       float2* M = sm.mres + (a - q0 / (D + 1)) * NM;
@@ -343,7 +351,8 @@ __device__ __forceinline__ void fs_load_u(const FsSmem& sm, uint32_t (&ah)[2][4]
 // ----------------------------------------------------------------------------
 __global__ void __launch_bounds__(FS_NP, 2) k_stage_fused(LaunchSet L, const float2* __restrict__ tin,
                                                           float2* __restrict__ tout, float2* __restrict__ psi,
-                                                          float2* __restrict__ P, float2* __restrict__ Pa, int m) {
+                                                          float2* __restrict__ P, float2* __restrict__ Pa, int m,
+                                                          int same_next) {
   constexpr int ND = ZM_ND, N = FS_N, NP = FS_NP;
   extern __shared__ __align__(128) unsigned char fs_raw[];
   FsSmem& sm = *reinterpret_cast<FsSmem*>(fs_raw);
@@ -477,14 +486,16 @@ __global__ void __launch_bounds__(FS_NP, 2) k_stage_fused(LaunchSet L, const flo
     }
     return;
   }
-  // m = 4: projections of psi(t_{n+1}) for the next step, then for the current
+  // m = 4: projections of psi(t_{n+1}) for the next step, then for the current.
+  // With a constant field both use the same q, and the first-order sums of the
+  // current's pass are those of the next step's (same z sums, rows and order).
   const float2* phn = (const float2*)L.ph_next + (long long)u * L.ph_stride;
   const float2* pho = (const float2*)L.ph_obs + (long long)u * L.ph_stride;
-  fs_load_z(sm.zt, c, phn);
-  sep_load_cols<N>(sm.colt, c, phn);
-  __syncthreads();
-  fs_project_pass<1, 2 * SEP_NA>(sm, 0, ah, al);
-  {
+  if (!same_next) {
+    fs_load_z(sm.zt, c, phn);
+    sep_load_cols<N>(sm.colt, c, phn);
+    __syncthreads();
+    fs_project_pass<1, 2 * SEP_NA>(sm, 0, ah, al);
     const int j = tid;
     if (j < c.n_proj) {
       const float2 M = sm.mres[(j >> 2) * 4 + (j & 3)];
@@ -510,7 +521,9 @@ __global__ void __launch_bounds__(FS_NP, 2) k_stage_fused(LaunchSet L, const flo
         if (s > 0) e[s - 1] += 1;
         const float2 M = sm.mres[al_ * 10 + fs_mono(e[0], e[1], e[2])];
         const double sc = c.dv * (double)c.pnormf[j];
-        Pab[4 * j + s] = make_float2((float)(sc * M.x), (float)(sc * M.y));
+        const float2 v = make_float2((float)(sc * M.x), (float)(sc * M.y));
+        Pab[4 * j + s] = v;
+        if (same_next && s == 0) Pu[j] = v;
       }
     }
     __syncthreads();
@@ -548,4 +561,145 @@ __global__ void __launch_bounds__(FS_NP, 2) k_bra_fused(LaunchSet L, const float
     const double sc = c.dv * (double)c.pnormf[j];
     P[U.p_off + (long long)b * c.n_proj + j] = make_float2((float)(sc * M.x), (float)(sc * M.y));
   }
+}
+
+// ----------------------------------------------------------------------------
+// Observation pass on 16^3 grids: one CTA per unit, bands in turn, each band
+// brought into shared memory by a bulk copy two bands ahead (double buffer).
+// Per column and plane it accumulates occ sum_b |u|^2 (rho; over bands as an
+// unevaluated float pair s + e updated by the error-free two-sum, which keeps
+// the sum to about 2^-44 relative, i.e. FP64-grade, without FP64 arithmetic),
+// per thread sum Re(u* (-i grad u)) (FP32 within a band, FP64 over bands) and
+// per band sum |u|^2 (CTA sum in a fixed order).  The unit's sums go to point
+// tile 0 of the partial buffers and zeros to the other tiles.
+// ----------------------------------------------------------------------------
+struct FoSmem {
+  float2 buf[2][FS_NPTS];
+  float red[8];
+  double redj[8][3];
+  unsigned long long mbar[2];
+};
+
+__global__ void __launch_bounds__(FS_NP, 2) k_observe_fused(LaunchSet L, const float2* __restrict__ psi,
+                                                            double* __restrict__ rho_part,
+                                                            double* __restrict__ jk_part,
+                                                            double* __restrict__ nrm_part) {
+  constexpr int ND = ZM_ND, N = FS_N, NP = FS_NP;
+  extern __shared__ __align__(128) unsigned char fo_raw[];
+  FoSmem& sm = *reinterpret_cast<FoSmem*>(fo_raw);
+  const CellDev& c = L.cell;
+  const int u = L.unit_ids[blockIdx.x];
+  const UnitDev U = L.units[u];
+  const SubDev S = L.subs[U.sub];
+  const int tid = threadIdx.x, col = tid, lane = tid & 31, warp = tid >> 5;
+  const int ix = col & (N - 1), iy = col / N;
+  const int nb = c.n_bands;
+  const float2* src = psi + U.psi_off;
+  const uint32_t bar0 = bk_smem(&sm.mbar[0]), bar1 = bk_smem(&sm.mbar[1]);
+  if (tid == 0) {
+    bk_mbar_init(bar0, 1);
+    bk_mbar_init(bar1, 1);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int k = 0; k < 2 && k < nb; ++k) {
+      const uint32_t bar = k ? bar1 : bar0;
+      bk_mbar_expect_tx(bar, FS_NPTS * (uint32_t)sizeof(float2));
+      bk_copy_g2s(bk_smem(sm.buf[k]), src + (long long)k * FS_NPTS, FS_NPTS * sizeof(float2), bar);
+    }
+  }
+  float rho[N], rho_e[N];
+#pragma unroll
+  for (int z = 0; z < N; ++z) rho[z] = rho_e[z] = 0.f;
+  double jx = 0.0, jy = 0.0, jz = 0.0;
+  const float2 zero = make_float2(0.f, 0.f);
+  const float2 neg1 = make_float2(-1.f, -1.f);
+  bool ok_all = true;
+  for (int b = 0; b < nb; ++b) {
+    const int slot = b & 1;
+    const bool ok = bk_mbar_wait(slot ? bar1 : bar0, (uint32_t)((b >> 1) & 1), BK_WAIT_POLLS);
+    if (!__syncthreads_and(ok)) {
+      ok_all = false;
+      break;
+    }
+    const float2* tb = sm.buf[slot];
+    const float2* cz = tb + col;
+    float2 qv[N + 2 * ND];
+#pragma unroll
+    for (int k = 0; k < 2 * ND; ++k) qv[k] = cz[((k - ND + N) & (N - 1)) * NP];
+    float nbs = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
+#pragma unroll
+    for (int z = 0; z < N; ++z) {
+      qv[z + 2 * ND] = cz[((z + ND) & (N - 1)) * NP];
+      const float2 ce = qv[z + ND];
+      float2 gx = zero, gy = zero, gz = zero;
+#pragma unroll
+      for (int mm = 1; mm <= ND; ++mm) {
+        const float2 xu = tb[z * NP + iy * N + ((ix + mm) & (N - 1))], xd = tb[z * NP + iy * N + ((ix - mm) & (N - 1))];
+        const float2 yu = tb[z * NP + ((iy + mm) & (N - 1)) * N + ix], yd = tb[z * NP + ((iy - mm) & (N - 1)) * N + ix];
+        const float2 zu = qv[z + ND + mm], zd = qv[z + ND - mm];
+        gx = f2fma(c.gradw2[0][mm], f2fma(neg1, xd, xu), gx);
+        gy = f2fma(c.gradw2[1][mm], f2fma(neg1, yd, yu), gy);
+        gz = f2fma(c.gradw2[2][mm], f2fma(neg1, zd, zu), gz);
+      }
+      const float n2v = ce.x * ce.x + ce.y * ce.y;
+      {
+        // two-sum: rho + n2v = t + err exactly
+        const float t = rho[z] + n2v, bb = t - rho[z];
+        rho_e[z] += (rho[z] - (t - bb)) + (n2v - bb);
+        rho[z] = t;
+      }
+      nbs += n2v;
+      // Re(conj(u) (-i g)) = u_r g_i - u_i g_r
+      bx += ce.x * gx.y - ce.y * gx.x;
+      by += ce.x * gy.y - ce.y * gy.x;
+      bz += ce.x * gz.y - ce.y * gz.x;
+    }
+    jx += bx;
+    jy += by;
+    jz += bz;
+    for (int off = 16; off > 0; off >>= 1) nbs += __shfl_xor_sync(0xffffffffu, nbs, off);
+    if (lane == 0) sm.red[warp] = nbs;
+    __syncthreads();   // band values read by every thread; norm partials in place
+    if (tid == 0) {
+      double sum = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += (double)sm.red[w];
+      nrm_part[U.nrm_off + b] = sum;
+      if (b + 2 < nb) {
+        // the buffer of band b is free: bring band b + 2 into it
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        const uint32_t bar = slot ? bar1 : bar0;
+        bk_mbar_expect_tx(bar, FS_NPTS * (uint32_t)sizeof(float2));
+        bk_copy_g2s(bk_smem(sm.buf[slot]), src + (long long)(b + 2) * FS_NPTS, FS_NPTS * sizeof(float2), bar);
+      }
+    }
+  }
+  if (!ok_all) {
+    if (tid == 0) {
+      atomicOr(S.status, BK_STATUS_TIMEOUT);
+      bk_mbar_wait(bar0, 0, BK_WAIT_POLLS);
+      bk_mbar_wait(bar1, 0, BK_WAIT_POLLS);
+    }
+    return;
+  }
+#pragma unroll
+  for (int z = 0; z < N; ++z) rho_part[U.rho_off + (long long)z * NP + col] = c.occ * ((double)rho[z] + (double)rho_e[z]);
+  for (int off = 16; off > 0; off >>= 1) {
+    jx += __shfl_xor_sync(0xffffffffu, jx, off);
+    jy += __shfl_xor_sync(0xffffffffu, jy, off);
+    jz += __shfl_xor_sync(0xffffffffu, jz, off);
+  }
+  if (lane == 0) {
+    sm.redj[warp][0] = jx;
+    sm.redj[warp][1] = jy;
+    sm.redj[warp][2] = jz;
+  }
+  __syncthreads();
+  if (tid < 3) {
+    double sum = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += sm.redj[w][tid];
+    jk_part[U.jk_off + tid] = sum;
+  }
+  for (int i = tid; i < 3 * (c.n_tiles - 1); i += blockDim.x) jk_part[U.jk_off + 3 + i] = 0.0;
+  for (int i = tid; i < c.n_bands * (c.n_tiles - 1); i += blockDim.x) nrm_part[U.nrm_off + c.n_bands + i] = 0.0;
 }

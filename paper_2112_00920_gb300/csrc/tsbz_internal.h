@@ -132,5 +132,8 @@ void launch_stage_v(const LaunchSet& L, const void* tin, void* tout, void* psi, 
 bool sep_supported(const CellDev& c);
 void launch_bra_sep(const LaunchSet& L, const void* src, void* out, int with_d, int use_obs, void* stream);
 // stage 4 on the bulk-staged path also writes P (next step) and Pa; returns whether it did
+// same_next: the field is constant, so at m = 4 the next step's projections come from the current's sums
 bool launch_stage_sep(const LaunchSet& L, const void* tin, void* tout, void* psi, void* P, void* Pa, int m,
-                      void* stream);
+                      int same_next, void* stream);
+bool launch_observe_fused(const LaunchSet& L, const void* psi, double* rho_part, double* jk_part, double* nrm_part,
+                          void* stream);

@@ -643,19 +643,23 @@ __global__ void __launch_bounds__(256) k_finalize(const SubDev* subs, const Unit
   const int s = blockIdx.x;
   const SubDev S = subs[s];
   const CellDev c = cells[S.cell];
-  const int step = *S.step;
-  const bool write_j = (mode == TSBZ_FIN_STEP) || (mask != nullptr && mask[s] != 0 &&
-                                                   (mode == TSBZ_FIN_J0MINUS || step == 0));
-  // density
+  // density: point tile blockIdx.y of the sub-simulation (fixed k and band-group order per point)
   const double inv_nk = 1.0 / S.n_k;
-  for (int r = threadIdx.x; r < c.npts; r += blockDim.x) {
+  const int chunk = (c.npts + (int)gridDim.y - 1) / (int)gridDim.y;
+  const int r_end = min(c.npts, ((int)blockIdx.y + 1) * chunk);
+  for (int r = (int)blockIdx.y * chunk + threadIdx.x; r < r_end; r += blockDim.x) {
     double acc = 0.0;
     for (int kl = 0; kl < S.n_k; ++kl) {
-      const UnitDev U = units[S.unit0 + kl];
-      for (int g = 0; g < c.n_bgroups; ++g) acc += rho_part[U.rho_off + (long long)g * c.npts + r];
+      const long long off = units[S.unit0 + kl].rho_off;
+      for (int g = 0; g < c.n_bgroups; ++g) acc += rho_part[off + (long long)g * c.npts + r];
     }
     S.rho[r] = acc * inv_nk;
   }
+  if (blockIdx.y != 0) return;
+  // current, norms and the step counter: point tile 0 only
+  const int step = *S.step;
+  const bool write_j = (mode == TSBZ_FIN_STEP) || (mask != nullptr && mask[s] != 0 &&
+                                                   (mode == TSBZ_FIN_J0MINUS || step == 0));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double jw[3] = {0.0, 0.0, 0.0};
   for (int kl = warp; kl < S.n_k; kl += 8) {
@@ -860,8 +864,9 @@ void launch_finalize_t(const SubDev* subs, int n_subs, const UnitDev* units, con
                        const double* nrm_part, const int* mask, int mode, void* stream) {
   using V = typename Cplx<T>::type;
   if (n_subs == 0) return;
-  k_finalize<T><<<n_subs, 256, 0, (cudaStream_t)stream>>>(subs, units, cells_dev, q_obs, (const V*)Pa, rho_part,
-                                                          jk_part, nrm_part, mask, mode);
+  // 16 density tiles per sub-simulation; tile 0 also forms J, the norms and the step counter
+  k_finalize<T><<<dim3(n_subs, 16), 256, 0, (cudaStream_t)stream>>>(subs, units, cells_dev, q_obs, (const V*)Pa,
+                                                                    rho_part, jk_part, nrm_part, mask, mode);
 }
 
 template <typename T>

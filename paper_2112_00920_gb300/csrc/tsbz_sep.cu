@@ -58,7 +58,7 @@ static void launch_stage_bulk(const LaunchSet& L, const void* tin, void* tout, v
 }
 
 bool launch_stage_sep(const LaunchSet& L, const void* tin, void* tout, void* psi, void* P, void* Pa, int m,
-                      void* stream) {
+                      int same_next, void* stream) {
   if (L.n_units == 0) return false;
   const CellDev& c = L.cell;
   cudaStream_t st = (cudaStream_t)stream;
@@ -71,7 +71,7 @@ bool launch_stage_sep(const LaunchSet& L, const void* tin, void* tout, void* psi
     }
     const unsigned grid = (unsigned)L.n_units * (unsigned)c.n_bands;
     k_stage_fused<<<grid, FS_NP, sizeof(FsSmem), st>>>(L, (const float2*)tin, (float2*)tout, (float2*)psi,
-                                                        (float2*)P, (float2*)Pa, m);
+                                                        (float2*)P, (float2*)Pa, m, same_next);
     return true;
   }
   if (next && c.n1 == 8 && c.n2 == 8 && c.n3 == 8) {
@@ -86,4 +86,18 @@ bool launch_stage_sep(const LaunchSet& L, const void* tin, void* tout, void* psi
   else
     k_stage_sep<8><<<grid, thr, pad, st>>>(L, (const float2*)tin, (float2*)tout, (float2*)psi, (float2*)P, m);
   return false;
+}
+
+bool launch_observe_fused(const LaunchSet& L, const void* psi, double* rho_part, double* jk_part, double* nrm_part,
+                          void* stream) {
+  const CellDev& c = L.cell;
+  if (L.n_units == 0 || c.n1 != 16 || c.n2 != 16 || c.n3 != 16) return false;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_observe_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(FoSmem));
+    attr = true;
+  }
+  k_observe_fused<<<L.n_units, FS_NP, sizeof(FoSmem), (cudaStream_t)stream>>>(L, (const float2*)psi, rho_part,
+                                                                              jk_part, nrm_part);
+  return true;
 }
