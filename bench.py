@@ -91,19 +91,74 @@ def cpu_model() -> str:
 # Clocks
 # ----------------------------------------------------------------------------
 class ClockSampler:
+    """SM clock and clock-event reasons sampled during the timed region.
+
+    NVML (libnvidia-ml through ctypes, read-only queries) every 10 ms when it
+    loads, so that even a short timed region gets many samples; otherwise
+    nvidia-smi every 100 ms.  The GPU is found by the UUID CUDA reports for
+    this process's device, falling back to the device index."""
     Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # clock-event reason bits of nvmlDeviceGetCurrentClocksEventReasons
+    BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40}
 
-    def __init__(self, index: int = 0):
+    def __init__(self, index: int = 0, uuid: str | None = None):
         self.index = index
+        self.uuid = uuid
         self.proc = None
-        self.lines = []
+        self.nvml = None
+        self.stop = threading.Event()
+        self.samples = []   # (sm_mhz, max_mhz, set of reasons)
+        self.source = None
+
+    def _nvml_open(self):
+        import ctypes
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            return None
+        h = ctypes.c_void_p()
+        ok = False
+        if self.uuid:
+            for u in (self.uuid, "GPU-" + self.uuid):
+                if lib.nvmlDeviceGetHandleByUUID(u.encode(), ctypes.byref(h)) == 0:
+                    ok = True
+                    break
+        if not ok:
+            ok = lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.index), ctypes.byref(h)) == 0
+        if not ok:
+            lib.nvmlShutdown()
+            return None
+        reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        return lib, h, reasons
+
+    def _nvml_loop(self):
+        import ctypes
+        lib, h, reasons = self.nvml
+        clk, mx, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        while not self.stop.is_set():
+            if (lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(clk)) == 0 and
+                    lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0 and
+                    reasons(h, ctypes.byref(rs)) == 0):
+                act = {nm for nm, b in self.BITS.items() if rs.value & b}
+                self.samples.append((float(clk.value), float(mx.value), act))
+            self.stop.wait(0.01)
 
     def __enter__(self):
         try:
+            self.nvml = self._nvml_open()
+        except (OSError, AttributeError):
+            self.nvml = None
+        if self.nvml:
+            self.source = "nvml 10 ms"
+            self.thread = threading.Thread(target=self._nvml_loop, daemon=True)
+            self.thread.start()
+            return self
+        try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.source = "nvidia-smi 100 ms"
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except (OSError, FileNotFoundError):
@@ -111,10 +166,22 @@ class ClockSampler:
         return self
 
     def _read(self):
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            parts = [p.strip() for p in line.strip().split(",")]
+            if len(parts) < 6:
+                continue
+            try:
+                sm, mx = float(parts[0]), float(parts[1])
+            except ValueError:
+                continue
+            self.samples.append((sm, mx, {nm for nm, v in zip(names, parts[2:6]) if v.lower() == "active"}))
 
     def __exit__(self, *a):
+        self.stop.set()
+        if self.nvml:
+            self.thread.join(timeout=2)
+            self.nvml[0].nvmlShutdown()
         if self.proc:
             self.proc.terminate()
             try:
@@ -123,24 +190,23 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 6:
-                continue
-            try:
-                sm.append(float(parts[0]))
-                mx.append(float(parts[1]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[2:6]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        if not sm:
+        if not self.samples:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        reasons = set()
+        for _, _, r in self.samples:
+            reasons |= r
+        return {"sm_mhz": statistics.median(x[0] for x in self.samples),
+                "sm_max_mhz": max(x[1] for x in self.samples), "reasons": sorted(reasons),
+                "samples": len(self.samples), "source": self.source}
+
+
+def device_uuid(index: int) -> str | None:
+    import torch
+    try:
+        u = getattr(torch.cuda.get_device_properties(index), "uuid", None)
+        return str(u) if u is not None else None
+    except Exception:
+        return None
 
 
 # ----------------------------------------------------------------------------
@@ -289,7 +355,7 @@ def main():
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    with ClockSampler(local_rank) as clk:
+    with ClockSampler(local_rank, device_uuid(local_rank)) as clk:
         start.record(stream)
         P.propagate(args.steps)
         end.record(stream)

@@ -111,8 +111,10 @@ int tsbz_create(tsbz_ctx** out, int device, int precision, void* cuda_stream, co
 int tsbz_init_cell(tsbz_ctx* ctx, const tsbz_cell_desc* desc, int* cell_id);
 
 /* Add one sub-simulation (Sec. II.B step 3): n_k k-points k_cart[n_k][3]
- * of cell `cell_id`, time step dt, capacity for max_steps steps of history.
- * Sub-simulations can only be added before the first load_ground_state. */
+ * of cell `cell_id`, time step dt and a budget of max_steps steps (also the
+ * capacity of its current history).  Sub-simulations of one context may
+ * differ in cell, n_k, dt and budget.  Sub-simulations can only be added
+ * before the first load_ground_state. */
 int tsbz_add_subsim(tsbz_ctx* ctx, int cell_id, int n_k, const double* k_cart, double dt, int max_steps,
                     int* subsim_id);
 
@@ -135,8 +137,12 @@ int tsbz_set_field(tsbz_ctx* ctx, int subsim_id, int n_steps, const double* a_sa
 /* Advance every sub-simulation by n_steps 4th-order Taylor steps (Eq. 1 with
  * the step defined in the header of the CUDA sources): h uses
  * q = k + A(t_n + dt/2) and v_Hxc[rho(t_n)]; after the step rho, v_Hxc and
- * J(t_{n+1}) (q = k + A(t_{n+1})) are updated.  Returns when the work is
- * complete; TSBZ_ENONFINITE names the first failing sub-simulation. */
+ * J(t_{n+1}) (q = k + A(t_{n+1})) are updated.  Step budgets are honoured:
+ * a sub-simulation that reaches its max_steps stops there (its units skip
+ * the remaining steps, decided on the device, so graph replays honour it
+ * too) while the others go on; tsbz_get_step gives each one's count.
+ * Returns when the work is complete; TSBZ_ENONFINITE names the first failing
+ * sub-simulation. */
 int tsbz_propagate(tsbz_ctx* ctx, int n_steps);
 
 /* Current history J(t_j), j = first .. first+count-1 (j = 0 is t = 0+), as
@@ -144,6 +150,16 @@ int tsbz_propagate(tsbz_ctx* ctx, int n_steps);
  * average (1/N_H) sum_m (J_m(t_j) - J_m(0-)) (Eq. 9, Sec. II.B step 4) and
  * J0_minus = 0; all sub-simulations then need the same dt. */
 int tsbz_get_current(tsbz_ctx* ctx, int subsim_id, int first, int count, double* J, double* J0_minus);
+
+/* The two-step mean of the current over all N_H sub-simulations (as
+ * tsbz_get_current with subsim_id = -1, Eq. 9) together with its standard
+ * error, the error bars of Sec. III.B (Fig. 6): the sub-simulations are N_H
+ * data sets, so sigma_E(t_j) = sqrt( sum_m (dJ_m - mean)^2 / (N_H (N_H - 1)) )
+ * per sample and component (0 when N_H = 1).  It is a true standard error
+ * for random shifts; for Halton shifts it is the paper's indicator.  mean
+ * and stderr_out are [count][3]; all sub-simulations need the same dt and at
+ * least first + count - 1 steps.  FP64 on the host, fixed order. */
+int tsbz_get_current_stats(tsbz_ctx* ctx, int first, int count, double* mean, double* stderr_out);
 
 /* Density rho(r) = (1/N_k) sum_k sum_b occ |u_bk(r)|^2 (Eq. 3) of a
  * sub-simulation at its current step, [n3][n2][n1] doubles (cap >= n_pts). */
@@ -181,6 +197,34 @@ int tsbz_set_profiling(tsbz_ctx* ctx, int on);
  * direct-launch path.  Set-up calls invalidate nothing: the graph reads the
  * step counters and field samples from device memory. */
 int tsbz_set_graphs(tsbz_ctx* ctx, int on);
+
+/* Autotuner of the batched launch (the per-cell choice of kernel variants:
+ * tile shapes and schedules; the method itself is the same in every variant).
+ * For each cell with more than one variant it runs, per variant, one untimed
+ * step of every sub-simulation and then two windows of two timed steps (CUDA
+ * events on the context stream; the faster window counts), the default
+ * variant first and the others while budget_ms of device time lasts, and
+ * keeps the fastest.  The trial steps are undone
+ * afterwards: orbitals, projections, step counts, densities, potentials and
+ * norms are restored bit for bit from a snapshot taken on the device (one
+ * temporary copy of the orbitals, from the context's allocator), and no
+ * current sample is exposed.  Results after tuning agree with the default
+ * variant's within the arithmetic's rounding, not bit for bit.  A captured
+ * step graph is dropped.  Needs loaded ground states and at least one
+ * sub-simulation with steps left (TSBZ_ESTATE otherwise).  *n_tried
+ * (nullable) receives the number of variants timed. */
+int tsbz_autotune(tsbz_ctx* ctx, int budget_ms, int* n_tried);
+
+/* The variant in force for a cell, the number it can run (n_variants) and the
+ * ms per step the autotuner measured for each (ms[0..n_ms-1], 0 = untimed);
+ * any output pointer may be NULL.  Variants: FP32 on 16^3 and 8^3 cells:
+ * 0 = fused tensor-core / bulk-staged stage, 1 = z-march stage with CUDA-core
+ * projections; point-parallel stage kernels (FP64, other FP32 shapes): bands
+ * per staged projection chunk 8 (0), 4 (1), 16 (2). */
+int tsbz_get_variant(tsbz_ctx* ctx, int cell_id, int* variant, int* n_variants, double* ms, int n_ms);
+
+/* Force a cell's variant (0 <= variant < n_variants; TSBZ_EINVAL otherwise). */
+int tsbz_set_variant(tsbz_ctx* ctx, int cell_id, int variant);
 
 const char* tsbz_last_error(tsbz_ctx* ctx);
 void tsbz_destroy(tsbz_ctx* ctx);

@@ -46,6 +46,26 @@ def dielectric(dj_component, dt, k0, omegas, t_w=None):
     return 1.0 + 4.0j * np.pi * sig / omegas
 
 
+def dielectric_statistics(dj_components, dt, k0, omegas, t_w=None):
+    """Mean and standard error of eps(omega) over N_H shifted sub-simulations
+    (Eqs. 12-14 per sub-simulation; error bars of Fig. 6, Sec. III.B).
+    eps is affine in dJ, so the mean of the per-shift eps is the eps of the
+    averaged dJ (Eq. 9).  The standard error is taken separately for the real
+    and imaginary parts: sigma = sqrt(sum (x_m - mean)^2 / (N_H (N_H - 1))).
+    dj_components: (N_H, n+1) along the kick.  Returns (mean eps, sigma_re,
+    sigma_im)."""
+    eps = np.stack([dielectric(d, dt, k0, omegas, t_w) for d in dj_components])
+    n = eps.shape[0]
+    mean = eps.sum(axis=0) / n
+    if n < 2:
+        z = np.zeros(mean.shape)
+        return mean, z, z
+    dev = eps - mean
+    sre = np.sqrt((dev.real ** 2).sum(axis=0) / (n * (n - 1)))
+    sim = np.sqrt((dev.imag ** 2).sum(axis=0) / (n * (n - 1)))
+    return mean, sre, sim
+
+
 def hhg_spectrum(j_component, dt, t_pulse, omegas):
     n1 = j_component.shape[0]
     t = np.arange(n1) * dt

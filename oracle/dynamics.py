@@ -189,6 +189,27 @@ def two_step_average(results):
     return np.mean(np.stack(dj), axis=0)
 
 
+def two_step_standard_error(results):
+    """Sec. III.B, discussion of the error bars of Fig. 6: the N_H
+    sub-simulations are N_H data sets whose mean is the two-step result of
+    Eq. 9, so the standard error of that mean is
+        sigma_E(t) = sqrt( sum_m (dJ_m(t) - dJ(t))^2 / (N_H (N_H - 1)) ),
+    per time sample and component (zero when N_H = 1).  Two passes (mean,
+    then squared deviations).  Returns (dJ, sigma_E), each (n_t, 3)."""
+    dj = [r["J"] - r["J0_minus"][None, :] for r in results]
+    n = len(dj)
+    mean = np.zeros_like(dj[0])
+    for d in dj:
+        mean = mean + d
+    mean = mean / n
+    if n < 2:
+        return mean, np.zeros_like(mean)
+    ss = np.zeros_like(mean)
+    for d in dj:
+        ss = ss + (d - mean) ** 2
+    return mean, np.sqrt(ss / (n * (n - 1)))
+
+
 def _run_one(args):
     sub, u0, hxc, v_frozen = args
     k = subsim_kpoints(sub)

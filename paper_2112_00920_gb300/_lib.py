@@ -75,6 +75,7 @@ _SIGS = {
     "tsbz_set_field": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _D], ctypes.c_int),
     "tsbz_propagate": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "tsbz_get_current": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D], ctypes.c_int),
+    "tsbz_get_current_stats": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _D, _D], ctypes.c_int),
     "tsbz_get_density": ([ctypes.c_void_p, ctypes.c_int, _D, ctypes.c_size_t], ctypes.c_int),
     "tsbz_get_norms": ([ctypes.c_void_p, ctypes.c_int, _D, ctypes.c_size_t], ctypes.c_int),
     "tsbz_get_step": ([ctypes.c_void_p, ctypes.c_int, _I], ctypes.c_int),
@@ -86,6 +87,9 @@ _SIGS = {
     "tsbz_get_timings": ([ctypes.c_void_p, _D, ctypes.c_int], ctypes.c_int),
     "tsbz_set_profiling": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "tsbz_set_graphs": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
+    "tsbz_autotune": ([ctypes.c_void_p, ctypes.c_int, _I], ctypes.c_int),
+    "tsbz_get_variant": ([ctypes.c_void_p, ctypes.c_int, _I, _I, _D, ctypes.c_int], ctypes.c_int),
+    "tsbz_set_variant": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "tsbz_last_error": ([ctypes.c_void_p], ctypes.c_char_p),
     "tsbz_destroy": ([ctypes.c_void_p], None),
     "tsbz_shifted_kpoints": ([_D, _I, _D, _D, ctypes.c_size_t], ctypes.c_int),
@@ -308,6 +312,15 @@ class Propagator:
         self._check(self.lib.tsbz_get_current(self.ctx, sid, first, count, _dptr(J), _dptr(j0)), "tsbz_get_current")
         return J, j0
 
+    def current_stats(self, first=0, count=None):
+        """Two-step mean of dJ over the sub-simulations (Eq. 9) and its standard error."""
+        if count is None:
+            count = min(self.step(i) for i in range(len(self.subs))) + 1 - first
+        mean, se = np.zeros((count, 3)), np.zeros((count, 3))
+        self._check(self.lib.tsbz_get_current_stats(self.ctx, first, count, _dptr(mean), _dptr(se)),
+                    "tsbz_get_current_stats")
+        return mean, se
+
     def density(self, sid):
         c = self.cells[self.subs[sid]["cell"]]
         out = np.zeros(c["n"][::-1])
@@ -356,6 +369,24 @@ class Propagator:
 
     def set_profiling(self, on: bool):
         self._check(self.lib.tsbz_set_profiling(self.ctx, 1 if on else 0), "tsbz_set_profiling")
+
+    def autotune(self, budget_ms: int = 2000) -> int:
+        """Time the kernel variants of every cell and keep the fastest (the
+        state is restored afterwards); returns the number of variants timed."""
+        n = ctypes.c_int()
+        self._check(self.lib.tsbz_autotune(self.ctx, int(budget_ms), ctypes.byref(n)), "tsbz_autotune")
+        return n.value
+
+    def variant(self, cell_id):
+        """(variant in force, number of variants, measured ms per step of each)."""
+        v, nv = ctypes.c_int(), ctypes.c_int()
+        ms = np.zeros(4)
+        self._check(self.lib.tsbz_get_variant(self.ctx, cell_id, ctypes.byref(v), ctypes.byref(nv), _dptr(ms), 4),
+                    "tsbz_get_variant")
+        return v.value, nv.value, ms[: nv.value].tolist()
+
+    def set_variant(self, cell_id, variant: int):
+        self._check(self.lib.tsbz_set_variant(self.ctx, cell_id, int(variant)), "tsbz_set_variant")
 
     def timings(self):
         t = np.zeros(7)

@@ -11,6 +11,7 @@
 // stage 3 tB -> tA (psi += t3), stage 4 tA -> (psi += t4).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -36,6 +37,8 @@ struct HostCell {
   std::vector<int> hxc_subs;   // non-frozen sub-simulations of this cell
   int* d_hxc_subs = nullptr;
   bool pa_by_stage = false;    // the last stage 4 also wrote P (next step) and Pa
+  int variant = 0;             // kernel variant (tsbz_autotune / tsbz_set_variant)
+  double tune_ms[TSBZ_MAX_VARIANTS] = {0, 0, 0, 0};   // ms per step measured per variant
 };
 
 struct HostSub {
@@ -98,11 +101,13 @@ struct tsbz_ctx {
   int* d_steps = nullptr;
   int* d_status = nullptr;
   int* d_mask = nullptr;
+  int* d_active = nullptr;   // per sub-simulation: takes part in the current step
   double2* work_a = nullptr;
   double2* work_b = nullptr;
   double2* staging = nullptr;
   long long staging_elems = 0;
   long long n_units = 0;
+  size_t psi_bytes = 0, p_bytes = 0;   // sizes of psi (= tA = tB) and P
   std::vector<long long> unit_psi_off;
   long long launches = 0;
   bool prof = false;
@@ -153,6 +158,19 @@ int dalloc(tsbz_ctx* ctx, size_t bytes, void** out) {
   return TSBZ_OK;
 }
 
+void dfree(tsbz_ctx* ctx, void* p) {
+  if (!p) return;
+  for (size_t i = 0; i < ctx->owned.size(); ++i)
+    if (ctx->owned[i] == p) {
+      ctx->owned.erase(ctx->owned.begin() + (long)i);
+      break;
+    }
+  if (ctx->has_alloc)
+    ctx->alloc.free(p, ctx->alloc.user);
+  else
+    cudaFree(p);
+}
+
 template <typename P> int dalloc_t(tsbz_ctx* ctx, size_t count, P** out) {
   void* p = nullptr;
   int rc = dalloc(ctx, count * sizeof(P), &p);
@@ -192,6 +210,7 @@ LaunchSet make_set(tsbz_ctx* ctx, HostCell& hc) {
   L.ph_next = ctx->ph_next;
   L.ph_stride = ctx->ph_stride;
   L.qt_half = ctx->qt_half;
+  L.variant = hc.variant;
   return L;
 }
 
@@ -241,6 +260,8 @@ int layout(tsbz_ctx* ctx) {
   ctx->n_units = (long long)units.size();
   ctx->ph_stride = ph_stride;
   int rc;
+  ctx->psi_bytes = (size_t)psi_e * es;
+  ctx->p_bytes = (size_t)std::max<long long>(p_e, 1) * es;
   if ((rc = dalloc(ctx, psi_e * es, &ctx->psi))) return rc;
   if ((rc = dalloc(ctx, psi_e * es, &ctx->tA))) return rc;
   if ((rc = dalloc(ctx, psi_e * es, &ctx->tB))) return rc;
@@ -263,6 +284,7 @@ int layout(tsbz_ctx* ctx) {
   if ((rc = dalloc_t(ctx, ctx->subs.size(), &ctx->d_steps))) return rc;
   if ((rc = dalloc_t(ctx, ctx->subs.size(), &ctx->d_status))) return rc;
   if ((rc = dalloc_t(ctx, ctx->subs.size(), &ctx->d_mask))) return rc;
+  if ((rc = dalloc_t(ctx, ctx->subs.size(), &ctx->d_active))) return rc;
   if ((rc = dalloc_t(ctx, std::max<long long>(work_max, 1), &ctx->work_a))) return rc;
   if ((rc = dalloc_t(ctx, std::max<long long>(work_max, 1), &ctx->work_b))) return rc;
   if ((rc = dalloc_t(ctx, stage_max, &ctx->staging))) return rc;
@@ -301,6 +323,7 @@ int layout(tsbz_ctx* ctx) {
     d.norms = hs.norms;
     d.step = ctx->d_steps + s;
     d.status = ctx->d_status + s;
+    d.active = ctx->d_active + s;
     CK(cudaMemsetAsync(hs.vhxc, 0, sizeof(double) * c.npts, ctx->stream));
     CK(cudaMemsetAsync(hs.J, 0, sizeof(double) * 3 * (hs.max_steps + 1), ctx->stream));
     CK(cudaMemsetAsync(hs.J0m, 0, sizeof(double) * 3, ctx->stream));
@@ -326,6 +349,10 @@ int layout(tsbz_ctx* ctx) {
   CK(cudaMemsetAsync(ctx->d_steps, 0, sizeof(int) * ctx->subs.size(), ctx->stream));
   CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int) * ctx->subs.size(), ctx->stream));
   CK(cudaMemsetAsync(ctx->d_mask, 0, sizeof(int) * ctx->subs.size(), ctx->stream));
+  {
+    const std::vector<int> ones(ctx->subs.size(), 1);
+    CK(cudaMemcpyAsync(ctx->d_active, ones.data(), sizeof(int) * ones.size(), cudaMemcpyHostToDevice, ctx->stream));
+  }
   CK(cudaMemsetAsync(ctx->rho_part, 0, sizeof(double) * std::max<long long>(rho_e, 1), ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->laid_out = true;
@@ -618,6 +645,104 @@ int sync_and_check(tsbz_ctx* ctx) {
   return TSBZ_OK;
 }
 
+// Kernel variants a cell can run (the autotuner's search space):
+//   FP32 on 16^3 / 8^3 cells: 0 fused tensor-core / bulk-staged stage, 1 z-march
+//     stage with CUDA-core projections;
+//   point-parallel path (FP64, and FP32 on shapes without a z-march kernel):
+//     bands per staged projection chunk 8 (0), 4 (1), 16 (2, when its shared
+//     memory fits);
+//   everything else: one variant.
+int n_variants(const tsbz_ctx* ctx, const HostCell& hc) {
+  const CellDev& c = hc.dev;
+  if (ctx->precision == TSBZ_FP32_TC) return 1;
+  if (ctx->precision == TSBZ_FP32 && sep_supported(c)) {
+    const bool cube16 = c.n1 == 16 && c.n2 == 16 && c.n3 == 16, cube8 = c.n1 == 8 && c.n2 == 8 && c.n3 == 8;
+    return (cube16 || cube8) ? 2 : 1;
+  }
+  const size_t big = (size_t)16 * (c.n_proj > 0 ? c.n_proj : 1) * ctx->elem_size();
+  return big <= 160 * 1024 ? 3 : 2;
+}
+
+// Everything a time step changes that outlives the step, so that trial steps
+// can be undone bit for bit: psi, P, the step counters, status words and the
+// per-sub-simulation rho, v_Hxc, v_eff and norms.
+struct Snapshot {
+  void* psi = nullptr;
+  void* P = nullptr;
+  std::vector<int> steps, status;
+  std::vector<std::vector<double>> rho, vhxc, norms;
+  std::vector<std::vector<unsigned char>> veff;
+  bool p_next_valid = false;
+  std::vector<bool> pa_by_stage;
+};
+
+int snapshot_take(tsbz_ctx* ctx, Snapshot& sn) {
+  int rc;
+  if ((rc = dalloc(ctx, ctx->psi_bytes, &sn.psi))) return rc;
+  if ((rc = dalloc(ctx, ctx->p_bytes, &sn.P))) return rc;
+  CK(cudaMemcpyAsync(sn.psi, ctx->psi, ctx->psi_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(sn.P, ctx->P, ctx->p_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  const size_t ns = ctx->subs.size();
+  sn.steps.resize(ns);
+  sn.status.resize(ns);
+  sn.rho.resize(ns);
+  sn.vhxc.resize(ns);
+  sn.norms.resize(ns);
+  sn.veff.resize(ns);
+  CK(cudaMemcpyAsync(sn.steps.data(), ctx->d_steps, sizeof(int) * ns, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(sn.status.data(), ctx->d_status, sizeof(int) * ns, cudaMemcpyDeviceToHost, ctx->stream));
+  const size_t rs = ctx->precision == TSBZ_FP64 ? 8 : 4;
+  for (size_t s = 0; s < ns; ++s) {
+    const HostSub& hs = ctx->subs[s];
+    const CellDev& c = ctx->cells[hs.cell].dev;
+    sn.rho[s].resize(c.npts);
+    sn.vhxc[s].resize(c.npts);
+    sn.norms[s].resize((size_t)hs.n_k * c.n_bands);
+    sn.veff[s].resize((size_t)c.npts * rs);
+    CK(cudaMemcpyAsync(sn.rho[s].data(), hs.rho, sizeof(double) * c.npts, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(sn.vhxc[s].data(), hs.vhxc, sizeof(double) * c.npts, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(sn.norms[s].data(), hs.norms, sizeof(double) * sn.norms[s].size(), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaMemcpyAsync(sn.veff[s].data(), hs.veff, sn.veff[s].size(), cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  sn.p_next_valid = ctx->p_next_valid;
+  for (auto& hc : ctx->cells) sn.pa_by_stage.push_back(hc.pa_by_stage);
+  return sync_and_check(ctx);
+}
+
+int snapshot_restore(tsbz_ctx* ctx, Snapshot& sn) {
+  CK(cudaMemcpyAsync(ctx->psi, sn.psi, ctx->psi_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->P, sn.P, ctx->p_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  const size_t ns = ctx->subs.size();
+  CK(cudaMemcpyAsync(ctx->d_steps, sn.steps.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->d_status, sn.status.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, ctx->stream));
+  for (size_t s = 0; s < ns; ++s) {
+    HostSub& hs = ctx->subs[s];
+    CK(cudaMemcpyAsync(hs.rho, sn.rho[s].data(), sizeof(double) * sn.rho[s].size(), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    CK(cudaMemcpyAsync(hs.vhxc, sn.vhxc[s].data(), sizeof(double) * sn.vhxc[s].size(), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    CK(cudaMemcpyAsync(hs.norms, sn.norms[s].data(), sizeof(double) * sn.norms[s].size(), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    CK(cudaMemcpyAsync(hs.veff, sn.veff[s].data(), sn.veff[s].size(), cudaMemcpyHostToDevice, ctx->stream));
+  }
+  ctx->p_next_valid = sn.p_next_valid;
+  for (size_t i = 0; i < ctx->cells.size(); ++i) ctx->cells[i].pa_by_stage = sn.pa_by_stage[i];
+  const int rc = sync_and_check(ctx);
+  dfree(ctx, sn.psi);
+  dfree(ctx, sn.P);
+  sn.psi = sn.P = nullptr;
+  return rc;
+}
+
+// A captured step holds the kernels of the variants it was captured with.
+void drop_step_graph(tsbz_ctx* ctx) {
+  if (ctx->step_graph) {
+    cudaGraphExecDestroy(ctx->step_graph);
+    ctx->step_graph = nullptr;
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -849,9 +974,8 @@ int tsbz_propagate(tsbz_ctx* ctx, int n_steps) {
   if (!ctx || n_steps < 0) return TSBZ_EINVAL;
   int rc = ensure_ready(ctx);
   if (rc) return rc;
-  for (size_t s = 0; s < ctx->subs.size(); ++s)
-    if (ctx->subs[s].steps + n_steps > ctx->subs[s].max_steps)
-      return set_err(ctx, TSBZ_EINVAL, "sub-simulation " + std::to_string(s) + " would exceed its max_steps");
+  // per-sub-simulation step budgets: a sub-simulation that reaches max_steps
+  // sits out the remaining steps (its units skip every kernel of the step)
   ctx->ev_marks.clear();
   ctx->ev_next = 0;
   if (ctx->graphs && !ctx->prof && n_steps > 0) {
@@ -864,7 +988,7 @@ int tsbz_propagate(tsbz_ctx* ctx, int n_steps) {
   }
   CK(cudaGetLastError());
   if ((rc = sync_and_check(ctx))) return rc;
-  for (auto& hs : ctx->subs) hs.steps += n_steps;
+  for (auto& hs : ctx->subs) hs.steps = std::min(hs.max_steps, hs.steps + n_steps);
   if (ctx->prof) {
     for (int f = 0; f < TSBZ_N_FAM; ++f) ctx->times[f] = 0.0;
     for (auto& m : ctx->ev_marks) {
@@ -911,6 +1035,39 @@ int tsbz_get_current(tsbz_ctx* ctx, int s, int first, int count, double* J, doub
   const double inv = 1.0 / (double)ctx->subs.size();
   for (size_t i = 0; i < acc.size(); ++i) J[i] = acc[i] * inv;
   if (J0_minus) J0_minus[0] = J0_minus[1] = J0_minus[2] = 0.0;
+  return TSBZ_OK;
+}
+
+int tsbz_get_current_stats(tsbz_ctx* ctx, int first, int count, double* mean, double* stderr_out) {
+  if (!ctx || first < 0 || count < 0 || (count > 0 && (!mean || !stderr_out))) return TSBZ_EINVAL;
+  int rc = ensure_ready(ctx);
+  if (rc) return rc;
+  if ((rc = sync_and_check(ctx))) return rc;
+  const double dt0 = ctx->subs[0].dt;
+  for (auto& hs : ctx->subs) {
+    if (hs.dt != dt0) return set_err(ctx, TSBZ_EINVAL, "two-step statistics need equal dt");
+    if (first + count > hs.steps + 1) return set_err(ctx, TSBZ_EINVAL, "requested steps not computed yet");
+  }
+  const size_t n3 = 3 * (size_t)count, ns = ctx->subs.size();
+  std::vector<double> dj(ns * n3), j0(3);
+  for (size_t m = 0; m < ns; ++m) {
+    const HostSub& hs = ctx->subs[m];
+    if (count) CK(cudaMemcpy(dj.data() + m * n3, hs.J + 3LL * first, sizeof(double) * n3, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(j0.data(), hs.J0m, sizeof(double) * 3, cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < n3; ++i) dj[m * n3 + i] -= j0[i % 3];
+  }
+  // two passes in sub-simulation order: the mean (Eq. 9), then the squared deviations
+  for (size_t i = 0; i < n3; ++i) {
+    double acc = 0.0;
+    for (size_t m = 0; m < ns; ++m) acc += dj[m * n3 + i];
+    mean[i] = acc / (double)ns;
+    double ss = 0.0;
+    for (size_t m = 0; m < ns; ++m) {
+      const double d = dj[m * n3 + i] - mean[i];
+      ss += d * d;
+    }
+    stderr_out[i] = ns > 1 ? std::sqrt(ss / ((double)ns * (double)(ns - 1))) : 0.0;
+  }
   return TSBZ_OK;
 }
 
@@ -1027,6 +1184,110 @@ int tsbz_set_profiling(tsbz_ctx* ctx, int on) {
 int tsbz_get_timings(tsbz_ctx* ctx, double* times_ms, int n) {
   if (!ctx || !times_ms || n < 0) return TSBZ_EINVAL;
   for (int i = 0; i < n && i < TSBZ_N_FAM; ++i) times_ms[i] = ctx->times[i];
+  return TSBZ_OK;
+}
+
+int tsbz_autotune(tsbz_ctx* ctx, int budget_ms, int* n_tried) {
+  if (!ctx || budget_ms < 0) return TSBZ_EINVAL;
+  int rc = ensure_ready(ctx);
+  if (rc) return rc;
+  bool any = false;
+  for (auto& hs : ctx->subs) any = any || hs.steps < hs.max_steps;
+  if (!any) return set_err(ctx, TSBZ_ESTATE, "every sub-simulation has spent its step budget: nothing to time");
+  Snapshot sn;
+  if ((rc = snapshot_take(ctx, sn))) {
+    if (sn.psi) dfree(ctx, sn.psi);
+    if (sn.P) dfree(ctx, sn.P);
+    return rc;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const bool prof = ctx->prof;
+  ctx->prof = false;
+  const long long launches0 = ctx->launches;
+  constexpr int kTimed = 2, kRounds = 2;   // timed windows of steps per variant, after one untimed step
+  float spent = 0.f;
+  int tried = 0;
+  std::vector<int> before;
+  for (auto& hc : ctx->cells) before.push_back(hc.variant);
+  for (auto& hc : ctx->cells) {
+    if (hc.unit_ids.empty()) continue;
+    const int nv = n_variants(ctx, hc);
+    for (int v = 0; v < TSBZ_MAX_VARIANTS; ++v) hc.tune_ms[v] = 0.0;
+    const int keep = hc.variant < nv ? hc.variant : 0;
+    int best = keep;
+    if (nv > 1) {
+      double best_ms = 0.0;
+      for (int v = 0; v < nv; ++v) {
+        // the default variant is always timed; the others while the budget lasts
+        if (v > 0 && spent >= (float)budget_ms) break;
+        hc.variant = v;
+        rc = ctx->precision == TSBZ_FP64 ? run_step<double>(ctx) : run_step<float>(ctx);
+        if (rc) break;
+        // the faster of kRounds windows of kTimed steps (the first window of a
+        // fresh variant can include one-time costs of its first launches)
+        float best_win = 0.f;
+        for (int r = 0; r < kRounds && !rc; ++r) {
+          cudaEventRecord(e0, ctx->stream);
+          for (int i = 0; i < kTimed && !rc; ++i)
+            rc = ctx->precision == TSBZ_FP64 ? run_step<double>(ctx) : run_step<float>(ctx);
+          cudaEventRecord(e1, ctx->stream);
+          if (rc) break;
+          const cudaError_t es = cudaEventSynchronize(e1);
+          if (es != cudaSuccess) {
+            rc = set_err(ctx, TSBZ_ECUDA, std::string("autotune: ") + cudaGetErrorString(es));
+            break;
+          }
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          spent += ms;
+          best_win = (r == 0 || ms < best_win) ? ms : best_win;
+        }
+        if (rc) break;
+        spent += best_win / kTimed;   // the untimed step
+        hc.tune_ms[v] = best_win / kTimed;
+        ++tried;
+        if (v == 0 || hc.tune_ms[v] < best_ms) {
+          best_ms = hc.tune_ms[v];
+          best = v;
+        }
+      }
+    }
+    hc.variant = best;
+    if (rc) break;
+  }
+  ctx->prof = prof;
+  ctx->launches = launches0;   // trial steps are not part of the run
+  for (size_t i = 0; i < ctx->cells.size(); ++i)
+    if (ctx->cells[i].variant != before[i]) sn.p_next_valid = false;   // P of the old variant's pass
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  const int rr = snapshot_restore(ctx, sn);
+  drop_step_graph(ctx);
+  if (n_tried) *n_tried = tried;
+  return rc ? rc : rr;
+}
+
+int tsbz_get_variant(tsbz_ctx* ctx, int cell_id, int* variant, int* n_variants_out, double* ms, int n_ms) {
+  if (!ctx || cell_id < 0 || cell_id >= (int)ctx->cells.size()) return TSBZ_EINVAL;
+  const HostCell& hc = ctx->cells[cell_id];
+  if (variant) *variant = hc.variant;
+  if (n_variants_out) *n_variants_out = n_variants(ctx, hc);
+  for (int v = 0; ms && v < n_ms && v < TSBZ_MAX_VARIANTS; ++v) ms[v] = hc.tune_ms[v];
+  return TSBZ_OK;
+}
+
+int tsbz_set_variant(tsbz_ctx* ctx, int cell_id, int variant) {
+  if (!ctx || cell_id < 0 || cell_id >= (int)ctx->cells.size()) return TSBZ_EINVAL;
+  HostCell& hc = ctx->cells[cell_id];
+  if (variant < 0 || variant >= n_variants(ctx, hc))
+    return set_err(ctx, TSBZ_EINVAL, "variant out of range for this cell and precision");
+  if (hc.variant != variant) {
+    hc.variant = variant;
+    ctx->p_next_valid = false;   // the projections in P may come from the other variant's pass
+    drop_step_graph(ctx);
+  }
   return TSBZ_OK;
 }
 

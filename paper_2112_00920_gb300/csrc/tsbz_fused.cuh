@@ -27,6 +27,9 @@
 #define FS_NPTS 4096
 #define FS_PU 260          // plane pitch of ubuf in float2 (bank-conflict-free fragment stores)
 #define FS_BKP 36          // row pitch of the ket B matrix in uint2
+#ifndef FS_SPLIT_CHAIN
+#define FS_SPLIT_CHAIN 0
+#endif
 
 __device__ __forceinline__ uint32_t fs_tf32(float x) {
   uint32_t r;
@@ -359,6 +362,7 @@ __global__ void __launch_bounds__(FS_NP, 2) k_stage_fused(LaunchSet L, const flo
   const CellDev& c = L.cell;
   const int b = blockIdx.x % c.n_bands;
   const int u = L.unit_ids[blockIdx.x / c.n_bands];
+  if (!unit_active(L, u)) return;
   const UnitDev U = L.units[u];
   const SubDev S = L.subs[U.sub];
   const int tid = threadIdx.x, col = tid;
@@ -436,20 +440,35 @@ __global__ void __launch_bounds__(FS_NP, 2) k_stage_fused(LaunchSet L, const flo
     const float e_nxt = (z + 1 < N) ? veff[(z + 1) * NP] : 0.f;
     const float2 ce = qv[z + ND];
     const float dg = dg0 + e_cur;
+#if FS_SPLIT_CHAIN
+    // one Laplacian accumulator per axis: three dependency chains of ND
+    // packed FMAs instead of one of 3 ND
+    float2 hx = zero, hy = zero, hz = zero;
+#else
     float2 h = __fmul2_rn(make_float2(dg, dg), ce);
+#endif
     float2 gx = zero, gy = zero, gz = zero;
 #pragma unroll
     for (int mm = 1; mm <= ND; ++mm) {
       const float2 xu = xp[mm - 1][z * NP], xd = xm[mm - 1][z * NP];
       const float2 yu = yp[mm - 1][z * NP], yd = ym[mm - 1][z * NP];
       const float2 zu = qv[z + ND + mm], zd = qv[z + ND - mm];
+#if FS_SPLIT_CHAIN
+      hx = f2fma(c.hlap2[0][mm], __fadd2_rn(xu, xd), hx);
+      hy = f2fma(c.hlap2[1][mm], __fadd2_rn(yu, yd), hy);
+      hz = f2fma(c.hlap2[2][mm], __fadd2_rn(zu, zd), hz);
+#else
       h = f2fma(c.hlap2[0][mm], __fadd2_rn(xu, xd), h);
       h = f2fma(c.hlap2[1][mm], __fadd2_rn(yu, yd), h);
       h = f2fma(c.hlap2[2][mm], __fadd2_rn(zu, zd), h);
+#endif
       gx = f2fma(c.gradw2[0][mm], f2fma(neg1, xd, xu), gx);
       gy = f2fma(c.gradw2[1][mm], f2fma(neg1, yd, yu), gy);
       gz = f2fma(c.gradw2[2][mm], f2fma(neg1, zd, zu), gz);
     }
+#if FS_SPLIT_CHAIN
+    const float2 h = f2fma(make_float2(dg, dg), ce, __fadd2_rn(__fadd2_rn(hx, hy), hz));
+#endif
     float2 qg = __fmul2_rn(make_float2(q0, q0), gx);
     qg = f2fma(make_float2(q1, q1), gy, qg);
     qg = f2fma(make_float2(q2, q2), gz, qg);
@@ -542,6 +561,7 @@ __global__ void __launch_bounds__(FS_NP, 2) k_bra_fused(LaunchSet L, const float
   const CellDev& c = L.cell;
   const int b = blockIdx.x % c.n_bands;
   const int u = L.unit_ids[blockIdx.x / c.n_bands];
+  if (!unit_active(L, u)) return;
   const UnitDev U = L.units[u];
   const int tid = threadIdx.x;
   const float2* ph = (const float2*)L.ph_half + (long long)u * L.ph_stride;
@@ -589,6 +609,7 @@ __global__ void __launch_bounds__(FS_NP, 2) k_observe_fused(LaunchSet L, const f
   FoSmem& sm = *reinterpret_cast<FoSmem*>(fo_raw);
   const CellDev& c = L.cell;
   const int u = L.unit_ids[blockIdx.x];
+  if (!unit_active(L, u)) return;
   const UnitDev U = L.units[u];
   const SubDev S = L.subs[U.sub];
   const int tid = threadIdx.x, col = tid, lane = tid & 31, warp = tid >> 5;

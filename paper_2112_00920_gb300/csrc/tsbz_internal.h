@@ -15,6 +15,7 @@
 #include <vector_types.h>
 
 #define TSBZ_MAX_ND 6
+#define TSBZ_MAX_VARIANTS 4  // kernel variants a cell can be tuned over
 #define TSBZ_PT 128        // points per CTA in the point-parallel kernels
 #define TSBZ_BG 32         // max bands per band group in the point-parallel kernels
 
@@ -75,6 +76,7 @@ struct SubDev {
   double* norms;       // [n_k][n_bands]
   int* step;           // steps done
   int* status;         // non-zero: non-finite current seen
+  int* active;         // 1 while the sub-simulation advances in the current step
 };
 
 // Finalize modes.
@@ -101,7 +103,16 @@ struct LaunchSet {
   void* ph_next;          // q = k + A(t_{n+1} + dt/2): tables of the next step (null if unused)
   long long ph_stride;    // complex elements per unit
   void* qt_half;          // [unit][4] in T: q_x, q_y, q_z, |q|^2 / 2 at t_n + dt/2
+  int variant;            // kernel variant of this cell (0 = default; chosen by the autotuner)
 };
+
+#ifdef __CUDACC__
+// A unit takes part in a time step only while its sub-simulation has steps
+// left in its budget; the field kernel writes the flag at the start of the step.
+__device__ __forceinline__ bool unit_active(const LaunchSet& L, int u) {
+  return *L.subs[L.units[u].sub].active != 0;
+}
+#endif
 
 // Launchers (templated on the real type in tsbz_kernels.cuh, instantiated per precision).
 template <typename T> void launch_field(const LaunchSet& L, int mode, void* stream);

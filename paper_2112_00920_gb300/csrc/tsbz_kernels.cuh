@@ -77,6 +77,12 @@ __global__ void k_field(LaunchSet L, int mode) {
   const UnitDev U = L.units[u];
   const SubDev S = L.subs[U.sub];
   const CellDev& c = L.cell;
+  // step budget: a sub-simulation that has done max_steps steps sits out the
+  // step (every later kernel of the step reads the flag); the evaluations of
+  // J(0-), J(0+) and of a restored state take part whatever the step count
+  const bool act = mode != TSBZ_FIELD_STEP || *S.step < S.max_steps;
+  if (U.kloc == 0 && threadIdx.x == 0) *S.active = act ? 1 : 0;
+  if (!act) return;
   double ah[3] = {0.0, 0.0, 0.0}, ao[3] = {0.0, 0.0, 0.0};
   if (mode == TSBZ_FIELD_STEP) {
     const int step = *S.step;
@@ -150,6 +156,7 @@ __global__ void __launch_bounds__(256) k_bra(LaunchSet L, const typename Cplx<T>
   __shared__ V red[RB][BB];
   const CellDev& c = L.cell;
   const int u = L.unit_ids[blockIdx.z];
+  if (!unit_active(L, u)) return;
   const UnitDev U = L.units[u];
   const int rows = c.n_proj * NW;
   const int a0 = blockIdx.x * APB;
@@ -260,6 +267,7 @@ __global__ void __launch_bounds__(TSBZ_PT) k_stage(LaunchSet L, const typename C
   V* Ws = reinterpret_cast<V*>(smraw);
   const CellDev& c = L.cell;
   const int u = L.unit_ids[blockIdx.y];
+  if (!unit_active(L, u)) return;
   const UnitDev U = L.units[u];
   const SubDev S = L.subs[U.sub];
   const int p = blockIdx.x * TSBZ_PT + threadIdx.x;
@@ -381,6 +389,7 @@ __global__ void __launch_bounds__(TSBZ_PT) k_stage_v(LaunchSet L, const typename
   using VT = typename Cplx<T>::type;
   const CellDev& c = L.cell;
   const int u = L.unit_ids[blockIdx.y];
+  if (!unit_active(L, u)) return;
   const UnitDev U = L.units[u];
   const SubDev S = L.subs[U.sub];
   const int p = blockIdx.x * TSBZ_PT + threadIdx.x;
@@ -459,6 +468,7 @@ __global__ void __launch_bounds__(256, 4) k_stage_z(LaunchSet L, const typename 
   const CellDev& c = L.cell;
   const int b = blockIdx.x;
   const int u = L.unit_ids[blockIdx.y];
+  if (!unit_active(L, u)) return;
   const UnitDev U = L.units[u];
   const SubDev S = L.subs[U.sub];
   const int n1 = c.n1, n2 = c.n2, n3 = c.n3, n12 = n1 * n2;
@@ -565,6 +575,7 @@ __global__ void __launch_bounds__(TSBZ_PT) k_observe(LaunchSet L, const typename
   }
   __syncthreads();
   const int u = L.unit_ids[blockIdx.y];
+  if (!unit_active(L, u)) return;
   const UnitDev U = L.units[u];
   const int tile = blockIdx.x, grp = blockIdx.z;
   const int p = tile * TSBZ_PT + threadIdx.x;
@@ -642,6 +653,7 @@ __global__ void __launch_bounds__(256) k_finalize(const SubDev* subs, const Unit
   __shared__ double red[8][3];
   const int s = blockIdx.x;
   const SubDev S = subs[s];
+  if (mode == TSBZ_FIN_STEP && !*S.active) return;   // budget spent: nothing of this step
   const CellDev c = cells[S.cell];
   // density: point tile blockIdx.y of the sub-simulation (fixed k and band-group order per point)
   const double inv_nk = 1.0 / S.n_k;
@@ -822,6 +834,11 @@ __global__ void k_convert_out(const typename Cplx<T>::type* __restrict__ src, do
 // ----------------------------------------------------------------------------
 // launchers
 // ----------------------------------------------------------------------------
+// Dynamic shared memory above the 48 KiB default needs the kernel's opt-in.
+template <typename K> void stage_smem_attr(K* kernel, size_t bytes) {
+  if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 template <typename T> void launch_field(const LaunchSet& L, int mode, void* stream) {
   if (L.n_units == 0) return;
   k_field<T><<<L.n_units, 128, 0, (cudaStream_t)stream>>>(L, mode);
@@ -843,10 +860,21 @@ template <typename T>
 void launch_stage(const LaunchSet& L, const void* tin, void* tout, void* psi, const void* P, int m, void* stream) {
   using V = typename Cplx<T>::type;
   if (L.n_units == 0) return;
-  constexpr int BC = 8;
+  // bands per chunk of the staged projections: 8 (variant 0), 4 (1) or 16 (2)
+  const int bc = L.variant == 1 ? 4 : (L.variant == 2 ? 16 : 8);
   dim3 grid(L.cell.n_tiles, L.n_units);
-  const size_t sm = (size_t)BC * (L.cell.n_proj > 0 ? L.cell.n_proj : 1) * sizeof(V);
-  k_stage<T, BC><<<grid, TSBZ_PT, sm, (cudaStream_t)stream>>>(L, (const V*)tin, (V*)tout, (V*)psi, (const V*)P, m);
+  const size_t sm = (size_t)bc * (L.cell.n_proj > 0 ? L.cell.n_proj : 1) * sizeof(V);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (bc == 4) {
+    stage_smem_attr(k_stage<T, 4>, sm);
+    k_stage<T, 4><<<grid, TSBZ_PT, sm, st>>>(L, (const V*)tin, (V*)tout, (V*)psi, (const V*)P, m);
+  } else if (bc == 16) {
+    stage_smem_attr(k_stage<T, 16>, sm);
+    k_stage<T, 16><<<grid, TSBZ_PT, sm, st>>>(L, (const V*)tin, (V*)tout, (V*)psi, (const V*)P, m);
+  } else {
+    stage_smem_attr(k_stage<T, 8>, sm);
+    k_stage<T, 8><<<grid, TSBZ_PT, sm, st>>>(L, (const V*)tin, (V*)tout, (V*)psi, (const V*)P, m);
+  }
 }
 
 template <typename T>

@@ -14,7 +14,7 @@ void launch_bra_sep(const LaunchSet& L, const void* src, void* out, int with_d, 
   if (L.n_units == 0 || !L.cell.use_proj) return;
   const unsigned grid = (unsigned)L.n_units * (unsigned)L.cell.n_bands;
   const CellDev& c = L.cell;
-  if (!with_d && !use_obs && L.ph_next != nullptr && c.n1 == 16 && c.n2 == 16 && c.n3 == 16) {
+  if (L.variant == 0 && !with_d && !use_obs && L.ph_next != nullptr && c.n1 == 16 && c.n2 == 16 && c.n3 == 16) {
     // the projections the 16^3 fused stage leaves are formed by the same pass
     static bool attr = false;
     if (!attr) {
@@ -62,7 +62,9 @@ bool launch_stage_sep(const LaunchSet& L, const void* tin, void* tout, void* psi
   if (L.n_units == 0) return false;
   const CellDev& c = L.cell;
   cudaStream_t st = (cudaStream_t)stream;
-  const bool next = L.ph_next != nullptr;
+  // variant 0: the fused tensor-core stage (16^3) or the bulk-staged stage (8^3);
+  // variant 1: the z-march stage with CUDA-core projections on every shape
+  const bool next = L.ph_next != nullptr && L.variant == 0;
   if (next && c.n1 == 16 && c.n2 == 16 && c.n3 == 16) {
     static bool attr = false;
     if (!attr) {

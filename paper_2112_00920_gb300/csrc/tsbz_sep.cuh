@@ -353,6 +353,7 @@ __global__ void __launch_bounds__(256, 2) k_stage_sep(LaunchSet L, const float2*
   const CellDev& c = L.cell;
   const int b = blockIdx.x % c.n_bands;
   const int u = L.unit_ids[blockIdx.x / c.n_bands];
+  if (!unit_active(L, u)) return;
   const UnitDev U = L.units[u];
   const SubDev S = L.subs[U.sub];
   const int n1 = c.n1, n2 = c.n2, n12 = n1 * n2;
@@ -470,6 +471,7 @@ __global__ void __launch_bounds__(256) k_bra_sep(LaunchSet L, const float2* __re
   const CellDev& c = L.cell;
   const int b = blockIdx.x % c.n_bands;
   const int u = L.unit_ids[blockIdx.x / c.n_bands];
+  if (!unit_active(L, u)) return;
   const UnitDev U = L.units[u];
   const int n1 = c.n1, n12 = n1 * c.n2;
   const int col = threadIdx.x;
@@ -521,6 +523,7 @@ __global__ void __launch_bounds__(N * N, (N == 16 ? SEP_BULK_MINB : 8))
   const CellDev& c = L.cell;
   const int b = blockIdx.x % c.n_bands;
   const int u = L.unit_ids[blockIdx.x / c.n_bands];
+  if (!unit_active(L, u)) return;
   const UnitDev U = L.units[u];
   const SubDev S = L.subs[U.sub];
   const int col = threadIdx.x;

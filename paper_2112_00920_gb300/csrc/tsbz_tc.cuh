@@ -223,6 +223,7 @@ __global__ void __launch_bounds__(256, 2) k_bra_w(LaunchSet L, const float2* __r
   TwSmem& sm = *reinterpret_cast<TwSmem*>(tw_raw);
   const CellDev& c = L.cell;
   const int u = L.unit_ids[blockIdx.x];
+  if (!unit_active(L, u)) return;
   const UnitDev U = L.units[u];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const float2* ph = (const float2*)(with_d ? L.ph_obs : L.ph_half) + (long long)u * L.ph_stride;
@@ -306,6 +307,7 @@ __global__ void __launch_bounds__(256, 2) k_ket_w(LaunchSet L, const float2* __r
   TwSmem& sm = *reinterpret_cast<TwSmem*>(tw_raw);
   const CellDev& c = L.cell;
   const int u = L.unit_ids[blockIdx.y];
+  if (!unit_active(L, u)) return;
   const UnitDev U = L.units[u];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, t4 = lane & 3;
@@ -403,6 +405,7 @@ __global__ void __launch_bounds__(256, 4) k_stage_zf(LaunchSet L, const float2* 
   const CellDev& c = L.cell;
   const int b = blockIdx.x;
   const int u = L.unit_ids[blockIdx.y];
+  if (!unit_active(L, u)) return;
   const UnitDev U = L.units[u];
   const SubDev S = L.subs[U.sub];
   const int n1 = c.n1, n2 = c.n2, n12 = n1 * n2;
@@ -497,6 +500,7 @@ __global__ void __launch_bounds__(256) k_observe_zf(LaunchSet L, const float2* _
   __shared__ double redj[8][3];
   const CellDev& c = L.cell;
   const int u = L.unit_ids[blockIdx.x];
+  if (!unit_active(L, u)) return;
   const UnitDev U = L.units[u];
   const int n1 = c.n1, n2 = c.n2, n12 = n1 * n2;
   const int col = threadIdx.x;

@@ -283,8 +283,14 @@ def test_error_paths():
     with pytest.raises(TsbzError) as e:
         P.propagate(1)
     assert e.value.code == -5
+    # step budget (max_steps = 3): the sub-simulation stops at 3 steps, not an error
+    # in itself; the non-finite status of the earlier step is still reported
     with pytest.raises(TsbzError) as e:
         P.propagate(5)
+    assert e.value.code == -5
+    assert P.step(sid) == 3
+    with pytest.raises(TsbzError) as e:
+        P.propagate(-1)
     assert e.value.code == -1
     P.close()
 
