@@ -38,6 +38,7 @@ struct HostCell {
   int* d_hxc_subs = nullptr;
   bool pa_by_stage = false;    // the last stage 4 also wrote P (next step) and Pa
   int variant = 0;             // kernel variant (tsbz_autotune / tsbz_set_variant)
+  bool tables_step = false;    // the phase tables hold a time step's q (not J(0-/0+) tables)
   double tune_ms[TSBZ_MAX_VARIANTS] = {0, 0, 0, 0};   // ms per step measured per variant
 };
 
@@ -383,7 +384,10 @@ template <typename T> int run_field(tsbz_ctx* ctx, int mode) {
   ev_start(ctx, FAM_FIELD);
   for (auto& hc : ctx->cells) {
     if (hc.unit_ids.empty()) continue;
-    launch_field<T>(make_set(ctx, hc), mode, ctx->stream);
+    // a constant field leaves the phase tables of the last step current
+    const bool keep = mode == TSBZ_FIELD_STEP && hc.tables_step && cell_field_const(ctx, hc);
+    launch_field<T>(make_set(ctx, hc), keep ? TSBZ_FIELD_STEP_KEEP : mode, ctx->stream);
+    hc.tables_step = mode == TSBZ_FIELD_STEP;
     ++ctx->launches;
   }
   ev_stop(ctx);
@@ -884,6 +888,39 @@ int tsbz_init_cell(tsbz_ctx* ctx, const tsbz_cell_desc* d, int* cell_id) {
   c.d1f = ddf;
   c.pnormf = pnff;
   c.wkbf = wkff;
+  // z groups: atoms with bit-identical z rows of the float factor tables
+  c.n_zg = 0;
+  for (int i = 0; i < 8; ++i) c.zg_of[i] = c.zg_rep[i] = c.zg_mem[i] = 0;
+  for (int i = 0; i <= 8; ++i) c.zg_off[i] = 0;
+  if (c.use_proj && d->n_atoms <= 8) {
+    const int nm = c.nmax;
+    auto same_z = [&](int a, int b) {
+      for (int i = 0; i < nm; ++i) {
+        const size_t ia = (size_t)(a * 3 + 2) * nm + i, ib = (size_t)(b * 3 + 2) * nm + i;
+        if (g1f[ia] != g1f[ib] || d1f[ia] != d1f[ib]) return false;
+      }
+      return true;
+    };
+    for (int a = 0; a < 8; ++a) c.zg_of[a] = 0;
+    for (int a = 0; a < d->n_atoms; ++a) {
+      int g = -1;
+      for (int h = 0; h < c.n_zg && g < 0; ++h)
+        if (same_z(a, c.zg_rep[h])) g = h;
+      if (g < 0) {
+        g = c.n_zg++;
+        c.zg_rep[g] = a;
+      }
+      c.zg_of[a] = g;
+    }
+    int k = 0;
+    for (int g = 0; g < c.n_zg; ++g) {
+      c.zg_off[g] = k;
+      for (int a = 0; a < d->n_atoms; ++a)
+        if (c.zg_of[a] == g) c.zg_mem[k++] = a;
+    }
+    for (int g = c.n_zg; g <= 8; ++g) c.zg_off[g] = k;
+    for (int g = c.n_zg; g < 8; ++g) c.zg_rep[g] = 0;
+  }
   const int nn[3] = {c.n1, c.n2, c.n3};
   for (int ax = 0; ax < 3; ++ax) {
     std::vector<double2> tw(nn[ax]);
@@ -1056,11 +1093,13 @@ int tsbz_get_current_stats(tsbz_ctx* ctx, int first, int count, double* mean, do
     CK(cudaMemcpy(j0.data(), hs.J0m, sizeof(double) * 3, cudaMemcpyDeviceToHost));
     for (size_t i = 0; i < n3; ++i) dj[m * n3 + i] -= j0[i % 3];
   }
-  // two passes in sub-simulation order: the mean (Eq. 9), then the squared deviations
+  // two passes in sub-simulation order: the mean (Eq. 9, the same arithmetic
+  // as tsbz_get_current(-1)), then the squared deviations
+  const double inv = 1.0 / (double)ns;
   for (size_t i = 0; i < n3; ++i) {
     double acc = 0.0;
     for (size_t m = 0; m < ns; ++m) acc += dj[m * n3 + i];
-    mean[i] = acc / (double)ns;
+    mean[i] = acc * inv;
     double ss = 0.0;
     for (size_t m = 0; m < ns; ++m) {
       const double d = dj[m * n3 + i] - mean[i];

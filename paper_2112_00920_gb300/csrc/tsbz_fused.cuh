@@ -27,9 +27,6 @@
 #define FS_NPTS 4096
 #define FS_PU 260          // plane pitch of ubuf in float2 (bank-conflict-free fragment stores)
 #define FS_BKP 36          // row pitch of the ket B matrix in uint2
-#ifndef FS_SPLIT_CHAIN
-#define FS_SPLIT_CHAIN 0
-#endif
 
 __device__ __forceinline__ uint32_t fs_tf32(float x) {
   uint32_t r;
@@ -73,8 +70,29 @@ struct FsSmem {
   float2 gt[SEP_NA * 3 * FS_N];      // ket column tables G00, G10, G01 per atom and ix
   float2 wt[SEP_NP];                 // pn E P of the band
   float2 mres[SEP_NA * 10];          // monomial sums of one projection pass
+  float vbuf[FS_NPTS];               // v_eff of the sub-simulation (stage kernel)
+  int zg[SEP_NA];                    // z group of atom a
+  int zrep[4];                       // first atom of group g
+  int zmem[4][2];                    // the (at most two) atoms of group g
+  int zcnt[4];
   unsigned long long mbar;
 };
+
+// z group tables of the cell into shared memory (grouped kernels; read after
+// the next barrier)
+template <int NZU> __device__ __forceinline__ void fz_load(FsSmem& sm, const CellDev& c) {
+  if constexpr (NZU != SEP_NA) {
+    const int t = threadIdx.x;
+    if (t < SEP_NA) sm.zg[t] = c.zg_of[t];
+    if (t < 4) {
+      const int lo = c.zg_off[t], n = c.zg_off[t + 1] - lo;
+      sm.zrep[t] = c.zg_rep[t];
+      sm.zcnt[t] = n;
+      sm.zmem[t][0] = n > 0 ? c.zg_mem[lo] : 0;
+      sm.zmem[t][1] = n > 1 ? c.zg_mem[lo + 1] : 0;
+    }
+  }
+}
 
 // z factors of one phase table
 __device__ __forceinline__ void fs_load_z(float4* zt, const CellDev& c, const float2* ph) {
@@ -110,10 +128,30 @@ __device__ __forceinline__ int fs_mono(int i, int j, int k) {
   return j ? 8 : 9;
 }
 
+// z groups (atoms with identical z factor tables, see CellDev): with NZU =
+// SEP_NA every atom is its own group; with NZU < SEP_NA the cell's groups
+// (at most NZU of them) are used and every z contraction runs per group.
+template <int NZU> __device__ __forceinline__ int fz_grp(const FsSmem& sm, int a) {
+  if constexpr (NZU == SEP_NA) return a; else return sm.zg[a];
+}
+template <int NZU> __device__ __forceinline__ float4 fz_table(const FsSmem& sm, const CellDev& c, int g, int z) {
+  if constexpr (NZU == SEP_NA) {
+    return sm.zt[g * FS_N + z];
+  } else {
+    return g < c.n_zg ? sm.zt[sm.zrep[g] * FS_N + z] : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
 // ----------------------------------------------------------------------------
-// ket: ubuf[z][col] = conj(V_NL t)(col, z) for the warp's 32 columns
+// ket: ubuf[z][col] = conj(V_NL t)(col, z) for the warp's 32 columns.  The z
+// dependence is a GEMM over q = (z group, {F_z, d_z F_z}): column coefficient
+// A[col][q] = sum over the group's atoms of F_y (G00 + d_y G10) or F_y G01.
 // ----------------------------------------------------------------------------
+template <int NZU>
 __device__ __forceinline__ void fs_ket(FsSmem& sm, const CellDev& c) {
+  constexpr int Q = 2 * NZU;   // complex columns of the GEMM
+  constexpr int KS = Q / 4;    // k steps of 8 over the 2 Q real rows (Re rows, then Im rows)
+  constexpr int NI = Q / 4;    // q values per thread: t4 + 4 i
   const int tid = threadIdx.x;
   // column tables G00, G10, G01 (conj W) and the B matrix B[k][n], k < 16: Re rows,
   // k >= 16: Im rows of q = (a, w); n = 2 z + c
@@ -127,47 +165,62 @@ __device__ __forceinline__ void fs_ket(FsSmem& sm, const CellDev& c) {
     sm.gt[(a * 3 + 1) * FS_N + ix] = sep_cmul(F, make_float2(wy.x, -wy.y));
     sm.gt[(a * 3 + 2) * FS_N + ix] = sep_cmul(F, make_float2(wz.x, -wz.y));
   }
-  for (int i = tid; i < 32 * 2 * FS_N; i += blockDim.x) {
+  for (int i = tid; i < 2 * Q * 2 * FS_N; i += blockDim.x) {
     const int k = i / (2 * FS_N), n = i - k * 2 * FS_N;
-    const int q = k & 15, z = n >> 1, cc = n & 1;
-    const float4 f = sm.zt[(q >> 1) * FS_N + z];
+    const bool rrow = k < Q;
+    const int q = rrow ? k : k - Q, z = n >> 1, cc = n & 1;
+    const float4 f = fz_table<NZU>(sm, c, q >> 1, z);
     const float s = (q & 1) ? f.z : 1.f;
     const float zr = s * f.x, zi = s * f.y;
-    const float v = (k < 16) ? (cc ? zi : zr) : (cc ? zr : -zi);
+    const float v = rrow ? (cc ? zi : zr) : (cc ? zr : -zi);
     sm.bk[k * FS_BKP + n] = fs_split2(v);
   }
   __syncthreads();
   const int lane = tid & 31, warp = tid >> 5, g = lane >> 2, t4 = lane & 3;
   // A fragments of both m-tiles: rows = columns 32 warp + 16 mt + g (+8), k = 8 ks + t4 (+4)
-  uint32_t ah[2][4][4], al[2][4][4];
+  uint32_t ah[2][KS][4], al[2][KS][4];
 #pragma unroll
   for (int mt = 0; mt < 2; ++mt) {
     const int iyc = 2 * warp + mt;
-    float re[2][4], im[2][4];   // [column A/B][q index i: q = t4 + 4 i]
+    float re[2][NI], im[2][NI];   // [column A/B][q index i: q = t4 + 4 i]
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int q = t4 + 4 * i, a = q >> 1;
-      const float4 fy = sm.colt[(2 * a + 1) * FS_N + iyc];
-      const float2 F = make_float2(fy.x, fy.y);
+    for (int i = 0; i < NI; ++i) {
+      const int q = t4 + 4 * i, gq = q >> 1;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int ixc = g + 8 * h;
-        float2 v;
-        if (q & 1) {
-          v = sep_cmul(F, sm.gt[(a * 3 + 2) * FS_N + ixc]);
+        float2 v = make_float2(0.f, 0.f);
+        auto add_atom = [&](int a) {
+          const float4 fy = sm.colt[(2 * a + 1) * FS_N + iyc];
+          const float2 F = make_float2(fy.x, fy.y);
+          float2 w;
+          if (q & 1) {
+            w = sep_cmul(F, sm.gt[(a * 3 + 2) * FS_N + ixc]);
+          } else {
+            const float2 g0 = sm.gt[(a * 3 + 0) * FS_N + ixc], g1 = sm.gt[(a * 3 + 1) * FS_N + ixc];
+            w = sep_cmul(F, make_float2(g0.x + fy.z * g1.x, g0.y + fy.z * g1.y));
+          }
+          v.x += w.x;
+          v.y += w.y;
+        };
+        if constexpr (NZU == SEP_NA) {
+          add_atom(gq);
         } else {
-          const float2 g0 = sm.gt[(a * 3 + 0) * FS_N + ixc], g1 = sm.gt[(a * 3 + 1) * FS_N + ixc];
-          v = sep_cmul(F, make_float2(g0.x + fy.z * g1.x, g0.y + fy.z * g1.y));
+          const int cnt = sm.zcnt[gq];
+#pragma unroll
+          for (int j = 0; j < 2; ++j)
+            if (j < cnt) add_atom(sm.zmem[gq][j]);
         }
         re[h][i] = v.x;
         im[h][i] = v.y;
       }
     }
-    // ks 0, 1: Re of q = t4 + 8 ks (+4); ks 2, 3: Im
+    // the first KS/2 k steps: Re of q = t4 + 8 ks (+4); the others: Im
 #pragma unroll
-    for (int ks = 0; ks < 4; ++ks) {
-      const int i0 = 2 * (ks & 1);
-      const float(&src)[2][4] = (ks < 2) ? re : im;
+    for (int ks = 0; ks < KS; ++ks) {
+      const bool rpart = ks < KS / 2;
+      const int i0 = 2 * (rpart ? ks : ks - KS / 2);
+      const float(&src)[2][NI] = rpart ? re : im;
       fs_split(src[0][i0], ah[mt][ks][0], al[mt][ks][0]);
       fs_split(src[1][i0], ah[mt][ks][1], al[mt][ks][1]);
       fs_split(src[0][i0 + 1], ah[mt][ks][2], al[mt][ks][2]);
@@ -178,7 +231,7 @@ __device__ __forceinline__ void fs_ket(FsSmem& sm, const CellDev& c) {
   for (int nt = 0; nt < (2 * FS_N) / 8; ++nt) {
     float d[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
 #pragma unroll
-    for (int ks = 0; ks < 4; ++ks) {
+    for (int ks = 0; ks < KS; ++ks) {
       const uint2 b0 = sm.bk[(8 * ks + t4) * FS_BKP + 8 * nt + g];
       const uint2 b1 = sm.bk[(8 * ks + t4 + 4) * FS_BKP + 8 * nt + g];
       fs_mma3(d[0], ah[0][ks], al[0][ks], b0, b1);
@@ -195,14 +248,16 @@ __device__ __forceinline__ void fs_ket(FsSmem& sm, const CellDev& c) {
 }
 
 // ----------------------------------------------------------------------------
-// Projection pass: monomial sums up to degree D of the atoms covered by the
-// z-weights q' = q0 .. q0 + NQ - 1 (q' = (D + 1) a + k, k = power of d_z),
+// Projection pass: monomial sums up to degree D of the atoms a0 .. a0 + NAP - 1,
 // from the split A fragments of u (ah/al) and the tables zt / colt of the
-// pass.  Leaves mres[a_local * NM + mono] (NM = 4 for D = 1, 10 for D = 2).
+// pass.  The z contraction covers the z weights q' = q0 .. q0 + NQ - 1 with
+// q' = (D + 1) g + k (g the z group, k the power of d_z); the x and y
+// contractions run per atom on the z sums of its group.  Leaves
+// mres[(a - a0) * NM + mono] (NM = 4 for D = 1, 10 for D = 2).
 // ----------------------------------------------------------------------------
-template <int D, int NQ>
-__device__ __forceinline__ void fs_project_pass(FsSmem& sm, int q0, const uint32_t (&ah)[2][4][4],
-                                                const uint32_t (&al)[2][4][4]) {
+template <int D, int NQ, int NAP, int NZU>
+__device__ __forceinline__ void fs_project_pass(FsSmem& sm, const CellDev& c, int q0, int a0,
+                                                const uint32_t (&ah)[2][4][4], const uint32_t (&al)[2][4][4]) {
   constexpr int NPR = 2 * NQ;          // real n of the pass
   constexpr int BZP = NPR + 4;         // B_z row pitch (uint2)
   constexpr int NM = D == 1 ? 4 : 10;
@@ -213,8 +268,8 @@ __device__ __forceinline__ void fs_project_pass(FsSmem& sm, int q0, const uint32
   for (int i = tid; i < 32 * NPR; i += blockDim.x) {
     const int k = i / NPR, n = i - k * NPR;
     const int z = k >> 1, cu = k & 1, qq = q0 + (n >> 1), cs = n & 1;
-    const int a = qq / (D + 1), kz = qq - a * (D + 1);
-    const float4 f = sm.zt[a * FS_N + z];
+    const int gz = qq / (D + 1), kz = qq - gz * (D + 1);
+    const float4 f = fz_table<NZU>(sm, c, gz, z);
     const float s = kz == 0 ? 1.f : (kz == 1 ? f.z : f.z * f.z);
     const float zr = s * f.x, zi = s * f.y;
     const float v = cs == 0 ? (cu == 0 ? zr : -zi) : (cu == 0 ? zi : zr);
@@ -244,19 +299,20 @@ __device__ __forceinline__ void fs_project_pass(FsSmem& sm, int q0, const uint32
   // x contraction per row (q', iy): R_i = sum_ix F_x d_x^i S, i <= D - k; then the
   // y contraction M_a(i, j, k) = sum_iy F_y d_y^j R_i over the 16 lanes of the
   // half-warp that holds the rows iy = 0..15 of one q' (fixed-order shuffles).
-  constexpr int NR = NQ * FS_N;
+  constexpr int NR = (D + 1) * NAP * FS_N;
   for (int r0 = 0; r0 < NR; r0 += FS_NP) {
     const int r = r0 + tid;
     const bool live = r < NR;
     const int ql = live ? (r >> 4) : 0, iyr = r & 15;
-    const int qq = q0 + ql, a = qq / (D + 1), kz = qq - a * (D + 1);
+    const int al_ = ql / (D + 1), kz = ql - al_ * (D + 1), a = a0 + al_;
+    const int sq = (D + 1) * fz_grp<NZU>(sm, a) + kz - q0;   // z sums of the atom's group
     // explicit round-to-nearest operations (no contraction), so that the sums a
     // D = 1 pass and a D = 2 pass have in common come out bit for bit the same
     float2 R0 = make_float2(0.f, 0.f), R1 = R0, R2 = R0;
     if (live) {
 #pragma unroll 4
       for (int ixr = 0; ixr < FS_N; ++ixr) {
-        const float2 s = sbuf[ql * FS_NP + iyr * FS_N + (ixr ^ iyr)];
+        const float2 s = sbuf[sq * FS_NP + iyr * FS_N + (ixr ^ iyr)];
         const float4 fx = sm.colt[(2 * a) * FS_N + ixr];
         const float2 p = fs_cmul_rn(make_float2(fx.x, fx.y), s);
         R0.x = __fadd_rn(R0.x, p.x);
@@ -297,7 +353,7 @@ __device__ __forceinline__ void fs_project_pass(FsSmem& sm, int q0, const uint32
         v[e].y = __fadd_rn(v[e].y, __shfl_xor_sync(0xffffffffu, v[e].y, off));
       }
     if (live && iyr == 0) {
-      float2* M = sm.mres + (a - q0 / (D + 1)) * NM;
+      float2* M = sm.mres + al_ * NM;
       if (D == 1) {
         if (kz == 0) {
           M[0] = v[0];
@@ -352,6 +408,7 @@ __device__ __forceinline__ void fs_load_u(const FsSmem& sm, uint32_t (&ah)[2][4]
 // accumulation, the projections of t_m (m < 4) or, at m = 4, those of
 // psi(t_{n+1}) for the next step (P) and for the current (Pa).
 // ----------------------------------------------------------------------------
+template <int NZU>
 __global__ void __launch_bounds__(FS_NP, 2) k_stage_fused(LaunchSet L, const float2* __restrict__ tin,
                                                           float2* __restrict__ tout, float2* __restrict__ psi,
                                                           float2* __restrict__ P, float2* __restrict__ Pa, int m,
@@ -374,10 +431,13 @@ __global__ void __launch_bounds__(FS_NP, 2) k_stage_fused(LaunchSet L, const flo
   const float2 zero = make_float2(0.f, 0.f);
   const uint32_t bar = bk_smem(&sm.mbar);
   if (tid == 0) bk_mbar_init(bar, 1);
+  fz_load<NZU>(sm, c);
   __syncthreads();
   if (tid == 0) {
-    bk_mbar_expect_tx(bar, FS_NPTS * (uint32_t)sizeof(float2));
+    // the band of t_{m-1} and the sub-simulation's v_eff, on one barrier
+    bk_mbar_expect_tx(bar, FS_NPTS * (uint32_t)(sizeof(float2) + sizeof(float)));
     bk_copy_g2s(bk_smem(sm.tbuf), tin + base, FS_NPTS * sizeof(float2), bar);
+    bk_copy_g2s(bk_smem(sm.vbuf), S.veff, FS_NPTS * sizeof(float), bar);
   }
   // psi of the column in registers (m >= 2), in flight while the ket runs
   float2 pq[N];
@@ -398,7 +458,7 @@ __global__ void __launch_bounds__(FS_NP, 2) k_stage_fused(LaunchSet L, const flo
   }
   __syncthreads();
   if (proj) {
-    fs_ket(sm, c);
+    fs_ket<NZU>(sm, c);
   } else {
 #pragma unroll
     for (int z = 0; z < N; ++z) sm.ubuf[z * FS_PU + col] = zero;
@@ -407,8 +467,6 @@ __global__ void __launch_bounds__(FS_NP, 2) k_stage_fused(LaunchSet L, const flo
   const float q0 = qt[0], q1 = qt[1], q2 = qt[2];
   const float dg0 = c.hlapf[0][0] + c.hlapf[1][0] + c.hlapf[2][0] + qt[3];
   const float hdt = (float)S.dt / (float)m;
-  const float* veff = reinterpret_cast<const float*>(S.veff) + col;
-  float e_cur = veff[0];
   const bool ok = bk_mbar_wait(bar, 0, BK_WAIT_POLLS);
   if (!__syncthreads_and(ok)) {
     if (tid == 0) {
@@ -437,38 +495,22 @@ __global__ void __launch_bounds__(FS_NP, 2) k_stage_fused(LaunchSet L, const flo
 #pragma unroll
   for (int z = 0; z < N; ++z) {
     qv[z + 2 * ND] = cz[((z + ND) & (N - 1)) * NP];
-    const float e_nxt = (z + 1 < N) ? veff[(z + 1) * NP] : 0.f;
     const float2 ce = qv[z + ND];
-    const float dg = dg0 + e_cur;
-#if FS_SPLIT_CHAIN
-    // one Laplacian accumulator per axis: three dependency chains of ND
-    // packed FMAs instead of one of 3 ND
-    float2 hx = zero, hy = zero, hz = zero;
-#else
+    const float dg = dg0 + sm.vbuf[z * NP + col];
     float2 h = __fmul2_rn(make_float2(dg, dg), ce);
-#endif
     float2 gx = zero, gy = zero, gz = zero;
 #pragma unroll
     for (int mm = 1; mm <= ND; ++mm) {
       const float2 xu = xp[mm - 1][z * NP], xd = xm[mm - 1][z * NP];
       const float2 yu = yp[mm - 1][z * NP], yd = ym[mm - 1][z * NP];
       const float2 zu = qv[z + ND + mm], zd = qv[z + ND - mm];
-#if FS_SPLIT_CHAIN
-      hx = f2fma(c.hlap2[0][mm], __fadd2_rn(xu, xd), hx);
-      hy = f2fma(c.hlap2[1][mm], __fadd2_rn(yu, yd), hy);
-      hz = f2fma(c.hlap2[2][mm], __fadd2_rn(zu, zd), hz);
-#else
       h = f2fma(c.hlap2[0][mm], __fadd2_rn(xu, xd), h);
       h = f2fma(c.hlap2[1][mm], __fadd2_rn(yu, yd), h);
       h = f2fma(c.hlap2[2][mm], __fadd2_rn(zu, zd), h);
-#endif
       gx = f2fma(c.gradw2[0][mm], f2fma(neg1, xd, xu), gx);
       gy = f2fma(c.gradw2[1][mm], f2fma(neg1, yd, yu), gy);
       gz = f2fma(c.gradw2[2][mm], f2fma(neg1, zd, zu), gz);
     }
-#if FS_SPLIT_CHAIN
-    const float2 h = f2fma(make_float2(dg, dg), ce, __fadd2_rn(__fadd2_rn(hx, hy), hz));
-#endif
     float2 qg = __fmul2_rn(make_float2(q0, q0), gx);
     qg = f2fma(make_float2(q1, q1), gy, qg);
     qg = f2fma(make_float2(q2, q2), gz, qg);
@@ -488,7 +530,6 @@ __global__ void __launch_bounds__(FS_NP, 2) k_stage_fused(LaunchSet L, const flo
       psi[idx] = uo;
     }
     sm.ubuf[z * FS_PU + col] = uo;
-    e_cur = e_nxt;
   }
   if (!proj) return;
   __syncthreads();
@@ -496,7 +537,7 @@ __global__ void __launch_bounds__(FS_NP, 2) k_stage_fused(LaunchSet L, const flo
   fs_load_u(sm, ah, al);
   __syncthreads();   // ubuf free for the z sums
   if (m < 4) {
-    fs_project_pass<1, 2 * SEP_NA>(sm, 0, ah, al);
+    fs_project_pass<1, 2 * NZU, SEP_NA, NZU>(sm, c, 0, 0, ah, al);
     const int j = tid;
     if (j < c.n_proj) {
       const float2 M = sm.mres[(j >> 2) * 4 + (j & 3)];
@@ -514,7 +555,7 @@ __global__ void __launch_bounds__(FS_NP, 2) k_stage_fused(LaunchSet L, const flo
     fs_load_z(sm.zt, c, phn);
     sep_load_cols<N>(sm.colt, c, phn);
     __syncthreads();
-    fs_project_pass<1, 2 * SEP_NA>(sm, 0, ah, al);
+    fs_project_pass<1, 2 * NZU, SEP_NA, NZU>(sm, c, 0, 0, ah, al);
     const int j = tid;
     if (j < c.n_proj) {
       const float2 M = sm.mres[(j >> 2) * 4 + (j & 3)];
@@ -526,14 +567,17 @@ __global__ void __launch_bounds__(FS_NP, 2) k_stage_fused(LaunchSet L, const flo
   sep_load_cols<N>(sm.colt, c, pho);
   __syncthreads();
   float2* Pab = Pa + U.pa_off + 4LL * b * c.n_proj;
+  // the second-order sums of every atom in one pass when the z groups halve
+  // the z weights (12 of them), else in two passes of 4 atoms
+  constexpr int NPASS = NZU == SEP_NA ? 2 : 1, NAP = SEP_NA / NPASS;
 #pragma unroll 1
-  for (int half = 0; half < 2; ++half) {
-    fs_project_pass<2, 3 * SEP_NA / 2>(sm, half * (3 * SEP_NA / 2), ah, al);
+  for (int half = 0; half < NPASS; ++half) {
+    fs_project_pass<2, 3 * NZU / NPASS, NAP, NZU>(sm, c, half * (3 * NZU / NPASS), half * NAP, ah, al);
     // rows (a, c_x, c_y, c_z) of projector type t: monomials w_t and w_t + e_alpha
     const int o = tid;
-    if (o < 4 * 4 * (SEP_NA / 2)) {
+    if (o < 4 * 4 * NAP) {
       const int al_ = o >> 4, t = (o >> 2) & 3, s = o & 3;
-      const int a = half * (SEP_NA / 2) + al_;
+      const int a = half * NAP + al_;
       const int j = 4 * a + t;
       if (j < c.n_proj) {
         int e[3] = {t == 1 ? 1 : 0, t == 2 ? 1 : 0, t == 3 ? 1 : 0};
@@ -554,6 +598,7 @@ __global__ void __launch_bounds__(FS_NP, 2) k_stage_fused(LaunchSet L, const flo
 // one CTA per (unit, band): the same tensor-core pass as the fused stage, so
 // the projections of a restored state equal those the stage leaves, bit for bit.
 // ----------------------------------------------------------------------------
+template <int NZU>
 __global__ void __launch_bounds__(FS_NP, 2) k_bra_fused(LaunchSet L, const float2* __restrict__ src,
                                                         float2* __restrict__ P) {
   extern __shared__ __align__(128) unsigned char fs_raw[];
@@ -566,6 +611,7 @@ __global__ void __launch_bounds__(FS_NP, 2) k_bra_fused(LaunchSet L, const float
   const int tid = threadIdx.x;
   const float2* ph = (const float2*)L.ph_half + (long long)u * L.ph_stride;
   const float2* sb = src + U.psi_off + (long long)b * FS_NPTS + tid;
+  fz_load<NZU>(sm, c);
 #pragma unroll
   for (int z = 0; z < FS_N; ++z) sm.ubuf[z * FS_PU + tid] = sb[z * FS_NP];
   fs_load_z(sm.zt, c, ph);
@@ -574,7 +620,7 @@ __global__ void __launch_bounds__(FS_NP, 2) k_bra_fused(LaunchSet L, const float
   uint32_t ah[2][4][4], al[2][4][4];
   fs_load_u(sm, ah, al);
   __syncthreads();
-  fs_project_pass<1, 2 * SEP_NA>(sm, 0, ah, al);
+  fs_project_pass<1, 2 * NZU, SEP_NA, NZU>(sm, c, 0, 0, ah, al);
   const int j = tid;
   if (j < c.n_proj) {
     const float2 M = sm.mres[(j >> 2) * 4 + (j & 3)];
@@ -645,23 +691,29 @@ __global__ void __launch_bounds__(FS_NP, 2) k_observe_fused(LaunchSet L, const f
     }
     const float2* tb = sm.buf[slot];
     const float2* cz = tb + col;
-    float2 qv[N + 2 * ND];
+    // the current's local part in correlation form: on the periodic grid
+    // sum_r Re(u* (-i grad_ax) u) = 2 sum_m w_m Im sum_r u*(r) u(r + m e_ax),
+    // which needs the forward neighbours only
+    float2 qv[N + ND];
 #pragma unroll
-    for (int k = 0; k < 2 * ND; ++k) qv[k] = cz[((k - ND + N) & (N - 1)) * NP];
-    float nbs = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
+    for (int k = 0; k < ND; ++k) qv[k] = cz[k * NP];
+    float nbs = 0.f;
+    float cx[ND], cy[ND], czs[ND];
+#pragma unroll
+    for (int mm = 0; mm < ND; ++mm) cx[mm] = cy[mm] = czs[mm] = 0.f;
 #pragma unroll
     for (int z = 0; z < N; ++z) {
-      qv[z + 2 * ND] = cz[((z + ND) & (N - 1)) * NP];
-      const float2 ce = qv[z + ND];
-      float2 gx = zero, gy = zero, gz = zero;
+      qv[z + ND] = cz[((z + ND) & (N - 1)) * NP];
+      const float2 ce = qv[z];
 #pragma unroll
       for (int mm = 1; mm <= ND; ++mm) {
-        const float2 xu = tb[z * NP + iy * N + ((ix + mm) & (N - 1))], xd = tb[z * NP + iy * N + ((ix - mm) & (N - 1))];
-        const float2 yu = tb[z * NP + ((iy + mm) & (N - 1)) * N + ix], yd = tb[z * NP + ((iy - mm) & (N - 1)) * N + ix];
-        const float2 zu = qv[z + ND + mm], zd = qv[z + ND - mm];
-        gx = f2fma(c.gradw2[0][mm], f2fma(neg1, xd, xu), gx);
-        gy = f2fma(c.gradw2[1][mm], f2fma(neg1, yd, yu), gy);
-        gz = f2fma(c.gradw2[2][mm], f2fma(neg1, zd, zu), gz);
+        const float2 xu = tb[z * NP + iy * N + ((ix + mm) & (N - 1))];
+        const float2 yu = tb[z * NP + ((iy + mm) & (N - 1)) * N + ix];
+        const float2 zu = qv[z + mm];
+        // Im(conj(u) v) = u_r v_i - u_i v_r
+        cx[mm - 1] = __fmaf_rn(ce.x, xu.y, __fmaf_rn(-ce.y, xu.x, cx[mm - 1]));
+        cy[mm - 1] = __fmaf_rn(ce.x, yu.y, __fmaf_rn(-ce.y, yu.x, cy[mm - 1]));
+        czs[mm - 1] = __fmaf_rn(ce.x, zu.y, __fmaf_rn(-ce.y, zu.x, czs[mm - 1]));
       }
       const float n2v = ce.x * ce.x + ce.y * ce.y;
       {
@@ -671,10 +723,13 @@ __global__ void __launch_bounds__(FS_NP, 2) k_observe_fused(LaunchSet L, const f
         rho[z] = t;
       }
       nbs += n2v;
-      // Re(conj(u) (-i g)) = u_r g_i - u_i g_r
-      bx += ce.x * gx.y - ce.y * gx.x;
-      by += ce.x * gy.y - ce.y * gy.x;
-      bz += ce.x * gz.y - ce.y * gz.x;
+    }
+    float bx = 0.f, by = 0.f, bz = 0.f;
+#pragma unroll
+    for (int mm = 1; mm <= ND; ++mm) {
+      bx = __fmaf_rn(2.f * c.gradwf[0][mm], cx[mm - 1], bx);
+      by = __fmaf_rn(2.f * c.gradwf[1][mm], cy[mm - 1], by);
+      bz = __fmaf_rn(2.f * c.gradwf[2][mm], czs[mm - 1], bz);
     }
     jx += bx;
     jy += by;

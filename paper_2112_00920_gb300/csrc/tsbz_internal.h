@@ -45,6 +45,15 @@ struct CellDev {
   const float* d1f;
   const float* pnormf;
   const float* wkbf;
+  // atoms whose z factor tables are identical (same z position, hence the same
+  // Gaussian, displacement and phase rows for every q) form one z group; the
+  // z contractions of the 16^3 fused stage run once per group (cells of at
+  // most 8 atoms; n_zg = 0 otherwise)
+  int n_zg;
+  int zg_of[8];       // group of atom a
+  int zg_rep[8];      // first atom of group g
+  int zg_off[9];      // members of group g: zg_mem[zg_off[g] .. zg_off[g + 1])
+  int zg_mem[8];
 };
 
 struct UnitDev {
@@ -87,6 +96,7 @@ struct SubDev {
 #define TSBZ_FIELD_STEP 0    // q_half = k + A(t_n + dt/2), q_obs = k + A(t_{n+1})
 #define TSBZ_FIELD_J0PLUS 1  // q_obs = k + A(0+)
 #define TSBZ_FIELD_J0MINUS 2 // q_obs = k
+#define TSBZ_FIELD_STEP_KEEP 3  // as STEP, phase tables kept: the field is constant and they are current
 
 struct LaunchSet {
   // Everything one kernel family needs for the units of one cell.

@@ -80,11 +80,12 @@ __global__ void k_field(LaunchSet L, int mode) {
   // step budget: a sub-simulation that has done max_steps steps sits out the
   // step (every later kernel of the step reads the flag); the evaluations of
   // J(0-), J(0+) and of a restored state take part whatever the step count
-  const bool act = mode != TSBZ_FIELD_STEP || *S.step < S.max_steps;
+  const bool step_mode = mode == TSBZ_FIELD_STEP || mode == TSBZ_FIELD_STEP_KEEP;
+  const bool act = !step_mode || *S.step < S.max_steps;
   if (U.kloc == 0 && threadIdx.x == 0) *S.active = act ? 1 : 0;
   if (!act) return;
   double ah[3] = {0.0, 0.0, 0.0}, ao[3] = {0.0, 0.0, 0.0};
-  if (mode == TSBZ_FIELD_STEP) {
+  if (step_mode) {
     const int step = *S.step;
     const int jh = 2 * step + 1, jo = 2 * step + 2;
     if (jo < S.n_field) {
@@ -108,6 +109,8 @@ __global__ void k_field(LaunchSet L, int mode) {
   }
   if (threadIdx.x == 3)
     reinterpret_cast<T*>(L.qt_half)[4 * u + 3] = (T)(0.5 * (qh[0] * qh[0] + qh[1] * qh[1] + qh[2] * qh[2]));
+  // constant field: q and every phase table equal those of the previous step
+  if (mode == TSBZ_FIELD_STEP_KEEP) return;
   V* phh = (V*)L.ph_half + (long long)u * L.ph_stride;
   V* pho = (V*)L.ph_obs + (long long)u * L.ph_stride;
   const int tab = c.n_atoms * 3 * c.nmax;

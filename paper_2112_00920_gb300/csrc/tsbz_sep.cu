@@ -3,6 +3,23 @@
 #include "tsbz_sep.cuh"
 #include "tsbz_fused.cuh"
 
+// The 16^3 fused kernels run their z contractions per z group when the cell's
+// atoms occupy at most 4 distinct z tables with at most two atoms each (NZU = 4),
+// else per atom (NZU = 8).
+#ifndef FS_ZGROUP
+#define FS_ZGROUP 1
+#endif
+static inline bool fs_grouped(const CellDev& c) {
+  if (!FS_ZGROUP || c.n_zg <= 0 || c.n_zg > 4) return false;
+  for (int g = 0; g < c.n_zg; ++g)
+    if (c.zg_off[g + 1] - c.zg_off[g] > 2) return false;   // the grouped ket adds at most two atoms
+  return true;
+}
+
+template <typename K> static void fs_attr(K* kernel, size_t bytes) {
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 bool sep_supported(const CellDev& c) {
   const int n12 = c.n1 * c.n2;
   return c.nd == ZM_ND && n12 <= 256 && (c.n3 == 8 || c.n3 == 16) && c.n_atoms <= SEP_NA;
@@ -18,10 +35,15 @@ void launch_bra_sep(const LaunchSet& L, const void* src, void* out, int with_d, 
     // the projections the 16^3 fused stage leaves are formed by the same pass
     static bool attr = false;
     if (!attr) {
-      cudaFuncSetAttribute(k_bra_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(FsSmem));
+      fs_attr(k_bra_fused<4>, sizeof(FsSmem));
+      fs_attr(k_bra_fused<SEP_NA>, sizeof(FsSmem));
       attr = true;
     }
-    k_bra_fused<<<grid, FS_NP, sizeof(FsSmem), (cudaStream_t)stream>>>(L, (const float2*)src, (float2*)out);
+    if (fs_grouped(c))
+      k_bra_fused<4><<<grid, FS_NP, sizeof(FsSmem), (cudaStream_t)stream>>>(L, (const float2*)src, (float2*)out);
+    else
+      k_bra_fused<SEP_NA><<<grid, FS_NP, sizeof(FsSmem), (cudaStream_t)stream>>>(L, (const float2*)src,
+                                                                                 (float2*)out);
     return;
   }
   const unsigned thr = sep_threads(L.cell);
@@ -68,12 +90,18 @@ bool launch_stage_sep(const LaunchSet& L, const void* tin, void* tout, void* psi
   if (next && c.n1 == 16 && c.n2 == 16 && c.n3 == 16) {
     static bool attr = false;
     if (!attr) {
-      cudaFuncSetAttribute(k_stage_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(FsSmem));
+      fs_attr(k_stage_fused<4>, sizeof(FsSmem));
+      fs_attr(k_stage_fused<SEP_NA>, sizeof(FsSmem));
       attr = true;
     }
     const unsigned grid = (unsigned)L.n_units * (unsigned)c.n_bands;
-    k_stage_fused<<<grid, FS_NP, sizeof(FsSmem), st>>>(L, (const float2*)tin, (float2*)tout, (float2*)psi,
-                                                        (float2*)P, (float2*)Pa, m, same_next);
+    if (fs_grouped(c))
+      k_stage_fused<4><<<grid, FS_NP, sizeof(FsSmem), st>>>(L, (const float2*)tin, (float2*)tout, (float2*)psi,
+                                                             (float2*)P, (float2*)Pa, m, same_next);
+    else
+      k_stage_fused<SEP_NA><<<grid, FS_NP, sizeof(FsSmem), st>>>(L, (const float2*)tin, (float2*)tout,
+                                                                  (float2*)psi, (float2*)P, (float2*)Pa, m,
+                                                                  same_next);
     return true;
   }
   if (next && c.n1 == 8 && c.n2 == 8 && c.n3 == 8) {

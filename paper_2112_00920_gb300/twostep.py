@@ -81,13 +81,11 @@ def adaptive_two_step(cell, mp, shifts, dt, n_steps, k0, omegas, tol, ground_sta
         P = Propagator(precision, device=device)
         try:
             cid = P.add_cell_spec(cell, hxc=hxc)
-            sids = []
-            for j, s in enumerate(chunk):
-                k = shifted_kpoints(cell.a, mp, s)
-                sid = P.add_subsim(cid, k, dt, n_steps)
+            ks = [shifted_kpoints(cell.a, mp, s) for s in chunk]
+            sids = [P.add_subsim(cid, k, dt, n_steps) for k in ks]
+            for j, (sid, k) in enumerate(zip(sids, ks)):
                 P.load_ground_state(sid, ground_state(k, used + j))
                 P.set_kick(sid, k0, direction)
-                sids.append(sid)
             P.propagate(n_steps)
             for sid in sids:
                 J, j0 = P.current(sid)

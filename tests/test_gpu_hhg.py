@@ -1,0 +1,87 @@
+"""GPU: the nonlinear (HHG) runs, where A(t) changes every step (Eq. 15).
+
+* The launch configuration of the two-step HHG workload at full size:
+  8 shifted 8^3 subgrids of cell A (4096 k, 65 536 orbitals), A(t) along
+  [001] sampled in the middle of the sin^4 pulse so that q changes from step
+  to step.  With v_Hxc frozen the k-points are independent, so the orbitals
+  of sampled k-points are checked element by element against the oracle run
+  on those k-points alone.
+* The HHG spectrum of Eqs. 16-17 from a short full pulse on the 8^3 cell,
+  GPU current against the oracle's.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import analysis, dynamics, hxc, kpoints
+from oracle.cell import Grid
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built_library():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2112_00920_gb300 import build_library
+    build_library()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+def test_hhg_workload_full_size_sampled(precision, tol):
+    from paper_2112_00920_gb300 import Propagator, shifted_kpoints
+    run = W.config3(n_steps=2)
+    cell = run.subsims[0].cell
+    dt, n = run.subsims[0].dt, 2
+    pulse = run.subsims[0].field
+    t0 = 0.5 * pulse.t_pulse
+    a = np.stack([dynamics.vector_potential(pulse, t0 + 0.5 * j * dt) for j in range(2 * n + 1)])
+    assert np.max(np.abs(np.diff(a[:, 2]))) > 0   # the field changes within every step
+    g = Grid(cell)
+    n_k = 512
+    psi = W.plane_wave_orbitals(cell.a, cell.n, W.plane_wave_set(cell.n_bands), n_k)
+    rho0 = 2.0 * np.sum(np.abs(psi[0]) ** 2, axis=0)
+    v_fr = hxc.v_hxc(g, rho0)
+    P = Propagator(precision)
+    cid = P.add_cell_spec(cell, hxc="frozen")
+    ks = [shifted_kpoints(cell.a, s.mp, s.shift) for s in run.subsims]
+    sids = [P.add_subsim(cid, k, dt, n) for k in ks]
+    for sid in sids:
+        P.load_ground_state(sid, psi, v_hxc_frozen=v_fr)
+        P.set_field(sid, a)
+    P.propagate(n)
+    rng = np.random.default_rng(2112)
+    for m in (0, 5):
+        state, step = P.get_state(sids[m])
+        assert step == n
+        kk = np.sort(rng.choice(n_k, size=3, replace=False))
+        k_orc = kpoints.kpoints_cartesian(cell.a, run.subsims[m].mp, run.subsims[m].shift)[kk]
+        np.testing.assert_allclose(k_orc, ks[m][kk], rtol=0, atol=1e-15)
+        o = dynamics.propagate(cell, k_orc, psi[kk], dt, n, a, hxc="frozen", v_hxc_frozen=v_fr)
+        err = np.max(np.abs(state[kk] - o["u"])) / np.max(np.abs(o["u"]))
+        print(precision, "subgrid", m, "k", kk.tolist(), "max rel orbital error", err)
+        assert err <= tol
+        nr = P.norms(sids[m])[kk]
+        assert np.max(np.abs(nr - o["norms"])) <= (1e-12 if precision == "fp64" else 1e-5)
+    P.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("fp32", 1e-4)])
+def test_hhg_spectrum_vs_oracle(precision, tol):
+    """A short sin^4 pulse (E0 = 0.05, w0 = 0.5, T_L = 20 au, polarisation z) on
+    cell A's 8^3 grid with 2 k-points, dt = 0.04, 500 steps (one pulse);
+    I(w) = w^2 |FT[W J_z]|^2 up to the 15th harmonic."""
+    from gpu_common import gpu_run, oracle_run
+    cell = W.cell_a_coarse(n=8)
+    pulse = W.Pulse(e0=0.05, omega0=0.5, t_pulse=20.0, direction=(0.0, 0.0, 1.0))
+    gr = Grid(cell)
+    s = dict(mp=(2, 1, 1), shift=(0.25, 0.5, 0.125), dt=0.04, n_steps=500, field=pulse,
+             psi=W.random_orbitals(2, cell.n_bands, cell.n, gr.dv, seed=77))
+    _, out = gpu_run(cell, [s], precision=precision)
+    o = oracle_run(cell, s)
+    om = np.linspace(0.05, 15 * pulse.omega0, 600)
+    i_gpu = analysis.hhg_spectrum(out[0]["J"][:, 2], s["dt"], pulse.t_pulse, om)
+    i_orc = analysis.hhg_spectrum(o["J"][:, 2], s["dt"], pulse.t_pulse, om)
+    err = np.max(np.abs(i_gpu - i_orc)) / np.max(i_orc)
+    print(precision, "HHG spectrum rel err", err, "err_J", analysis.err_j(out[0]["J"], o["J"]))
+    assert err <= tol

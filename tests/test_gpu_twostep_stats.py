@@ -39,8 +39,8 @@ def test_current_stats_match_oracle():
     n = 12
     P = Propagator("fp64")
     cid = P.add_cell_spec(CELL)
-    for i, s in enumerate(shifts):
-        sid = P.add_subsim(cid, shifted_kpoints(CELL.a, (1, 1, 1), s), DT, n)
+    sids = [P.add_subsim(cid, shifted_kpoints(CELL.a, (1, 1, 1), s), DT, n) for s in shifts]
+    for i, sid in enumerate(sids):
         P.load_ground_state(sid, _psi(i))
         P.set_kick(sid, K0, (1.0, 0.0, 0.0))
     P.propagate(n)
