@@ -488,10 +488,19 @@ template <typename T> int run_step(tsbz_ctx* ctx) {
         ev_stop(ctx);
         if (hc.dev.use_proj) ++ctx->launches;
       }
+      const int same_next = cell_field_const(ctx, hc) ? 1 : 0;
+      ev_start(ctx, FAM_STAGE);
+      const bool whole = launch_step_fused(L, ctx->psi, ctx->P, ctx->Pa, same_next, ctx->stream);
+      ev_stop(ctx);
+      if (whole) {
+        hc.pa_by_stage = true;
+        ++ctx->launches;
+        continue;
+      }
       for (int m = 1; m <= 4; ++m) {
         ev_start(ctx, FAM_STAGE);
         const bool fused4 = launch_stage_sep(L, srcs[m - 1], dsts[m - 1], ctx->psi, ctx->P, ctx->Pa, m,
-                                             cell_field_const(ctx, hc) ? 1 : 0, ctx->stream);
+                                             same_next, ctx->stream);
         if (m == 4) hc.pa_by_stage = fused4;
         ev_stop(ctx);
         ++ctx->launches;
@@ -659,10 +668,7 @@ int sync_and_check(tsbz_ctx* ctx) {
 int n_variants(const tsbz_ctx* ctx, const HostCell& hc) {
   const CellDev& c = hc.dev;
   if (ctx->precision == TSBZ_FP32_TC) return 1;
-  if (ctx->precision == TSBZ_FP32 && sep_supported(c)) {
-    const bool cube16 = c.n1 == 16 && c.n2 == 16 && c.n3 == 16, cube8 = c.n1 == 8 && c.n2 == 8 && c.n3 == 8;
-    return (cube16 || cube8) ? 2 : 1;
-  }
+  if (ctx->precision == TSBZ_FP32 && sep_supported(c)) return sep_variants(c);
   const size_t big = (size_t)16 * (c.n_proj > 0 ? c.n_proj : 1) * ctx->elem_size();
   return big <= 160 * 1024 ? 3 : 2;
 }

@@ -62,8 +62,10 @@ __device__ __forceinline__ void fs_mma3(float (&d)[4], const uint32_t (&ah)[4], 
 }
 
 struct FsSmem {
-  float2 tbuf[FS_NPTS];              // band of t_{m-1}; after the march: B_z
-  float2 ubuf[FS_N * FS_PU];         // V_NL per plane (ket), then u; then the z sums S
+  // two plane buffers of pitch FS_PU: the band of t_{m-1}, and V_NL per plane
+  // (ket) overwritten by t_m; the projection passes use them as scratch
+  float2 xb[FS_N * FS_PU];
+  float2 yb[FS_N * FS_PU];
   uint2 bk[32 * FS_BKP];             // ket B matrix (hi, lo)
   float4 zt[SEP_NA * FS_N];          // (Re F_z, Im F_z, d_z, 0) per atom and plane
   float4 colt[SEP_NA * 2 * FS_N];    // x and y factors (Re F, Im F, d, 0)
@@ -148,7 +150,7 @@ template <int NZU> __device__ __forceinline__ float4 fz_table(const FsSmem& sm, 
 // A[col][q] = sum over the group's atoms of F_y (G00 + d_y G10) or F_y G01.
 // ----------------------------------------------------------------------------
 template <int NZU>
-__device__ __forceinline__ void fs_ket(FsSmem& sm, const CellDev& c) {
+__device__ __forceinline__ void fs_ket(FsSmem& sm, const CellDev& c, float2* vout, bool build_b) {
   constexpr int Q = 2 * NZU;   // complex columns of the GEMM
   constexpr int KS = Q / 4;    // k steps of 8 over the 2 Q real rows (Re rows, then Im rows)
   constexpr int NI = Q / 4;    // q values per thread: t4 + 4 i
@@ -165,7 +167,7 @@ __device__ __forceinline__ void fs_ket(FsSmem& sm, const CellDev& c) {
     sm.gt[(a * 3 + 1) * FS_N + ix] = sep_cmul(F, make_float2(wy.x, -wy.y));
     sm.gt[(a * 3 + 2) * FS_N + ix] = sep_cmul(F, make_float2(wz.x, -wz.y));
   }
-  for (int i = tid; i < 2 * Q * 2 * FS_N; i += blockDim.x) {
+  for (int i = tid; build_b && i < 2 * Q * 2 * FS_N; i += blockDim.x) {
     const int k = i / (2 * FS_N), n = i - k * 2 * FS_N;
     const bool rrow = k < Q;
     const int q = rrow ? k : k - Q, z = n >> 1, cc = n & 1;
@@ -241,8 +243,8 @@ __device__ __forceinline__ void fs_ket(FsSmem& sm, const CellDev& c) {
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt) {
       const int cA = 32 * warp + 16 * mt + g;
-      sm.ubuf[z * FS_PU + cA] = make_float2(d[mt][0], d[mt][1]);
-      sm.ubuf[z * FS_PU + cA + 8] = make_float2(d[mt][2], d[mt][3]);
+      vout[z * FS_PU + cA] = make_float2(d[mt][0], d[mt][1]);
+      vout[z * FS_PU + cA + 8] = make_float2(d[mt][2], d[mt][3]);
     }
   }
 }
@@ -257,13 +259,13 @@ __device__ __forceinline__ void fs_ket(FsSmem& sm, const CellDev& c) {
 // ----------------------------------------------------------------------------
 template <int D, int NQ, int NAP, int NZU>
 __device__ __forceinline__ void fs_project_pass(FsSmem& sm, const CellDev& c, int q0, int a0,
-                                                const uint32_t (&ah)[2][4][4], const uint32_t (&al)[2][4][4]) {
+                                                const uint32_t (&ah)[2][4][4], const uint32_t (&al)[2][4][4],
+                                                uint2* bz, float2* sbuf) {
+  // bz: B_z (32 x (2 NQ + 4) uint2); sbuf: the z sums [q'][iy][ix ^ iy] (NQ x 256 float2)
   constexpr int NPR = 2 * NQ;          // real n of the pass
   constexpr int BZP = NPR + 4;         // B_z row pitch (uint2)
   constexpr int NM = D == 1 ? 4 : 10;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, g = lane >> 2, t4 = lane & 3;
-  uint2* bz = reinterpret_cast<uint2*>(sm.tbuf);
-  float2* sbuf = sm.ubuf;                                      // [q'][iy][ix ^ iy]
   // B_z[k][n], k = 2 z + c (component of u), n = 2 q' + c' (component of S)
   for (int i = tid; i < 32 * NPR; i += blockDim.x) {
     const int k = i / NPR, n = i - k * NPR;
@@ -384,9 +386,9 @@ __device__ __forceinline__ void fs_project_pass(FsSmem& sm, const CellDev& c, in
 }
 
 // A fragments (split) of u = ubuf[z][col] for the warp's columns, k = 2 z + c
-__device__ __forceinline__ void fs_load_u(const FsSmem& sm, uint32_t (&ah)[2][4][4], uint32_t (&al)[2][4][4]) {
+__device__ __forceinline__ void fs_load_u(const float2* src, uint32_t (&ah)[2][4][4], uint32_t (&al)[2][4][4]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t4 = lane & 3;
-  const float* ub = reinterpret_cast<const float*>(sm.ubuf);
+  const float* ub = reinterpret_cast<const float*>(src);
 #pragma unroll
   for (int mt = 0; mt < 2; ++mt) {
     const int cA = 32 * warp + 16 * mt + g;
@@ -403,106 +405,72 @@ __device__ __forceinline__ void fs_load_u(const FsSmem& sm, uint32_t (&ah)[2][4]
 }
 
 // ----------------------------------------------------------------------------
-// Taylor stage m on a 16^3 grid, one CTA per (unit, band), one thread per
-// (x, y) column; same arithmetic contract as k_stage_bulk: t_m, the psi
-// accumulation, the projections of t_m (m < 4) or, at m = 4, those of
-// psi(t_{n+1}) for the next step (P) and for the current (Pa).
+// Pieces shared by the per-stage and the whole-step kernels.
 // ----------------------------------------------------------------------------
-template <int NZU>
-__global__ void __launch_bounds__(FS_NP, 2) k_stage_fused(LaunchSet L, const float2* __restrict__ tin,
-                                                          float2* __restrict__ tout, float2* __restrict__ psi,
-                                                          float2* __restrict__ P, float2* __restrict__ Pa, int m,
-                                                          int same_next) {
+// One band (16 planes of 256 complex values) into a buffer of plane pitch FS_PU.
+__device__ __forceinline__ void fs_copy_band(float2* dst, const float2* src, uint32_t bar) {
+#pragma unroll 1
+  for (int z = 0; z < FS_N; ++z)
+    bk_copy_g2s(bk_smem(dst + z * FS_PU), src + z * FS_NP, FS_NP * (uint32_t)sizeof(float2), bar);
+}
+
+// Factor tables of the unit (q of the step) and W = E P of the band.
+__device__ __forceinline__ void fs_unit_tables(FsSmem& sm, const CellDev& c, const float2* ph, const float2* Pu) {
+  fs_load_z(sm.zt, c, ph);
+  sep_load_cols<FS_N>(sm.colt, c, ph);
+  for (int j = threadIdx.x; j < SEP_NP; j += blockDim.x) {
+    float2 w = make_float2(0.f, 0.f);
+    if (j < c.n_proj) {
+      const float2 p = Pu[j];
+      const float e = c.wkbf[j];
+      w = make_float2(e * p.x, e * p.y);
+    }
+    sm.wt[j] = w;
+  }
+}
+
+// z-march of Taylor stage m over the band held in `tin`: t_m = (-i dt/m) h t_{m-1}
+// with h t = -1/2 lap t - i q.grad t + (|q|^2/2 + v_eff) t + V_NL t.  `vio`
+// holds conj(V_NL t_{m-1}) per plane on entry and receives, column by column,
+// t_m (m < 4) or psi(t_{n+1}) (m = 4).
+//   STEP = false (one launch per stage): psi in global memory, `acc` holds the
+//     psi column (m >= 2), t_m goes to tout (m < 4);
+//   STEP = true (the whole step in one launch): psi accumulates in `acc`
+//     (acc = t_0 + t_1 at m = 1) and is written once, at m = 4.
+template <bool STEP>
+__device__ __forceinline__ void fs_march(const FsSmem& sm, const CellDev& c, const float2* tin, float2* vio, int m,
+                                         float hdt, float q0, float q1, float q2, float dg0, float2 (&acc)[FS_N],
+                                         float2* __restrict__ tout, float2* __restrict__ psi, long long base) {
   constexpr int ND = ZM_ND, N = FS_N, NP = FS_NP;
-  extern __shared__ __align__(128) unsigned char fs_raw[];
-  FsSmem& sm = *reinterpret_cast<FsSmem*>(fs_raw);
-  const CellDev& c = L.cell;
-  const int b = blockIdx.x % c.n_bands;
-  const int u = L.unit_ids[blockIdx.x / c.n_bands];
-  if (!unit_active(L, u)) return;
-  const UnitDev U = L.units[u];
-  const SubDev S = L.subs[U.sub];
-  const int tid = threadIdx.x, col = tid;
-  const int ix = col & (N - 1), iy = col / N;
-  const bool proj = c.use_proj != 0;
-  const float2* ph = (const float2*)L.ph_half + (long long)u * L.ph_stride;
-  float2* Pu = P + U.p_off + (long long)b * c.n_proj;
-  const long long base = U.psi_off + (long long)b * FS_NPTS;
+  const int col = threadIdx.x, ix = col & (N - 1), iy = col / N;
   const float2 zero = make_float2(0.f, 0.f);
-  const uint32_t bar = bk_smem(&sm.mbar);
-  if (tid == 0) bk_mbar_init(bar, 1);
-  fz_load<NZU>(sm, c);
-  __syncthreads();
-  if (tid == 0) {
-    // the band of t_{m-1} and the sub-simulation's v_eff, on one barrier
-    bk_mbar_expect_tx(bar, FS_NPTS * (uint32_t)(sizeof(float2) + sizeof(float)));
-    bk_copy_g2s(bk_smem(sm.tbuf), tin + base, FS_NPTS * sizeof(float2), bar);
-    bk_copy_g2s(bk_smem(sm.vbuf), S.veff, FS_NPTS * sizeof(float), bar);
-  }
-  // psi of the column in registers (m >= 2), in flight while the ket runs
-  float2 pq[N];
-#pragma unroll
-  for (int z = 0; z < N; ++z) pq[z] = m >= 2 ? psi[base + z * NP + col] : zero;
-  if (proj) {
-    fs_load_z(sm.zt, c, ph);
-    sep_load_cols<N>(sm.colt, c, ph);
-    for (int j = tid; j < SEP_NP; j += blockDim.x) {
-      float2 w = zero;
-      if (j < c.n_proj) {
-        const float2 p = Pu[j];
-        const float e = c.wkbf[j];
-        w = make_float2(e * p.x, e * p.y);
-      }
-      sm.wt[j] = w;
-    }
-  }
-  __syncthreads();
-  if (proj) {
-    fs_ket<NZU>(sm, c);
-  } else {
-#pragma unroll
-    for (int z = 0; z < N; ++z) sm.ubuf[z * FS_PU + col] = zero;
-  }
-  const float* qt = reinterpret_cast<const float*>(L.qt_half) + 4 * u;
-  const float q0 = qt[0], q1 = qt[1], q2 = qt[2];
-  const float dg0 = c.hlapf[0][0] + c.hlapf[1][0] + c.hlapf[2][0] + qt[3];
-  const float hdt = (float)S.dt / (float)m;
-  const bool ok = bk_mbar_wait(bar, 0, BK_WAIT_POLLS);
-  if (!__syncthreads_and(ok)) {
-    if (tid == 0) {
-      atomicOr(S.status, BK_STATUS_TIMEOUT);
-      bk_mbar_wait(bar, 0, BK_WAIT_POLLS);
-    }
-    return;
-  }
-  const float2* tb = sm.tbuf;
-  const float2* cz = tb + col;
+  const float2* cz = tin + col;
   const float2* xp[ND];
   const float2* xm[ND];
   const float2* yp[ND];
   const float2* ym[ND];
 #pragma unroll
   for (int mm = 1; mm <= ND; ++mm) {
-    xp[mm - 1] = tb + iy * N + ((ix + mm) & (N - 1));
-    xm[mm - 1] = tb + iy * N + ((ix - mm) & (N - 1));
-    yp[mm - 1] = tb + ((iy + mm) & (N - 1)) * N + ix;
-    ym[mm - 1] = tb + ((iy - mm) & (N - 1)) * N + ix;
+    xp[mm - 1] = tin + iy * N + ((ix + mm) & (N - 1));
+    xm[mm - 1] = tin + iy * N + ((ix - mm) & (N - 1));
+    yp[mm - 1] = tin + ((iy + mm) & (N - 1)) * N + ix;
+    ym[mm - 1] = tin + ((iy - mm) & (N - 1)) * N + ix;
   }
   const float2 neg1 = make_float2(-1.f, -1.f);
   float2 qv[N + 2 * ND];
 #pragma unroll
-  for (int k = 0; k < 2 * ND; ++k) qv[k] = cz[((k - ND + N) & (N - 1)) * NP];
+  for (int k = 0; k < 2 * ND; ++k) qv[k] = cz[((k - ND + N) & (N - 1)) * FS_PU];
 #pragma unroll
   for (int z = 0; z < N; ++z) {
-    qv[z + 2 * ND] = cz[((z + ND) & (N - 1)) * NP];
+    qv[z + 2 * ND] = cz[((z + ND) & (N - 1)) * FS_PU];
     const float2 ce = qv[z + ND];
     const float dg = dg0 + sm.vbuf[z * NP + col];
     float2 h = __fmul2_rn(make_float2(dg, dg), ce);
     float2 gx = zero, gy = zero, gz = zero;
 #pragma unroll
     for (int mm = 1; mm <= ND; ++mm) {
-      const float2 xu = xp[mm - 1][z * NP], xd = xm[mm - 1][z * NP];
-      const float2 yu = yp[mm - 1][z * NP], yd = ym[mm - 1][z * NP];
+      const float2 xu = xp[mm - 1][z * FS_PU], xd = xm[mm - 1][z * FS_PU];
+      const float2 yu = yp[mm - 1][z * FS_PU], yd = ym[mm - 1][z * FS_PU];
       const float2 zu = qv[z + ND + mm], zd = qv[z + ND - mm];
       h = f2fma(c.hlap2[0][mm], __fadd2_rn(xu, xd), h);
       h = f2fma(c.hlap2[1][mm], __fadd2_rn(yu, yd), h);
@@ -514,57 +482,66 @@ __global__ void __launch_bounds__(FS_NP, 2) k_stage_fused(LaunchSet L, const flo
     float2 qg = __fmul2_rn(make_float2(q0, q0), gx);
     qg = f2fma(make_float2(q1, q1), gy, qg);
     qg = f2fma(make_float2(q2, q2), gz, qg);
-    const float2 vq = sm.ubuf[z * FS_PU + col];   // conj(V_NL t)
+    const float2 vq = vio[z * FS_PU + col];   // conj(V_NL t)
     const float hr = h.x + qg.y + vq.x;
     const float hi = h.y - qg.x - vq.y;
     const float2 t = make_float2(hdt * hi, -hdt * hr);
     const long long idx = base + (long long)z * NP + col;
     float2 uo = t;
-    if (m < 4) tout[idx] = t;
-    if (m == 2) {
-      psi[idx] = __fadd2_rn(pq[z], __fadd2_rn(ce, t));
-    } else if (m == 3) {
-      psi[idx] = __fadd2_rn(pq[z], t);
-    } else if (m == 4) {
-      uo = __fadd2_rn(pq[z], t);   // psi(t_{n+1})
-      psi[idx] = uo;
+    if constexpr (STEP) {
+      if (m == 1) {
+        acc[z] = __fadd2_rn(ce, t);
+      } else if (m < 4) {
+        acc[z] = __fadd2_rn(acc[z], t);
+      } else {
+        uo = __fadd2_rn(acc[z], t);   // psi(t_{n+1})
+        psi[idx] = uo;
+      }
+    } else {
+      if (m < 4) tout[idx] = t;
+      if (m == 2) {
+        psi[idx] = __fadd2_rn(acc[z], __fadd2_rn(ce, t));
+      } else if (m == 3) {
+        psi[idx] = __fadd2_rn(acc[z], t);
+      } else if (m == 4) {
+        uo = __fadd2_rn(acc[z], t);   // psi(t_{n+1})
+        psi[idx] = uo;
+      }
     }
-    sm.ubuf[z * FS_PU + col] = uo;
+    vio[z * FS_PU + col] = uo;
   }
-  if (!proj) return;
-  __syncthreads();
-  uint32_t ah[2][4][4], al[2][4][4];
-  fs_load_u(sm, ah, al);
-  __syncthreads();   // ubuf free for the z sums
-  if (m < 4) {
-    fs_project_pass<1, 2 * NZU, SEP_NA, NZU>(sm, c, 0, 0, ah, al);
-    const int j = tid;
-    if (j < c.n_proj) {
-      const float2 M = sm.mres[(j >> 2) * 4 + (j & 3)];
-      const double sc = c.dv * (double)c.pnormf[j];
-      Pu[j] = make_float2((float)(sc * M.x), (float)(sc * M.y));
-    }
-    return;
-  }
-  // m = 4: projections of psi(t_{n+1}) for the next step, then for the current.
-  // With a constant field both use the same q, and the first-order sums of the
-  // current's pass are those of the next step's (same z sums, rows and order).
+}
+
+// P_j = dV pn_j M_j of a degree-1 pass (float, as stored in P).
+__device__ __forceinline__ float2 fs_proj_value(const FsSmem& sm, const CellDev& c, int j) {
+  const float2 M = sm.mres[(j >> 2) * 4 + (j & 3)];
+  const double sc = c.dv * (double)c.pnormf[j];
+  return make_float2((float)(sc * M.x), (float)(sc * M.y));
+}
+
+// Stage 4 after the march: projections of psi(t_{n+1}) (split fragments ah/al)
+// for the next step (P, q of the next step) and for the current (Pa, q at
+// t_{n+1}).  With a constant field both use the same q, and the first-order
+// sums of the current's pass are those of the next step's (same z sums, rows
+// and order).  bz / sbuf: scratch (B_z, z sums), both buffers free.
+template <int NZU>
+__device__ __forceinline__ void fs_stage4_projections(FsSmem& sm, const LaunchSet& L, const CellDev& c, int u,
+                                                      const UnitDev& U, int b, float2* __restrict__ Pu,
+                                                      float2* __restrict__ Pa, int same_next,
+                                                      const uint32_t (&ah)[2][4][4], const uint32_t (&al)[2][4][4],
+                                                      uint2* bz, float2* sbuf) {
+  const int tid = threadIdx.x;
   const float2* phn = (const float2*)L.ph_next + (long long)u * L.ph_stride;
   const float2* pho = (const float2*)L.ph_obs + (long long)u * L.ph_stride;
   if (!same_next) {
     fs_load_z(sm.zt, c, phn);
-    sep_load_cols<N>(sm.colt, c, phn);
+    sep_load_cols<FS_N>(sm.colt, c, phn);
     __syncthreads();
-    fs_project_pass<1, 2 * NZU, SEP_NA, NZU>(sm, c, 0, 0, ah, al);
-    const int j = tid;
-    if (j < c.n_proj) {
-      const float2 M = sm.mres[(j >> 2) * 4 + (j & 3)];
-      const double sc = c.dv * (double)c.pnormf[j];
-      Pu[j] = make_float2((float)(sc * M.x), (float)(sc * M.y));
-    }
+    fs_project_pass<1, 2 * NZU, SEP_NA, NZU>(sm, c, 0, 0, ah, al, bz, sbuf);
+    if (tid < c.n_proj) Pu[tid] = fs_proj_value(sm, c, tid);
   }
   fs_load_z(sm.zt, c, pho);
-  sep_load_cols<N>(sm.colt, c, pho);
+  sep_load_cols<FS_N>(sm.colt, c, pho);
   __syncthreads();
   float2* Pab = Pa + U.pa_off + 4LL * b * c.n_proj;
   // the second-order sums of every atom in one pass when the z groups halve
@@ -572,7 +549,7 @@ __global__ void __launch_bounds__(FS_NP, 2) k_stage_fused(LaunchSet L, const flo
   constexpr int NPASS = NZU == SEP_NA ? 2 : 1, NAP = SEP_NA / NPASS;
 #pragma unroll 1
   for (int half = 0; half < NPASS; ++half) {
-    fs_project_pass<2, 3 * NZU / NPASS, NAP, NZU>(sm, c, half * (3 * NZU / NPASS), half * NAP, ah, al);
+    fs_project_pass<2, 3 * NZU / NPASS, NAP, NZU>(sm, c, half * (3 * NZU / NPASS), half * NAP, ah, al, bz, sbuf);
     // rows (a, c_x, c_y, c_z) of projector type t: monomials w_t and w_t + e_alpha
     const int o = tid;
     if (o < 4 * 4 * NAP) {
@@ -590,6 +567,182 @@ __global__ void __launch_bounds__(FS_NP, 2) k_stage_fused(LaunchSet L, const flo
       }
     }
     __syncthreads();
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Taylor stage m on a 16^3 grid, one CTA per (unit, band), one thread per
+// (x, y) column; same arithmetic contract as k_stage_bulk: t_m, the psi
+// accumulation, the projections of t_m (m < 4) or, at m = 4, those of
+// psi(t_{n+1}) for the next step (P) and for the current (Pa).
+// ----------------------------------------------------------------------------
+template <int NZU>
+__global__ void __launch_bounds__(FS_NP, 2) k_stage_fused(LaunchSet L, const float2* __restrict__ tin,
+                                                          float2* __restrict__ tout, float2* __restrict__ psi,
+                                                          float2* __restrict__ P, float2* __restrict__ Pa, int m,
+                                                          int same_next) {
+  constexpr int N = FS_N, NP = FS_NP;
+  extern __shared__ __align__(128) unsigned char fs_raw[];
+  FsSmem& sm = *reinterpret_cast<FsSmem*>(fs_raw);
+  const CellDev& c = L.cell;
+  const int b = blockIdx.x % c.n_bands;
+  const int u = L.unit_ids[blockIdx.x / c.n_bands];
+  if (!unit_active(L, u)) return;
+  const UnitDev U = L.units[u];
+  const SubDev S = L.subs[U.sub];
+  const int tid = threadIdx.x, col = tid;
+  const bool proj = c.use_proj != 0;
+  const float2* ph = (const float2*)L.ph_half + (long long)u * L.ph_stride;
+  float2* Pu = P + U.p_off + (long long)b * c.n_proj;
+  const long long base = U.psi_off + (long long)b * FS_NPTS;
+  const float2 zero = make_float2(0.f, 0.f);
+  const uint32_t bar = bk_smem(&sm.mbar);
+  if (tid == 0) bk_mbar_init(bar, 1);
+  fz_load<NZU>(sm, c);
+  __syncthreads();
+  if (tid == 0) {
+    // the band of t_{m-1} and the sub-simulation's v_eff, on one barrier
+    bk_mbar_expect_tx(bar, FS_NPTS * (uint32_t)(sizeof(float2) + sizeof(float)));
+    fs_copy_band(sm.xb, tin + base, bar);
+    bk_copy_g2s(bk_smem(sm.vbuf), S.veff, FS_NPTS * sizeof(float), bar);
+  }
+  // psi of the column in registers (m >= 2), in flight while the ket runs
+  float2 pq[N];
+#pragma unroll
+  for (int z = 0; z < N; ++z) pq[z] = m >= 2 ? psi[base + z * NP + col] : zero;
+  if (proj) fs_unit_tables(sm, c, ph, Pu);
+  __syncthreads();
+  if (proj) {
+    fs_ket<NZU>(sm, c, sm.yb, true);
+  } else {
+#pragma unroll
+    for (int z = 0; z < N; ++z) sm.yb[z * FS_PU + col] = zero;
+  }
+  const float* qt = reinterpret_cast<const float*>(L.qt_half) + 4 * u;
+  const float dg0 = c.hlapf[0][0] + c.hlapf[1][0] + c.hlapf[2][0] + qt[3];
+  const bool ok = bk_mbar_wait(bar, 0, BK_WAIT_POLLS);
+  if (!__syncthreads_and(ok)) {
+    if (tid == 0) {
+      atomicOr(S.status, BK_STATUS_TIMEOUT);
+      bk_mbar_wait(bar, 0, BK_WAIT_POLLS);
+    }
+    return;
+  }
+  fs_march<false>(sm, c, sm.xb, sm.yb, m, (float)S.dt / (float)m, qt[0], qt[1], qt[2], dg0, pq, tout, psi, base);
+  if (!proj) return;
+  __syncthreads();
+  uint32_t ah[2][4][4], al[2][4][4];
+  fs_load_u(sm.yb, ah, al);
+  __syncthreads();   // both buffers free for the projection scratch
+  uint2* bz = reinterpret_cast<uint2*>(sm.xb);
+  if (m < 4) {
+    fs_project_pass<1, 2 * NZU, SEP_NA, NZU>(sm, c, 0, 0, ah, al, bz, sm.yb);
+    if (tid < c.n_proj) Pu[tid] = fs_proj_value(sm, c, tid);
+    return;
+  }
+  fs_stage4_projections<NZU>(sm, L, c, u, U, b, Pu, Pa, same_next, ah, al, bz, sm.yb);
+}
+
+// ----------------------------------------------------------------------------
+// The whole time step in one launch (cells whose atoms form z groups of at
+// most two: NZU = 4), one CTA per (unit, band): the band of psi is brought in
+// once, the four Taylor terms live in the two plane buffers (t_{m-1} in one,
+// V_NL and then t_m in the other, roles swapping each stage), psi accumulates
+// in registers, and each stage's projections go straight to the next stage's
+// ket.  Memory traffic per step: psi read and written once, P and Pa.  Same
+// arithmetic per stage as k_stage_fused; psi is summed as
+// (((t_0 + t_1) + t_2) + t_3) + t_4.
+// ----------------------------------------------------------------------------
+template <int NZU>
+__global__ void __launch_bounds__(FS_NP, 2) k_step_fused(LaunchSet L, float2* __restrict__ psi,
+                                                         float2* __restrict__ P, float2* __restrict__ Pa,
+                                                         int same_next) {
+  static_assert(NZU == 4, "the projection scratch of a stage fits one plane buffer only with z groups");
+  constexpr int N = FS_N;
+  extern __shared__ __align__(128) unsigned char fs_raw[];
+  FsSmem& sm = *reinterpret_cast<FsSmem*>(fs_raw);
+  const CellDev& c = L.cell;
+  const int b = blockIdx.x % c.n_bands;
+  const int u = L.unit_ids[blockIdx.x / c.n_bands];
+  if (!unit_active(L, u)) return;
+  const UnitDev U = L.units[u];
+  const SubDev S = L.subs[U.sub];
+  const int tid = threadIdx.x, col = tid;
+  const bool proj = c.use_proj != 0;
+  const float2* ph = (const float2*)L.ph_half + (long long)u * L.ph_stride;
+  float2* Pu = P + U.p_off + (long long)b * c.n_proj;
+  const long long base = U.psi_off + (long long)b * FS_NPTS;
+  const uint32_t bar = bk_smem(&sm.mbar);
+  if (tid == 0) bk_mbar_init(bar, 1);
+  fz_load<NZU>(sm, c);
+  __syncthreads();
+  if (tid == 0) {
+    bk_mbar_expect_tx(bar, FS_NPTS * (uint32_t)(sizeof(float2) + sizeof(float)));
+    fs_copy_band(sm.xb, psi + base, bar);
+    bk_copy_g2s(bk_smem(sm.vbuf), S.veff, FS_NPTS * sizeof(float), bar);
+  }
+  if (proj) fs_unit_tables(sm, c, ph, Pu);
+  __syncthreads();
+  const float* qt = reinterpret_cast<const float*>(L.qt_half) + 4 * u;
+  const float q0 = qt[0], q1 = qt[1], q2 = qt[2];
+  const float dg0 = c.hlapf[0][0] + c.hlapf[1][0] + c.hlapf[2][0] + qt[3];
+  float2 acc[N];
+  uint32_t ah[2][4][4], al[2][4][4];
+  float2* tin = sm.xb;
+  float2* vio = sm.yb;
+  bool waited = false;
+#pragma unroll 1
+  for (int m = 1; m <= 4; ++m) {
+    if (proj) {
+      fs_ket<NZU>(sm, c, vio, m == 1);   // the z-table B matrix once per step
+    } else {
+#pragma unroll
+      for (int z = 0; z < N; ++z) vio[z * FS_PU + col] = make_float2(0.f, 0.f);
+    }
+    if (!waited) {
+      const bool ok = bk_mbar_wait(bar, 0, BK_WAIT_POLLS);
+      if (!__syncthreads_and(ok)) {
+        if (tid == 0) {
+          atomicOr(S.status, BK_STATUS_TIMEOUT);
+          bk_mbar_wait(bar, 0, BK_WAIT_POLLS);
+        }
+        return;
+      }
+      waited = true;
+    } else {
+      __syncthreads();
+    }
+    fs_march<true>(sm, c, tin, vio, m, (float)S.dt / (float)m, q0, q1, q2, dg0, acc, nullptr, psi, base);
+    __syncthreads();
+    if (!proj) {
+      float2* t = tin;
+      tin = vio;
+      vio = t;
+      continue;
+    }
+    fs_load_u(vio, ah, al);
+    if (m < 4) {
+      // projections of t_m for the next stage; scratch in the buffer of t_{m-1}
+      fs_project_pass<1, 2 * NZU, SEP_NA, NZU>(sm, c, 0, 0, ah, al,
+                                               reinterpret_cast<uint2*>(tin + 2 * NZU * FS_NP), tin);
+      if (tid < SEP_NP) {
+        float2 w = make_float2(0.f, 0.f);
+        if (tid < c.n_proj) {
+          const float2 p = fs_proj_value(sm, c, tid);
+          const float e = c.wkbf[tid];
+          w = make_float2(e * p.x, e * p.y);
+        }
+        sm.wt[tid] = w;
+      }
+      __syncthreads();
+      float2* t = tin;
+      tin = vio;
+      vio = t;
+    } else {
+      __syncthreads();   // both buffers free for the projection scratch
+      fs_stage4_projections<NZU>(sm, L, c, u, U, b, Pu, Pa, same_next, ah, al, reinterpret_cast<uint2*>(tin),
+                                 vio);
+    }
   }
 }
 
@@ -613,20 +766,15 @@ __global__ void __launch_bounds__(FS_NP, 2) k_bra_fused(LaunchSet L, const float
   const float2* sb = src + U.psi_off + (long long)b * FS_NPTS + tid;
   fz_load<NZU>(sm, c);
 #pragma unroll
-  for (int z = 0; z < FS_N; ++z) sm.ubuf[z * FS_PU + tid] = sb[z * FS_NP];
+  for (int z = 0; z < FS_N; ++z) sm.yb[z * FS_PU + tid] = sb[z * FS_NP];
   fs_load_z(sm.zt, c, ph);
   sep_load_cols<FS_N>(sm.colt, c, ph);
   __syncthreads();
   uint32_t ah[2][4][4], al[2][4][4];
-  fs_load_u(sm, ah, al);
+  fs_load_u(sm.yb, ah, al);
   __syncthreads();
-  fs_project_pass<1, 2 * NZU, SEP_NA, NZU>(sm, c, 0, 0, ah, al);
-  const int j = tid;
-  if (j < c.n_proj) {
-    const float2 M = sm.mres[(j >> 2) * 4 + (j & 3)];
-    const double sc = c.dv * (double)c.pnormf[j];
-    P[U.p_off + (long long)b * c.n_proj + j] = make_float2((float)(sc * M.x), (float)(sc * M.y));
-  }
+  fs_project_pass<1, 2 * NZU, SEP_NA, NZU>(sm, c, 0, 0, ah, al, reinterpret_cast<uint2*>(sm.xb), sm.yb);
+  if (tid < c.n_proj) P[U.p_off + (long long)b * c.n_proj + tid] = fs_proj_value(sm, c, tid);
 }
 
 // ----------------------------------------------------------------------------

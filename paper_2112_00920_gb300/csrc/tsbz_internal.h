@@ -151,6 +151,10 @@ bool launch_observe_zf(const LaunchSet& L, const void* psi, double* rho_part, do
 void launch_stage_v(const LaunchSet& L, const void* tin, void* tout, void* psi, const void* V, int m, void* stream);
 // single-precision fused stage and projections (cells with at most 8 atoms, depth 8 or 16, n1 n2 <= 256)
 bool sep_supported(const CellDev& c);
+int sep_variants(const CellDev& c);   // kernel variants of the single-precision path on this cell
+// The whole time step of every unit in one launch (16^3 cells with z groups,
+// variant 0); false when the cell takes the per-stage kernels.
+bool launch_step_fused(const LaunchSet& L, void* psi, void* P, void* Pa, int same_next, void* stream);
 void launch_bra_sep(const LaunchSet& L, const void* src, void* out, int with_d, int use_obs, void* stream);
 // stage 4 on the bulk-staged path also writes P (next step) and Pa; returns whether it did
 // same_next: the field is constant, so at m = 4 the next step's projections come from the current's sums

@@ -20,6 +20,28 @@ template <typename K> static void fs_attr(K* kernel, size_t bytes) {
   cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+static inline bool fs_cube16(const CellDev& c) { return c.n1 == 16 && c.n2 == 16 && c.n3 == 16; }
+
+// Kernel variants of the single-precision path (LaunchSet::variant):
+//   16^3 cells with z groups: 0 whole step in one launch, 1 fused stage per
+//     launch, 2 z-march stage with CUDA-core projections;
+//   other 16^3 cells and 8^3 cells: 0 fused / bulk-staged stage, 1 z-march stage;
+//   other shapes: the z-march stage only.
+// Returns 0 (whole step), 1 (fused or bulk-staged stage) or 2 (z-march stage).
+static int stage_kind(const LaunchSet& L) {
+  const CellDev& c = L.cell;
+  if (L.ph_next == nullptr) return 2;
+  if (fs_cube16(c) && fs_grouped(c)) return L.variant;
+  if (fs_cube16(c) || (c.n1 == 8 && c.n2 == 8 && c.n3 == 8)) return L.variant == 0 ? 1 : 2;
+  return 2;
+}
+
+int sep_variants(const CellDev& c) {
+  if (fs_cube16(c) && fs_grouped(c)) return 3;
+  if (fs_cube16(c) || (c.n1 == 8 && c.n2 == 8 && c.n3 == 8)) return 2;
+  return 1;
+}
+
 bool sep_supported(const CellDev& c) {
   const int n12 = c.n1 * c.n2;
   return c.nd == ZM_ND && n12 <= 256 && (c.n3 == 8 || c.n3 == 16) && c.n_atoms <= SEP_NA;
@@ -31,7 +53,7 @@ void launch_bra_sep(const LaunchSet& L, const void* src, void* out, int with_d, 
   if (L.n_units == 0 || !L.cell.use_proj) return;
   const unsigned grid = (unsigned)L.n_units * (unsigned)L.cell.n_bands;
   const CellDev& c = L.cell;
-  if (L.variant == 0 && !with_d && !use_obs && L.ph_next != nullptr && c.n1 == 16 && c.n2 == 16 && c.n3 == 16) {
+  if (stage_kind(L) <= 1 && !with_d && !use_obs && fs_cube16(c)) {
     // the projections the 16^3 fused stage leaves are formed by the same pass
     static bool attr = false;
     if (!attr) {
@@ -84,10 +106,8 @@ bool launch_stage_sep(const LaunchSet& L, const void* tin, void* tout, void* psi
   if (L.n_units == 0) return false;
   const CellDev& c = L.cell;
   cudaStream_t st = (cudaStream_t)stream;
-  // variant 0: the fused tensor-core stage (16^3) or the bulk-staged stage (8^3);
-  // variant 1: the z-march stage with CUDA-core projections on every shape
-  const bool next = L.ph_next != nullptr && L.variant == 0;
-  if (next && c.n1 == 16 && c.n2 == 16 && c.n3 == 16) {
+  const bool next = stage_kind(L) <= 1;
+  if (next && fs_cube16(c)) {
     static bool attr = false;
     if (!attr) {
       fs_attr(k_stage_fused<4>, sizeof(FsSmem));
@@ -116,6 +136,19 @@ bool launch_stage_sep(const LaunchSet& L, const void* tin, void* tout, void* psi
   else
     k_stage_sep<8><<<grid, thr, pad, st>>>(L, (const float2*)tin, (float2*)tout, (float2*)psi, (float2*)P, m);
   return false;
+}
+
+bool launch_step_fused(const LaunchSet& L, void* psi, void* P, void* Pa, int same_next, void* stream) {
+  if (L.n_units == 0 || stage_kind(L) != 0) return false;
+  static bool attr = false;
+  if (!attr) {
+    fs_attr(k_step_fused<4>, sizeof(FsSmem));
+    attr = true;
+  }
+  const unsigned grid = (unsigned)L.n_units * (unsigned)L.cell.n_bands;
+  k_step_fused<4><<<grid, FS_NP, sizeof(FsSmem), (cudaStream_t)stream>>>(L, (float2*)psi, (float2*)P, (float2*)Pa,
+                                                                          same_next);
+  return true;
 }
 
 bool launch_observe_fused(const LaunchSet& L, const void* psi, double* rho_part, double* jk_part, double* nrm_part,

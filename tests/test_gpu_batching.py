@@ -135,7 +135,7 @@ def test_autotune_restores_state_and_keeps_parity(precision):
     P.propagate(1)
     before = [(P.get_state(sid), P.density(sid), P.norms(sid), P.current(sid)) for _, sid, _, _ in ids]
     n = P.autotune(budget_ms=60000)
-    assert n >= 4   # cell A: 2 variants (fp32) or 3; cell B: 3
+    assert n >= 6   # cell A: 3 variants; cell B: 3
     for (_, sid, _, _), (st, rho, nr, cur) in zip(ids, before):
         st2 = P.get_state(sid)
         assert st2[1] == st[1] == 1
@@ -157,7 +157,7 @@ def test_autotune_restores_state_and_keeps_parity(precision):
 
 VARIANT_CASES = [
     # (precision, cell factory, mp, number of variants)
-    ("fp32", W.cell_a, (2, 1, 1), 2),                 # fused tensor-core stage / CUDA-core z-march
+    ("fp32", W.cell_a, (2, 1, 1), 3),                 # whole step / fused tensor-core stage / CUDA-core z-march
     ("fp32", _tiny, (2, 2, 1), 2),                    # bulk-staged 8^3 stage / z-march
     ("fp32", lambda: W.cell_tiny(atoms="offgrid", n=(10, 12, 14), a=(7.0, 8.0, 9.0), n_bands=3), (3, 1, 1), 3),
     ("fp64", _tiny, (2, 2, 1), 3),                    # point-parallel: 8, 4, 16 bands per chunk
