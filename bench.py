@@ -224,35 +224,63 @@ def build_propagator(precision, n_steps_cap, device=0, n_subsims=64):
     return P, sids, run
 
 
-# DRAM traffic of the stage kernel from an ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum), per launch averaged over m = 1..4, measured on the
-# reduced workload (8 of the 64 subgrids, 8192 orbitals) and scaled by the
-# orbital count to the full workload.  Valid only for the kernel source it
-# was taken on: the SHA-1 of the kernel text is checked at run time.
-STAGE_TRAFFIC = {
-    "fp32": {"kernel": "k_stage_fused", "file": "tsbz_fused.cuh", "sha1": "3dc3b1ef25df6d969dbe0e3933a4f10d0a8a1754",
-             "bytes_per_launch_full": 6.644e9, "profile": "profiles/k_stage_fused_fp32_reduced8.md"},
-    "fp32_tc": {"kernel": "k_stage_zf", "file": "tsbz_tc.cuh", "sha1": None, "bytes_per_launch_full": None,
-                "profile": None},
-}
 STAGE_KERNEL = {
-    "fp32": "k_stage_fused (z-march stencil + tensor-core projector contractions + Taylor accumulate)",
+    "fp32": "k_stage_fused (z-march stencil + tensor-core projector contractions + Taylor accumulate), one launch "
+            "per Taylor stage",
     "fp32_tc": "k_stage_zf (z-march stencil + non-local term + Taylor accumulate)",
     "fp64": "k_stage (stencil + ket + Taylor accumulate)",
 }
+STEP_KERNEL = ("k_step_fused (the four Taylor stages of a time step in one launch: z-march stencil, tensor-core "
+               "projector contractions, Taylor accumulation in registers)")
+# FP32 arithmetic of the local part of h, the Taylor scaling and the psi sum,
+# per grid point, orbital and Taylor stage (complex values): Laplacian and
+# gradient pairs 3 axes x 4 x (2 + 4 + 2 + 4) = 144, q.grad 10, diagonal 3,
+# combination 4, (-i dt/m) 2, accumulation 2.
+FLOPS_LOCAL_PER_POINT_STAGE = 165
+FP32_LANES_PER_SM, N_SM = 128, 152
+# DRAM bytes of one k_step_fused launch from an ncu capture (dram__bytes_read.sum
+# + dram__bytes_write.sum) on the reduced workload (8 of the 64 subgrids, 8192
+# orbitals), scaled by the orbital count to the full workload.  Valid only for
+# the source it was taken on: the SHA-1 of the kernel header is checked at run time.
+STEP_TRAFFIC = {"file": "tsbz_fused.cuh", "sha1": "18f3e4c9ef2be6f2ca9f0c742a8f894c507225f7",
+                "bytes_per_launch_full": 8 * 496.676864e6, "profile": "profiles/k_step_fused_fp32_twostep8.md"}
 
 
-def _kernel_sha1(path: str, name: str) -> str | None:
+def _file_sha1(path: str) -> str | None:
     import hashlib
     try:
-        src = open(path).read()
+        return hashlib.sha1(open(path, "rb").read()).hexdigest()
     except OSError:
         return None
-    i = src.find(f" {name}(")
-    if i < 0:
-        return None
-    j = src.find("\n}\n", i)
-    return hashlib.sha1(src[i:j].encode()).hexdigest()
+
+
+def step_roofline(step_ms, n_orb, cell, elem, peaks, subsims, clocks):
+    """Roofline of k_step_fused.  It reads and writes psi once per step, so its
+    HBM traffic is 2 arrays (plus P and Pa) and it is bound by its arithmetic
+    issue, not by HBM: the ALU roofline (FP32 lanes x 2 flop x max SM clock)
+    is the primary one, the HBM figures are given beside it."""
+    npts = cell.n_pts
+    n_proj = 4 * cell.n_atoms
+    flops = 4.0 * FLOPS_LOCAL_PER_POINT_STAGE * npts * n_orb
+    byts = float(n_orb) * (2 * elem * npts + 6 * n_proj * elem)
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = N_SM * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    achieved = flops / (step_ms / 1e3) / 1e12
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    gbs = byts / (step_ms / 1e3) / 1e9
+    traffic = None
+    path = os.path.join(ROOT, "paper_2112_00920_gb300", "csrc", STEP_TRAFFIC["file"])
+    if subsims == 64 and STEP_TRAFFIC["sha1"] and _file_sha1(path) == STEP_TRAFFIC["sha1"]:
+        traffic = STEP_TRAFFIC["bytes_per_launch_full"]
+    return {"kernel": STEP_KERNEL, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": traffic, "algorithmic_flops_per_launch": flops,
+            "algorithmic_bytes_per_launch": byts,
+            "peak_source": f"{N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {mhz:.0f} MHz "
+                           "(max SM clock, MEASURED_PEAKS.json)",
+            "launches_per_step": 1,
+            "hbm": {"achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)"},
+            "sm_mhz_median": clocks.get("sm_mhz")}
 
 
 def eps_check(precision, device):
@@ -382,22 +410,20 @@ def main():
         pass
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     elem = 16 if args.precision == "fp64" else 8
-    n_stage = 4 * args.steps
-    stage_ms = fam["stage"] / n_stage
-    bytes_launch = stage_bytes_per_launch(elem, n_orb, cell.n_pts)
-    achieved = bytes_launch / (stage_ms / 1e3) / 1e9
-    kname = STAGE_KERNEL[args.precision]
-    traffic = None
-    st = STAGE_TRAFFIC.get(args.precision)
-    if st and args.subsims == 64 and st["sha1"]:
-        sha = _kernel_sha1(os.path.join(ROOT, "paper_2112_00920_gb300", "csrc", st["file"]), st["kernel"])
-        if sha == st["sha1"]:
-            traffic = st["bytes_per_launch_full"]
-    roof = {"kernel": kname, "bound": "hbm", "achieved": achieved,
-            "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
-            "algorithmic_bytes_per_launch": bytes_launch,
-            "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)" if peaks else "fallback 6.8 TB/s",
-            "family_ms_per_step": {k: v / args.steps for k, v in fam.items()}}
+    variant, n_var, _ = P.variant(0)
+    whole = args.precision == "fp32" and variant == 0 and n_var == 3
+    fam_ms = {k: v / args.steps for k, v in fam.items()}
+    if whole:
+        roof = step_roofline(fam["stage"] / args.steps, n_orb, cell, elem, peaks, args.subsims, clk.summary())
+    else:
+        stage_ms = fam["stage"] / (4 * args.steps)
+        bytes_launch = stage_bytes_per_launch(elem, n_orb, cell.n_pts)
+        achieved = bytes_launch / (stage_ms / 1e3) / 1e9
+        roof = {"kernel": STAGE_KERNEL[args.precision], "bound": "hbm", "achieved": achieved,
+                "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                "algorithmic_bytes_per_launch": bytes_launch,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)" if peaks else "fallback 6.8 TB/s"}
+    roof["family_ms_per_step"] = fam_ms
 
     if args.profile_run:
         # profiler runs (launch lists, kernel captures): the warm-up and timed steps only
