@@ -329,6 +329,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_tc", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--etrs-steps", type=int, default=3,
+                    help="steps of the ETRS propagator timed on the same workload (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-run", action="store_true",
                     help="run only the warm-up and timed steps (for profiler launch lists and captures)")
@@ -365,7 +367,9 @@ def main():
     from paper_2112_00920_gb300 import build_library
     build_library()
 
-    cap = args.warmup + 2 * args.steps + 1
+    # room for the autotuner's trial steps (undone afterwards) within the step budget
+    tune_room = 5 * 3 + 1
+    cap = args.warmup + 2 * args.steps + 1 + tune_room
     P, sids, run = build_propagator(args.precision, cap, device=local_rank, n_subsims=args.subsims)
     cell = run.subsims[0].cell
     n_orb = run.n_orbitals
@@ -376,6 +380,13 @@ def main():
         P.load_ground_state(sid, psi_dev)
     P.set_kick(-1, 0.005, (1.0, 0.0, 0.0))
     P.propagate(args.warmup)
+    # the autotuner picks each cell's kernel variant on this workload (trial steps undone);
+    # profiler runs keep the default variant so that their launch lists hold only the timed steps
+    n_tried = 0
+    if not args.profile_run:
+        n_tried = P.autotune(budget_ms=5000)
+    tuned_variant, tuned_n, tuned_ms = P.variant(0)
+    P.propagate(1)   # first step after tuning (forms the projections if the variant changed)
     stream = torch.cuda.current_stream()
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     P.set_profiling(True)
@@ -471,6 +482,29 @@ def main():
     if args.precision != "fp64":
         eps_err = eps_check(args.precision, local_rank)
 
+    # the enforced-time-reversal-symmetry propagator on the same workload (three
+    # Taylor-4 expansions per step: predictor and two half steps)
+    etrs = None
+    if args.etrs_steps > 0 and args.precision != "fp32_tc":
+        P4, sids4, _ = build_propagator(args.precision, args.etrs_steps + 2, device=local_rank,
+                                        n_subsims=args.subsims)
+        P4.set_propagator("etrs")
+        for sid in sids4:
+            P4.load_ground_state(sid, psi_dev)
+        P4.set_kick(-1, 0.005, (1.0, 0.0, 0.0))
+        P4.propagate(1)
+        torch.cuda.synchronize()
+        s4, e4 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s4.record(stream)
+        P4.propagate(args.etrs_steps)
+        e4.record(stream)
+        torch.cuda.synchronize()
+        etrs_ms = s4.elapsed_time(e4)
+        P4.close()
+        etrs = {"value": n_orb * args.etrs_steps / (etrs_ms / 1e3), "unit": UNIT, "steps": args.etrs_steps,
+                "ms_per_step": etrs_ms / args.etrs_steps,
+                "propagator": "ETRS: Taylor-4 predictor for rho(t+dt), then two Taylor-4 half steps"}
+
     # plain FP64 GPU path on the same workload (comparison)
     fp64 = None
     if args.precision != "fp64" and args.fp64_steps > 0:
@@ -509,8 +543,13 @@ def main():
                           "parallelism": f"replica x{world} (independent shifts per GPU)"},
                "roofline": roof, "e2e": e2e, "gpu_launches": launches,
                "graph_replay_value": graph_value,
+               "autotune": {"variant": tuned_variant, "n_variants": tuned_n, "variants_timed": n_tried,
+                            "ms_per_step": tuned_ms,
+                            "variants": "0 whole step in one launch, 1 fused stage per launch, "
+                                        "2 z-march stage with CUDA-core projections" if tuned_n == 3 else None},
                "clocks": clk.summary(),
                "fp64_gpu": fp64,
+               "etrs": etrs,
                "eps_rel_err_vs_fp64": eps_err,
                "eps_check": "cell A (16^3 grid), MP 2^3, plane-wave start, kick 0.005 x, 600 steps, "
                             "eps over 0.1-20 eV vs the FP64 GPU path (FP64 GPU vs oracle: err_J <= 1e-10)",

@@ -57,6 +57,14 @@ extern "C" {
                                 cores in their own kernels (scaled split-FP16,
                                 three products, FP32 accumulate)              */
 
+/* Time step (tsbz_set_propagator). */
+#define TSBZ_PROP_TAYLOR4 0  /* 4th-order Taylor with q = k + A(t_n + dt/2) and
+                                v_Hxc[rho(t_n)] (the default)                 */
+#define TSBZ_PROP_ETRS 1     /* enforced time-reversal symmetry: a Taylor-4
+                                predictor gives rho~(t_{n+1}); then
+                                T4(dt/2; A(t_{n+1}), v_Hxc[rho~])
+                                T4(dt/2; A(t_n), v_Hxc[rho(t_n)])             */
+
 #define TSBZ_HXC_SCF 0       /* v_Hxc[rho(t)] updated every step (Eq. 2)      */
 #define TSBZ_HXC_FROZEN 1    /* v_Hxc kept at its loaded value                */
 
@@ -198,6 +206,13 @@ int tsbz_set_profiling(tsbz_ctx* ctx, int on);
  * step counters and field samples from device memory. */
 int tsbz_set_graphs(tsbz_ctx* ctx, int on);
 
+/* Choose the time step (TSBZ_PROP_TAYLOR4 or TSBZ_PROP_ETRS).  The paper
+ * leaves the propagator to its TDDFT code; ETRS costs three Taylor-4
+ * expansions per step (predictor and two half steps) and keeps psi(t_n) and
+ * v_eff(t_n) on the device during the step.  ETRS runs in TSBZ_FP64 and
+ * TSBZ_FP32 (TSBZ_EINVAL in TSBZ_FP32_TC).  A captured step graph is dropped. */
+int tsbz_set_propagator(tsbz_ctx* ctx, int propagator);
+
 /* Autotuner of the batched launch (the per-cell choice of kernel variants:
  * tile shapes and schedules; the method itself is the same in every variant).
  * For each cell with more than one variant it runs, per variant, one untimed
@@ -225,6 +240,15 @@ int tsbz_get_variant(tsbz_ctx* ctx, int cell_id, int* variant, int* n_variants, 
 
 /* Force a cell's variant (0 <= variant < n_variants; TSBZ_EINVAL otherwise). */
 int tsbz_set_variant(tsbz_ctx* ctx, int cell_id, int variant);
+
+/* Self-test of failure detection without a GPU fault: one CTA on `device`
+ * waits on a bulk-copy barrier with the same bounded wait the kernels use,
+ * limited to `polls` polls (1 .. 2^24).  With deliver = 0 no copy is issued,
+ * the wait runs out, the kernel records the timeout and returns, and the call
+ * returns TSBZ_ETIMEOUT with the device still usable; with deliver = 1 the
+ * 16-byte copy completes the barrier and the call returns TSBZ_OK.
+ * *status_out (nullable) receives the kernel's status word. */
+int tsbz_selftest_bounded_wait(int device, int polls, int deliver, int* status_out);
 
 const char* tsbz_last_error(tsbz_ctx* ctx);
 void tsbz_destroy(tsbz_ctx* ctx);

@@ -14,8 +14,9 @@ Modules (each function cites the paper passage it follows):
   hxc       -- Hartree (FFT Poisson) and LDA (Perdew-Zunger 1981) potentials
   hamiltonian -- application of h_k(t) (Eq. 2) and its dense matrix
   scf       -- ground state (fixed occupations, Pulay mixing)
-  dynamics  -- fields (Eqs. 11, 15), Taylor-4 step, density (Eq. 3),
+  dynamics  -- fields (Eqs. 11, 15), Taylor-4 and ETRS steps, density (Eq. 3),
                current (Eqs. 5-6), two-step driver (Eq. 9, Sec. II.B steps 1-4)
+               and the standard error of the two-step mean (Sec. III.B)
   analysis  -- windowed Fourier transforms, eps(omega) (Eqs. 12-14),
                HHG spectrum (Eqs. 16-17), error metrics, free-electron closed form
 

@@ -143,13 +143,17 @@ def fd_velocity(grid: Grid, gint, nd: int = 4):
                      for ax in range(3)])
 
 
-def free_electron_current(grid: Grid, occ, kcart, gints, dt, n_steps, a_samples, xc: bool = True, nd: int = 4):
+def free_electron_current(grid: Grid, occ, kcart, gints, dt, n_steps, a_samples, xc: bool = True, nd: int = 4,
+                          propagator: str = "taylor4"):
     """Closed-form J(t_n) for plane-wave orbitals in a cell with no ions.
 
     Each orbital stays a plane wave, u_n = c_n u_0 with
     c_{n+1} = c_n T_4(-i e_n dt), e_n = kinetic(G, k + A(t_n + dt/2)) + v_xc(rho_n);
     rho_n = f sum |c_n|^2 / (Omega N_k) is uniform so v_H = 0.
     J_n = -(f/(Omega N_k)) sum |c_n|^2 (s(G)/h + k + A(t_n)).
+    With propagator "etrs": c_{n+1} = c_n T_4(-i e'' dt/2) T_4(-i e' dt/2),
+    e' = kinetic(G, k + A(t_n)) + v_xc(rho_n), e'' = kinetic(G, k + A(t_{n+1}))
+    + v_xc(rho~), rho~ the uniform density of the Taylor-4 predictor c_n T_4(-i e_n dt).
     Returns (J (n_steps+1, 3), J0_minus (3,), |c|^2 (n_k, n_b))."""
     n_k, n_b, _ = gints.shape
     c = np.ones((n_k, n_b), dtype=np.complex128)
@@ -162,13 +166,23 @@ def free_electron_current(grid: Grid, occ, kcart, gints, dt, n_steps, a_samples,
 
     j0m = cur(c, np.zeros(3))
     js = [cur(c, a_samples[0])]
+    def vxc_of(cc):
+        rho = occ * np.sum(np.abs(cc) ** 2) / (grid.omega * n_k)
+        return float(pz81(np.array([rho]))[1][0]) if xc else 0.0
+
     for n in range(n_steps):
-        rho = occ * np.sum(np.abs(c) ** 2) / (grid.omega * n_k)
-        vxc = float(pz81(np.array([rho]))[1][0]) if xc else 0.0
+        vxc = vxc_of(c)
         a_half = a_samples[2 * n + 1]
-        for k in range(n_k):
-            for b in range(n_b):
-                e = fd_kinetic(grid, gints[k, b], kcart[k] + a_half, nd) + vxc
-                c[k, b] *= taylor4_factor(-1j * e * dt)
+        step = np.array([[taylor4_factor(-1j * (fd_kinetic(grid, gints[k, b], kcart[k] + a_half, nd) + vxc) * dt)
+                          for b in range(n_b)] for k in range(n_k)])
+        if propagator == "etrs":
+            vxc_p = vxc_of(c * step)
+            for k in range(n_k):
+                for b in range(n_b):
+                    e1 = fd_kinetic(grid, gints[k, b], kcart[k] + a_samples[2 * n], nd) + vxc
+                    e2 = fd_kinetic(grid, gints[k, b], kcart[k] + a_samples[2 * n + 2], nd) + vxc_p
+                    c[k, b] *= taylor4_factor(-1j * e1 * 0.5 * dt) * taylor4_factor(-1j * e2 * 0.5 * dt)
+        else:
+            c = c * step
         js.append(cur(c, a_samples[2 * n + 2]))
     return np.array(js), j0m, np.abs(c) ** 2

@@ -21,6 +21,14 @@ Current (Eqs. 5-6) with pi_q = dh/dq = -i grad_FD + q + d V_NL / dq:
   J = -(1/Omega) (1/N_k) sum_{k,b} f_b <u|pi|u>.
 Two-step (Eq. 9 and Sec. II.B steps 1-4): each shifted sub-simulation m is
 propagated on its own; dJ_m = J_m - J_m(0-); J = (1/N_H) sum_m dJ_m.
+
+Propagator variant (the paper leaves the propagator to its TDDFT code):
+enforced time-reversal symmetry, step n:
+  1. predictor: the step above from u(t_n), giving rho~(t_{n+1}) and
+     v~_eff = v_loc + v_Hxc[rho~] (frozen mode: v_eff unchanged);
+  2. u(t_{n+1}) = T4(dt/2; q = k + A(t_{n+1}), v~_eff) T4(dt/2; q = k + A(t_n), v_eff(t_n)) u(t_n),
+     T4(tau) the 4th-order Taylor polynomial of exp(-i tau h);
+  3. rho, v_Hxc and J(t_{n+1}) as above.
 """
 from __future__ import annotations
 
@@ -149,8 +157,10 @@ def taylor4(ops: Operators, u, q, v_eff, dt):
 
 
 def propagate(cell: CellSpec, kcart, u0, dt, n_steps, a_samples, hxc: str = "scf",
-              v_hxc_frozen=None, ops: Operators | None = None, keep_state: bool = True):
-    """Propagate one (sub-)simulation.
+              v_hxc_frozen=None, ops: Operators | None = None, keep_state: bool = True,
+              propagator: str = "taylor4"):
+    """Propagate one (sub-)simulation with the Taylor-4 step ("taylor4") or the
+    enforced-time-reversal-symmetry step ("etrs") of the module header.
 
     Returns dict(J (n_steps+1, 3) at t_0 = 0+ .. t_n, J0_minus (3,), rho,
     norms (n_k, n_b), u, v_hxc)."""
@@ -166,11 +176,23 @@ def propagate(cell: CellSpec, kcart, u0, dt, n_steps, a_samples, hxc: str = "scf
     j0m = current(ops, u, kcart, np.zeros(3))
     js = [current(ops, u, kcart, a_samples[0])]
     for n in range(n_steps):
+        a_now = a_samples[2 * n]
         a_half = a_samples[2 * n + 1]
         a_next = a_samples[2 * n + 2]
         v_eff = ops.vloc + vh
-        for k in range(u.shape[0]):
-            u[k] = taylor4(ops, u[k], kcart[k] + a_half, v_eff, dt)
+        if propagator == "etrs":
+            # predictor density at t_{n+1}, then the two half steps
+            u_pred = np.stack([taylor4(ops, u[k], kcart[k] + a_half, v_eff, dt) for k in range(u.shape[0])])
+            vh_pred = vh if hxc == "frozen" else build_v_hxc(grid, density_from(cell, u_pred))
+            v_pred = ops.vloc + vh_pred
+            for k in range(u.shape[0]):
+                w = taylor4(ops, u[k], kcart[k] + a_now, v_eff, 0.5 * dt)
+                u[k] = taylor4(ops, w, kcart[k] + a_next, v_pred, 0.5 * dt)
+        elif propagator == "taylor4":
+            for k in range(u.shape[0]):
+                u[k] = taylor4(ops, u[k], kcart[k] + a_half, v_eff, dt)
+        else:
+            raise ValueError(f"unknown propagator {propagator!r}")
         rho = density_from(cell, u)
         if hxc != "frozen":
             vh = build_v_hxc(grid, rho)

@@ -87,9 +87,11 @@ _SIGS = {
     "tsbz_get_timings": ([ctypes.c_void_p, _D, ctypes.c_int], ctypes.c_int),
     "tsbz_set_profiling": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "tsbz_set_graphs": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
+    "tsbz_set_propagator": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "tsbz_autotune": ([ctypes.c_void_p, ctypes.c_int, _I], ctypes.c_int),
     "tsbz_get_variant": ([ctypes.c_void_p, ctypes.c_int, _I, _I, _D, ctypes.c_int], ctypes.c_int),
     "tsbz_set_variant": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "tsbz_selftest_bounded_wait": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, _I], ctypes.c_int),
     "tsbz_last_error": ([ctypes.c_void_p], ctypes.c_char_p),
     "tsbz_destroy": ([ctypes.c_void_p], None),
     "tsbz_shifted_kpoints": ([_D, _I, _D, _D, ctypes.c_size_t], ctypes.c_int),
@@ -154,6 +156,13 @@ def pulse_samples(e0, omega0, t_pulse, direction, dt, n_steps) -> np.ndarray:
     if rc:
         raise TsbzError(rc, "tsbz_pulse_samples")
     return out
+
+
+def selftest_bounded_wait(device: int = 0, polls: int = 1000, deliver: bool = False):
+    """Run the bounded-wait self-test; returns (return code, kernel status word)."""
+    st = ctypes.c_int()
+    rc = load().tsbz_selftest_bounded_wait(int(device), int(polls), 1 if deliver else 0, ctypes.byref(st))
+    return rc, st.value
 
 
 def density_noalloc(psi, occ, rho=None, stream=None):
@@ -369,6 +378,11 @@ class Propagator:
 
     def set_profiling(self, on: bool):
         self._check(self.lib.tsbz_set_profiling(self.ctx, 1 if on else 0), "tsbz_set_profiling")
+
+    def set_propagator(self, name: str):
+        """"taylor4" (default) or "etrs"."""
+        code = {"taylor4": 0, "etrs": 1}[name]
+        self._check(self.lib.tsbz_set_propagator(self.ctx, code), "tsbz_set_propagator")
 
     def autotune(self, budget_ms: int = 2000) -> int:
         """Time the kernel variants of every cell and keep the fastest (the

@@ -63,6 +63,7 @@ struct HostSub {
   double* vhxc = nullptr;
   double* norms = nullptr;
   void* veff = nullptr;
+  void* veff_save = nullptr;   // the other v_eff of an ETRS step
 };
 
 }  // namespace
@@ -103,6 +104,11 @@ struct tsbz_ctx {
   int* d_status = nullptr;
   int* d_mask = nullptr;
   int* d_active = nullptr;   // per sub-simulation: takes part in the current step
+  int propagator = TSBZ_PROP_TAYLOR4;
+  double dt_scale = 1.0;     // of the stage launches being issued (ETRS half steps: 1/2)
+  void* psi_save = nullptr;  // psi(t_n) during an ETRS step (allocated on first use)
+  double* d_jtile = nullptr; // per sub-simulation: [16][3] partial currents of the finalize
+  int* d_jcount = nullptr;   // per sub-simulation: finalize tiles done
   double2* work_a = nullptr;
   double2* work_b = nullptr;
   double2* staging = nullptr;
@@ -212,6 +218,7 @@ LaunchSet make_set(tsbz_ctx* ctx, HostCell& hc) {
   L.ph_stride = ctx->ph_stride;
   L.qt_half = ctx->qt_half;
   L.variant = hc.variant;
+  L.dt_scale = ctx->dt_scale;
   return L;
 }
 
@@ -286,6 +293,8 @@ int layout(tsbz_ctx* ctx) {
   if ((rc = dalloc_t(ctx, ctx->subs.size(), &ctx->d_status))) return rc;
   if ((rc = dalloc_t(ctx, ctx->subs.size(), &ctx->d_mask))) return rc;
   if ((rc = dalloc_t(ctx, ctx->subs.size(), &ctx->d_active))) return rc;
+  if ((rc = dalloc_t(ctx, 48 * ctx->subs.size(), &ctx->d_jtile))) return rc;
+  if ((rc = dalloc_t(ctx, ctx->subs.size(), &ctx->d_jcount))) return rc;
   if ((rc = dalloc_t(ctx, std::max<long long>(work_max, 1), &ctx->work_a))) return rc;
   if ((rc = dalloc_t(ctx, std::max<long long>(work_max, 1), &ctx->work_b))) return rc;
   if ((rc = dalloc_t(ctx, stage_max, &ctx->staging))) return rc;
@@ -303,6 +312,7 @@ int layout(tsbz_ctx* ctx) {
     if ((rc = dalloc_t(ctx, c.npts, &hs.vhxc))) return rc;
     if ((rc = dalloc_t(ctx, (long long)hs.n_k * c.n_bands, &hs.norms))) return rc;
     if ((rc = dalloc(ctx, (size_t)c.npts * (ctx->precision == TSBZ_FP64 ? 8 : 4), &hs.veff))) return rc;
+    if ((rc = dalloc(ctx, (size_t)c.npts * (ctx->precision == TSBZ_FP64 ? 8 : 4), &hs.veff_save))) return rc;
     if (hs.A.empty()) hs.A.assign(3LL * nf, 0.0);
     hs.field_dirty = true;
     SubDev& d = sd[s];
@@ -325,6 +335,9 @@ int layout(tsbz_ctx* ctx) {
     d.step = ctx->d_steps + s;
     d.status = ctx->d_status + s;
     d.active = ctx->d_active + s;
+    d.veff_save = hs.veff_save;
+    d.jtile = ctx->d_jtile + 48 * s;
+    d.jcount = ctx->d_jcount + s;
     CK(cudaMemsetAsync(hs.vhxc, 0, sizeof(double) * c.npts, ctx->stream));
     CK(cudaMemsetAsync(hs.J, 0, sizeof(double) * 3 * (hs.max_steps + 1), ctx->stream));
     CK(cudaMemsetAsync(hs.J0m, 0, sizeof(double) * 3, ctx->stream));
@@ -350,6 +363,7 @@ int layout(tsbz_ctx* ctx) {
   CK(cudaMemsetAsync(ctx->d_steps, 0, sizeof(int) * ctx->subs.size(), ctx->stream));
   CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int) * ctx->subs.size(), ctx->stream));
   CK(cudaMemsetAsync(ctx->d_mask, 0, sizeof(int) * ctx->subs.size(), ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_jcount, 0, sizeof(int) * ctx->subs.size(), ctx->stream));
   {
     const std::vector<int> ones(ctx->subs.size(), 1);
     CK(cudaMemcpyAsync(ctx->d_active, ones.data(), sizeof(int) * ones.size(), cudaMemcpyHostToDevice, ctx->stream));
@@ -385,7 +399,8 @@ template <typename T> int run_field(tsbz_ctx* ctx, int mode) {
   for (auto& hc : ctx->cells) {
     if (hc.unit_ids.empty()) continue;
     // a constant field leaves the phase tables of the last step current
-    const bool keep = mode == TSBZ_FIELD_STEP && hc.tables_step && cell_field_const(ctx, hc);
+    const bool keep = mode == TSBZ_FIELD_STEP && hc.tables_step && cell_field_const(ctx, hc) &&
+                      ctx->propagator == TSBZ_PROP_TAYLOR4;
     launch_field<T>(make_set(ctx, hc), keep ? TSBZ_FIELD_STEP_KEEP : mode, ctx->stream);
     hc.tables_step = mode == TSBZ_FIELD_STEP;
     ++ctx->launches;
@@ -399,7 +414,8 @@ template <typename T> int run_observe(tsbz_ctx* ctx, int fin_mode) {
     if (hc.unit_ids.empty()) continue;
     LaunchSet L = make_set(ctx, hc);
     const bool sep = ctx->precision == TSBZ_FP32 && sep_supported(hc.dev);
-    if (!(fin_mode == TSBZ_FIN_STEP && hc.pa_by_stage)) {
+    // the projections for the current (not needed for the density-only ETRS predictor)
+    if (fin_mode != TSBZ_FIN_RHO && !(fin_mode == TSBZ_FIN_STEP && hc.pa_by_stage)) {
       ev_start(ctx, FAM_BRA);
       if (ctx->precision == TSBZ_FP32_TC)
         launch_bra_tc(L, ctx->psi, ctx->Pa, 1, ctx->stream);
@@ -469,9 +485,10 @@ int run_step_tc(tsbz_ctx* ctx) {
   return TSBZ_OK;
 }
 
-template <typename T> int run_step(tsbz_ctx* ctx) {
-  if (ctx->precision == TSBZ_FP32_TC) return run_step_tc(ctx);
-  run_field<T>(ctx, TSBZ_FIELD_STEP);
+// The four Taylor stages of every cell (after the field launch): psi advances by
+// dt * ctx->dt_scale.  fresh_p: the projections of psi are recomputed first
+// (else they are taken from P when the last step left them there).
+template <typename T> int run_stages(tsbz_ctx* ctx, bool fresh_p, int same_next_allowed) {
   void* srcs[4] = {ctx->psi, ctx->tA, ctx->tB, ctx->tA};
   void* dsts[4] = {ctx->tA, ctx->tB, ctx->tA, nullptr};
   for (auto& hc : ctx->cells) {
@@ -482,13 +499,13 @@ template <typename T> int run_step(tsbz_ctx* ctx) {
       // bulk-staged stage 4 those of psi(t_{n+1}) for the next step and of the
       // current (Pa).  The projections of psi are computed here only when P does
       // not hold them already (first step, or after the state or field changed).
-      if (!ctx->p_next_valid || !hc.pa_by_stage) {
+      if (fresh_p || !ctx->p_next_valid || !hc.pa_by_stage) {
         ev_start(ctx, FAM_BRA);
         launch_bra_sep(L, ctx->psi, ctx->P, 0, 0, ctx->stream);
         ev_stop(ctx);
         if (hc.dev.use_proj) ++ctx->launches;
       }
-      const int same_next = cell_field_const(ctx, hc) ? 1 : 0;
+      const int same_next = (same_next_allowed && cell_field_const(ctx, hc)) ? 1 : 0;
       ev_start(ctx, FAM_STAGE);
       const bool whole = launch_step_fused(L, ctx->psi, ctx->P, ctx->Pa, same_next, ctx->stream);
       ev_stop(ctx);
@@ -518,6 +535,49 @@ template <typename T> int run_step(tsbz_ctx* ctx) {
       ++ctx->launches;
     }
   }
+  return TSBZ_OK;
+}
+
+// Enforced-time-reversal-symmetry step: a Taylor-4 predictor gives rho~(t_{n+1})
+// and v~_eff; then psi(t_{n+1}) = T4(dt/2; A(t_{n+1}), v~_eff) T4(dt/2; A(t_n),
+// v_eff(t_n)) psi(t_n).  psi(t_n) and v_eff(t_n) are kept on the device.
+template <typename T> int run_step_etrs(tsbz_ctx* ctx) {
+  int rc;
+  if (!ctx->psi_save && (rc = dalloc(ctx, ctx->psi_bytes, &ctx->psi_save))) return rc;
+  const int ns = (int)ctx->subs.size();
+  CK(cudaMemcpyAsync(ctx->psi_save, ctx->psi, ctx->psi_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  launch_veff_keep_t<T>(ctx->d_subs, ctx->d_cells, ns, 0, ctx->stream);
+  ++ctx->launches;
+  // predictor: the Taylor-4 step, then rho~ and v~_eff (no current, step unchanged)
+  ctx->dt_scale = 1.0;
+  run_field<T>(ctx, TSBZ_FIELD_STEP);
+  if ((rc = run_stages<T>(ctx, true, 0))) return rc;
+  run_observe<T>(ctx, TSBZ_FIN_RHO);
+  run_hxc<T>(ctx);
+  launch_veff_keep_t<T>(ctx->d_subs, ctx->d_cells, ns, 1, ctx->stream);   // v_eff(t_n) back, v~_eff kept
+  ++ctx->launches;
+  CK(cudaMemcpyAsync(ctx->psi, ctx->psi_save, ctx->psi_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  // the two half steps
+  ctx->dt_scale = 0.5;
+  run_field<T>(ctx, TSBZ_FIELD_AT_NOW);
+  if ((rc = run_stages<T>(ctx, true, 0))) return rc;
+  launch_veff_keep_t<T>(ctx->d_subs, ctx->d_cells, ns, 1, ctx->stream);   // v~_eff in place
+  ++ctx->launches;
+  run_field<T>(ctx, TSBZ_FIELD_AT_NEXT);
+  if ((rc = run_stages<T>(ctx, true, 0))) return rc;
+  ctx->dt_scale = 1.0;
+  run_observe<T>(ctx, TSBZ_FIN_STEP);
+  run_hxc<T>(ctx);
+  ctx->p_next_valid = false;
+  return TSBZ_OK;
+}
+
+template <typename T> int run_step(tsbz_ctx* ctx) {
+  if (ctx->precision == TSBZ_FP32_TC) return run_step_tc(ctx);
+  if (ctx->propagator == TSBZ_PROP_ETRS) return run_step_etrs<T>(ctx);
+  run_field<T>(ctx, TSBZ_FIELD_STEP);
+  int rc = run_stages<T>(ctx, false, 1);
+  if (rc) return rc;
   run_observe<T>(ctx, TSBZ_FIN_STEP);
   run_hxc<T>(ctx);
   ctx->p_next_valid = true;
@@ -743,6 +803,27 @@ int snapshot_restore(tsbz_ctx* ctx, Snapshot& sn) {
   dfree(ctx, sn.P);
   sn.psi = sn.P = nullptr;
   return rc;
+}
+
+// Self-test of the bounded device wait: thread 0 announces a 16-byte
+// transaction on an mbarrier and, if `deliver`, issues the bulk copy that
+// completes it; every thread then waits at most `polls` polls.  Without the
+// copy the wait runs out and the kernel records BK_STATUS_TIMEOUT and returns,
+// with no copy in flight.
+__device__ __align__(16) unsigned char g_selftest_src[16];
+
+__global__ void k_selftest_wait(int polls, int deliver, int* status) {
+  __shared__ __align__(16) unsigned char dst[16];
+  __shared__ __align__(8) unsigned long long mbar;
+  const uint32_t bar = bk_smem(&mbar);
+  if (threadIdx.x == 0) bk_mbar_init(bar, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    bk_mbar_expect_tx(bar, 16);
+    if (deliver) bk_copy_g2s(bk_smem(dst), g_selftest_src, 16, bar);
+  }
+  const bool ok = bk_mbar_wait(bar, 0, polls);
+  if (!__syncthreads_and(ok) && threadIdx.x == 0) atomicOr(status, BK_STATUS_TIMEOUT);
 }
 
 // A captured step holds the kernels of the variants it was captured with.
@@ -1314,6 +1395,20 @@ int tsbz_autotune(tsbz_ctx* ctx, int budget_ms, int* n_tried) {
   return rc ? rc : rr;
 }
 
+int tsbz_set_propagator(tsbz_ctx* ctx, int propagator) {
+  if (!ctx) return TSBZ_EINVAL;
+  if (propagator != TSBZ_PROP_TAYLOR4 && propagator != TSBZ_PROP_ETRS)
+    return set_err(ctx, TSBZ_EINVAL, "unknown propagator");
+  if (propagator == TSBZ_PROP_ETRS && ctx->precision == TSBZ_FP32_TC)
+    return set_err(ctx, TSBZ_EINVAL, "the ETRS propagator runs in TSBZ_FP64 and TSBZ_FP32 modes");
+  if (propagator != ctx->propagator) {
+    ctx->propagator = propagator;
+    ctx->p_next_valid = false;
+    drop_step_graph(ctx);
+  }
+  return TSBZ_OK;
+}
+
 int tsbz_get_variant(tsbz_ctx* ctx, int cell_id, int* variant, int* n_variants_out, double* ms, int n_ms) {
   if (!ctx || cell_id < 0 || cell_id >= (int)ctx->cells.size()) return TSBZ_EINVAL;
   const HostCell& hc = ctx->cells[cell_id];
@@ -1334,6 +1429,24 @@ int tsbz_set_variant(tsbz_ctx* ctx, int cell_id, int variant) {
     drop_step_graph(ctx);
   }
   return TSBZ_OK;
+}
+
+int tsbz_selftest_bounded_wait(int device, int polls, int deliver, int* status_out) {
+  if (polls < 1 || polls > (1 << 24)) return TSBZ_EINVAL;
+  if (cudaSetDevice(device) != cudaSuccess) return TSBZ_ECUDA;
+  int* d_status = nullptr;
+  if (cudaMalloc(&d_status, sizeof(int)) != cudaSuccess) return TSBZ_ENOMEM;
+  int st = 0;
+  cudaError_t e = cudaMemset(d_status, 0, sizeof(int));
+  if (e == cudaSuccess) {
+    k_selftest_wait<<<1, 64>>>(polls, deliver ? 1 : 0, d_status);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(&st, d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(d_status);
+  if (e != cudaSuccess) return TSBZ_ECUDA;
+  if (status_out) *status_out = st;
+  return (st & BK_STATUS_TIMEOUT) ? TSBZ_ETIMEOUT : TSBZ_OK;
 }
 
 const char* tsbz_last_error(tsbz_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }

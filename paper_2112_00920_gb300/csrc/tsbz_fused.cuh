@@ -628,7 +628,7 @@ __global__ void __launch_bounds__(FS_NP, 2) k_stage_fused(LaunchSet L, const flo
     }
     return;
   }
-  fs_march<false>(sm, c, sm.xb, sm.yb, m, (float)S.dt / (float)m, qt[0], qt[1], qt[2], dg0, pq, tout, psi, base);
+  fs_march<false>(sm, c, sm.xb, sm.yb, m, (float)(S.dt * L.dt_scale) / (float)m, qt[0], qt[1], qt[2], dg0, pq, tout, psi, base);
   if (!proj) return;
   __syncthreads();
   uint32_t ah[2][4][4], al[2][4][4];
@@ -712,7 +712,7 @@ __global__ void __launch_bounds__(FS_NP, 2) k_step_fused(LaunchSet L, float2* __
     } else {
       __syncthreads();
     }
-    fs_march<true>(sm, c, tin, vio, m, (float)S.dt / (float)m, q0, q1, q2, dg0, acc, nullptr, psi, base);
+    fs_march<true>(sm, c, tin, vio, m, (float)(S.dt * L.dt_scale) / (float)m, q0, q1, q2, dg0, acc, nullptr, psi, base);
     __syncthreads();
     if (!proj) {
       float2* t = tin;

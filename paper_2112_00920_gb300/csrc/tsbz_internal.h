@@ -86,17 +86,23 @@ struct SubDev {
   int* step;           // steps done
   int* status;         // non-zero: non-finite current seen
   int* active;         // 1 while the sub-simulation advances in the current step
+  void* veff_save;     // [npts] in T: the other v_eff of an ETRS step (null otherwise)
+  double* jtile;       // [16][3] per-tile partial sums of the current (finalize)
+  int* jcount;         // tiles of the finalize done (reset by the last one)
 };
 
 // Finalize modes.
 #define TSBZ_FIN_J0MINUS 0   // write J(0-)
 #define TSBZ_FIN_J0PLUS 1    // write J[0] (t = 0+), only at step 0
 #define TSBZ_FIN_STEP 2      // write J[step + 1] and advance the step
+#define TSBZ_FIN_RHO 3       // density and norms only (ETRS predictor): no current, step unchanged
 // Field modes (which q the observation tables use).
 #define TSBZ_FIELD_STEP 0    // q_half = k + A(t_n + dt/2), q_obs = k + A(t_{n+1})
 #define TSBZ_FIELD_J0PLUS 1  // q_obs = k + A(0+)
 #define TSBZ_FIELD_J0MINUS 2 // q_obs = k
 #define TSBZ_FIELD_STEP_KEEP 3  // as STEP, phase tables kept: the field is constant and they are current
+#define TSBZ_FIELD_AT_NOW 4     // as STEP with the h tables at q = k + A(t_n)      (ETRS first half step)
+#define TSBZ_FIELD_AT_NEXT 5    // as STEP with the h tables at q = k + A(t_{n+1})  (ETRS second half step)
 
 struct LaunchSet {
   // Everything one kernel family needs for the units of one cell.
@@ -114,6 +120,7 @@ struct LaunchSet {
   long long ph_stride;    // complex elements per unit
   void* qt_half;          // [unit][4] in T: q_x, q_y, q_z, |q|^2 / 2 at t_n + dt/2
   int variant;            // kernel variant of this cell (0 = default; chosen by the autotuner)
+  double dt_scale;        // the stage kernels advance by dt * dt_scale (1, or 1/2 in the ETRS half steps)
 };
 
 #ifdef __CUDACC__
@@ -143,6 +150,8 @@ int launch_hxc_t(const SubDev* subs_dev, const int* sub_ids_dev, int n_subs, con
 template <typename T> void launch_convert_in_t(const double2* src, void* dst, long long n, void* stream);
 template <typename T> void launch_convert_out_t(const void* src, double2* dst, long long n, void* stream);
 template <typename T> void launch_veff_frozen_t(const SubDev* subs_dev, int s, const CellDev& c, void* stream);
+template <typename T> void launch_veff_keep_t(const SubDev* subs, const CellDev* cells, int n_subs, int swap,
+                                              void* stream);
 // tensor-core mode (float orbitals)
 void launch_bra_tc(const LaunchSet& L, const void* psi, void* out, int with_d, void* stream);
 void launch_ket_tc(const LaunchSet& L, const void* P, void* V, void* stream);

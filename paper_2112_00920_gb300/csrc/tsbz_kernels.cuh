@@ -80,14 +80,16 @@ __global__ void k_field(LaunchSet L, int mode) {
   // step budget: a sub-simulation that has done max_steps steps sits out the
   // step (every later kernel of the step reads the flag); the evaluations of
   // J(0-), J(0+) and of a restored state take part whatever the step count
-  const bool step_mode = mode == TSBZ_FIELD_STEP || mode == TSBZ_FIELD_STEP_KEEP;
+  const bool step_mode = mode == TSBZ_FIELD_STEP || mode == TSBZ_FIELD_STEP_KEEP || mode == TSBZ_FIELD_AT_NOW ||
+                         mode == TSBZ_FIELD_AT_NEXT;
   const bool act = !step_mode || *S.step < S.max_steps;
   if (U.kloc == 0 && threadIdx.x == 0) *S.active = act ? 1 : 0;
   if (!act) return;
   double ah[3] = {0.0, 0.0, 0.0}, ao[3] = {0.0, 0.0, 0.0};
   if (step_mode) {
     const int step = *S.step;
-    const int jh = 2 * step + 1, jo = 2 * step + 2;
+    const int jh = 2 * step + (mode == TSBZ_FIELD_AT_NOW ? 0 : (mode == TSBZ_FIELD_AT_NEXT ? 2 : 1));
+    const int jo = 2 * step + 2;
     if (jo < S.n_field) {
       for (int ax = 0; ax < 3; ++ax) {
         ah[ax] = S.A[3 * jh + ax];
@@ -283,7 +285,7 @@ __global__ void __launch_bounds__(TSBZ_PT) k_stage(LaunchSet L, const typename C
   const T q2h = qt[3];
   const T v = valid ? reinterpret_cast<const T*>(S.veff)[pp] : (T)0;
   const T diag = q2h + v;
-  const T hdt = (T)S.dt / (T)m;
+  const T hdt = (T)(S.dt * L.dt_scale) / (T)m;
   const V* ph = (const V*)L.ph_half + (long long)u * L.ph_stride;
   const int nm = c.nmax;
   const V zero = cmk<V>((T)0, (T)0);
@@ -412,7 +414,7 @@ __global__ void __launch_bounds__(TSBZ_PT) k_stage_v(LaunchSet L, const typename
   const T* qt = reinterpret_cast<const T*>(L.qt_half) + 4 * u;
   const T q0 = qt[0], q1 = qt[1], q2 = qt[2];
   const T dg = (T)(c.hlapf[0][0] + c.hlapf[1][0] + c.hlapf[2][0]) + qt[3] + reinterpret_cast<const T*>(S.veff)[p];
-  const T hdt = (T)S.dt / (T)m;
+  const T hdt = (T)(S.dt * L.dt_scale) / (T)m;
   for (int b = 0; b < c.n_bands; ++b) {
     const long long base = U.psi_off + (long long)b * c.npts + p;
     const VT* tb = tin + base;
@@ -482,7 +484,7 @@ __global__ void __launch_bounds__(256, 4) k_stage_z(LaunchSet L, const typename 
   const T* qt = reinterpret_cast<const T*>(L.qt_half) + 4 * u;
   const T q0 = qt[0], q1 = qt[1], q2 = qt[2];
   const T dg0 = (T)(c.hlapf[0][0] + c.hlapf[1][0] + c.hlapf[2][0]) + qt[3];
-  const T hdt = (T)S.dt / (T)m;
+  const T hdt = (T)(S.dt * L.dt_scale) / (T)m;
   const T* veff = reinterpret_cast<const T*>(S.veff);
   const long long base0 = U.psi_off + (long long)b * c.npts + col;
   const VT* tb = tin + base0;
@@ -656,7 +658,7 @@ __global__ void __launch_bounds__(256) k_finalize(const SubDev* subs, const Unit
   __shared__ double red[8][3];
   const int s = blockIdx.x;
   const SubDev S = subs[s];
-  if (mode == TSBZ_FIN_STEP && !*S.active) return;   // budget spent: nothing of this step
+  if ((mode == TSBZ_FIN_STEP || mode == TSBZ_FIN_RHO) && !*S.active) return;   // budget spent: nothing of this step
   const CellDev c = cells[S.cell];
   // density: point tile blockIdx.y of the sub-simulation (fixed k and band-group order per point)
   const double inv_nk = 1.0 / S.n_k;
@@ -670,14 +672,17 @@ __global__ void __launch_bounds__(256) k_finalize(const SubDev* subs, const Unit
     }
     S.rho[r] = acc * inv_nk;
   }
-  if (blockIdx.y != 0) return;
-  // current, norms and the step counter: point tile 0 only
+  // current and norms: the units kl = tile + ntile j are this CTA's (warp w takes
+  // every 8th of them); the partial sums of the tiles are added in tile order by
+  // the CTA that finishes last, which also writes J and advances the step
+  const int tile = blockIdx.y, ntile = gridDim.y;
   const int step = *S.step;
-  const bool write_j = (mode == TSBZ_FIN_STEP) || (mask != nullptr && mask[s] != 0 &&
-                                                   (mode == TSBZ_FIN_J0MINUS || step == 0));
+  const bool write_j = mode != TSBZ_FIN_RHO &&
+                       ((mode == TSBZ_FIN_STEP) || (mask != nullptr && mask[s] != 0 &&
+                                                    (mode == TSBZ_FIN_J0MINUS || step == 0)));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double jw[3] = {0.0, 0.0, 0.0};
-  for (int kl = warp; kl < S.n_k; kl += 8) {
+  for (int kl = tile + ntile * warp; kl < S.n_k; kl += ntile * 8) {
     const UnitDev U = units[S.unit0 + kl];
     const int u = S.unit0 + kl;
     double jk[3] = {0.0, 0.0, 0.0}, jn[3] = {0.0, 0.0, 0.0}, nsum = 0.0;
@@ -713,23 +718,35 @@ __global__ void __launch_bounds__(256) k_finalize(const SubDev* subs, const Unit
   }
   if (lane == 0)
     for (int ax = 0; ax < 3; ++ax) red[warp][ax] = jw[ax];
+  __shared__ int last;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double J[3];
-    bool finite = true;
     for (int ax = 0; ax < 3; ++ax) {
       double t = 0.0;
       for (int w = 0; w < 8; ++w) t += red[w][ax];
-      J[ax] = -t / (c.omega * S.n_k);
-      finite = finite && isfinite(J[ax]);
+      S.jtile[3 * tile + ax] = t;
     }
-    if (!finite) *S.status |= 1;
-    if (write_j) {
-      double* dst = (mode == TSBZ_FIN_J0MINUS) ? S.J0m : (mode == TSBZ_FIN_J0PLUS ? S.J : S.J + 3LL * (step + 1));
-      for (int ax = 0; ax < 3; ++ax) dst[ax] = J[ax];
-    }
-    if (mode == TSBZ_FIN_STEP) *S.step = step + 1;
+    __threadfence();
+    last = atomicAdd(S.jcount, 1) == ntile - 1;
   }
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  __threadfence();
+  double J[3];
+  bool finite = true;
+  for (int ax = 0; ax < 3; ++ax) {
+    double t = 0.0;
+    for (int y = 0; y < ntile; ++y) t += __ldcg(S.jtile + 3 * y + ax);
+    J[ax] = -t / (c.omega * S.n_k);
+    finite = finite && isfinite(J[ax]);
+  }
+  *S.jcount = 0;
+  if (!finite) *S.status |= 1;
+  if (write_j) {
+    double* dst = (mode == TSBZ_FIN_J0MINUS) ? S.J0m : (mode == TSBZ_FIN_J0PLUS ? S.J : S.J + 3LL * (step + 1));
+    for (int ax = 0; ax < 3; ++ax) dst[ax] = J[ax];
+  }
+  if (mode == TSBZ_FIN_STEP) *S.step = step + 1;
 }
 
 // ----------------------------------------------------------------------------
@@ -811,6 +828,140 @@ __global__ void k_hxc_final(const SubDev* subs, const int* sub_ids, int n_subs, 
   if (S.xc) v += pz81_potential(S.rho[r]);
   S.vhxc[r] = v;
   reinterpret_cast<T*>(S.veff)[r] = (T)(c.vloc[r] + v);
+}
+
+// ----------------------------------------------------------------------------
+// v_Hxc of one sub-simulation per CTA on small power-of-two grids (each axis
+// 2..16, at most 4096 points): rho -> 3-D FFT in shared memory (radix-2 line
+// transforms of each axis, one line per thread in registers), Poisson scaling
+// (G = 0 -> 0), inverse FFT, PZ81, v_eff.  The same FP64 arithmetic as the
+// multi-launch path with the O(N^2) line DFTs replaced by FFTs.
+// ----------------------------------------------------------------------------
+#define HXC_FFT_MAXN 16
+#define HXC_FFT_MAXPTS 4096
+
+// In-place radix-2 transform of the line x (length N, a power of two):
+// x[k] <- sum_n x[n] exp(sign 2 pi i n k / N); tw[m] = exp(2 pi i m / N).
+template <int N>
+__device__ __forceinline__ void hxc_fft_line(double2 (&x)[N], const double2* __restrict__ tw, int sign) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    int j = 0;
+#pragma unroll
+    for (int b = 1, r = i; b < N; b <<= 1, r >>= 1) j = (j << 1) | (r & 1);
+    if (j > i) {
+      const double2 t = x[i];
+      x[i] = x[j];
+      x[j] = t;
+    }
+  }
+#pragma unroll
+  for (int len = 2; len <= N; len <<= 1) {
+    const int half = len >> 1, step = N / len;
+#pragma unroll
+    for (int i = 0; i < N; i += len) {
+#pragma unroll
+      for (int k = 0; k < half; ++k) {
+        const double2 w = tw[k * step];
+        const double wi = sign * w.y;
+        const double2 v = x[i + k + half];
+        const double2 vw = make_double2(v.x * w.x - v.y * wi, v.x * wi + v.y * w.x);
+        const double2 u = x[i + k];
+        x[i + k] = make_double2(u.x + vw.x, u.y + vw.y);
+        x[i + k + half] = make_double2(u.x - vw.x, u.y - vw.y);
+      }
+    }
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void hxc_fft_axis(double2* w, int npts, int stride, const double2* __restrict__ tw,
+                                             int sign) {
+  // lines: every r0 whose coordinate on this axis is 0, r0 = outer * (stride * N) + in, in < stride
+  const int lines = npts / N;
+  for (int l = threadIdx.x; l < lines; l += blockDim.x) {
+    const int in = l % stride, outer = l / stride;
+    const int r0 = outer * stride * N + in;
+    double2 x[N];
+#pragma unroll
+    for (int n = 0; n < N; ++n) x[n] = w[r0 + n * stride];
+    hxc_fft_line<N>(x, tw, sign);
+#pragma unroll
+    for (int n = 0; n < N; ++n) w[r0 + n * stride] = x[n];
+  }
+}
+
+__device__ __forceinline__ void hxc_fft_any(double2* w, int npts, int n, int stride, const double2* tw, int sign) {
+  switch (n) {
+    case 2: hxc_fft_axis<2>(w, npts, stride, tw, sign); break;
+    case 4: hxc_fft_axis<4>(w, npts, stride, tw, sign); break;
+    case 8: hxc_fft_axis<8>(w, npts, stride, tw, sign); break;
+    default: hxc_fft_axis<16>(w, npts, stride, tw, sign); break;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_hxc_fft(const SubDev* subs, const int* sub_ids, CellDev c,
+                                                  const double2* __restrict__ tw1, const double2* __restrict__ tw2,
+                                                  const double2* __restrict__ tw3) {
+  extern __shared__ __align__(16) double2 hw[];
+  const SubDev S = subs[sub_ids[blockIdx.x]];
+  const int npts = c.npts, n12 = c.n1 * c.n2;
+  for (int r = threadIdx.x; r < npts; r += blockDim.x) hw[r] = make_double2(S.rho[r], 0.0);
+  __syncthreads();
+  hxc_fft_any(hw, npts, c.n1, 1, tw1, -1);
+  __syncthreads();
+  hxc_fft_any(hw, npts, c.n2, c.n1, tw2, -1);
+  __syncthreads();
+  hxc_fft_any(hw, npts, c.n3, n12, tw3, -1);
+  __syncthreads();
+  for (int r = threadIdx.x; r < npts; r += blockDim.x) {
+    const int i1 = r % c.n1, i2 = (r / c.n1) % c.n2, i3 = r / n12;
+    const int m1 = i1 < (c.n1 + 1) / 2 ? i1 : i1 - c.n1;
+    const int m2 = i2 < (c.n2 + 1) / 2 ? i2 : i2 - c.n2;
+    const int m3 = i3 < (c.n3 + 1) / 2 ? i3 : i3 - c.n3;
+    const double g1 = m1 * c.gsq_scale[0], g2 = m2 * c.gsq_scale[1], g3 = m3 * c.gsq_scale[2];
+    const double gg = g1 * g1 + g2 * g2 + g3 * g3;
+    const double f = gg > 0.0 ? 4.0 * M_PI / (gg * npts) : 0.0;
+    hw[r] = make_double2(hw[r].x * f, hw[r].y * f);
+  }
+  __syncthreads();
+  hxc_fft_any(hw, npts, c.n3, n12, tw3, +1);
+  __syncthreads();
+  hxc_fft_any(hw, npts, c.n2, c.n1, tw2, +1);
+  __syncthreads();
+  hxc_fft_any(hw, npts, c.n1, 1, tw1, +1);
+  __syncthreads();
+  for (int r = threadIdx.x; r < npts; r += blockDim.x) {
+    double v = 0.0;
+    if (S.hartree) v += hw[r].x;
+    if (S.xc) v += pz81_potential(S.rho[r]);
+    S.vhxc[r] = v;
+    reinterpret_cast<T*>(S.veff)[r] = (T)(c.vloc[r] + v);
+  }
+}
+
+__host__ __device__ inline bool hxc_fft_ok(int n) { return n == 2 || n == 4 || n == 8 || n == 16; }
+
+// v_eff of every sub-simulation of the list: copied to veff_save (swap = 0) or
+// exchanged with it (swap = 1).
+template <typename T>
+__global__ void k_veff_keep(const SubDev* subs, const CellDev* cells, int swap) {
+  const SubDev S = subs[blockIdx.y];
+  const int npts = cells[S.cell].npts;
+  T* a = reinterpret_cast<T*>(S.veff);
+  T* b = reinterpret_cast<T*>(S.veff_save);
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < npts; r += gridDim.x * blockDim.x) {
+    const T v = a[r];
+    if (swap) a[r] = b[r];
+    b[r] = v;
+  }
+}
+
+template <typename T> void launch_veff_keep_t(const SubDev* subs, const CellDev* cells, int n_subs, int swap,
+                                              void* stream) {
+  if (n_subs == 0) return;
+  k_veff_keep<T><<<dim3(16, n_subs), 256, 0, (cudaStream_t)stream>>>(subs, cells, swap);
 }
 
 template <typename T>
@@ -895,7 +1046,7 @@ void launch_finalize_t(const SubDev* subs, int n_subs, const UnitDev* units, con
                        const double* nrm_part, const int* mask, int mode, void* stream) {
   using V = typename Cplx<T>::type;
   if (n_subs == 0) return;
-  // 16 density tiles per sub-simulation; tile 0 also forms J, the norms and the step counter
+  // 16 tiles per sub-simulation: density points, and units for the current and the norms
   k_finalize<T><<<dim3(n_subs, 16), 256, 0, (cudaStream_t)stream>>>(subs, units, cells_dev, q_obs, (const V*)Pa,
                                                                     rho_part, jk_part, nrm_part, mask, mode);
 }
@@ -905,6 +1056,12 @@ int launch_hxc_t(const SubDev* subs_dev, const int* sub_ids_dev, int n_subs, con
                  double2* wb, double2* const tw[3], void* stream) {
   if (n_subs == 0) return 0;
   cudaStream_t st = (cudaStream_t)stream;
+  if (hxc_fft_ok(c.n1) && hxc_fft_ok(c.n2) && hxc_fft_ok(c.n3) && c.npts <= HXC_FFT_MAXPTS) {
+    const size_t sm = (size_t)c.npts * sizeof(double2);
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_hxc_fft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_hxc_fft<T><<<n_subs, 256, sm, st>>>(subs_dev, sub_ids_dev, c, tw[0], tw[1], tw[2]);
+    return 1;
+  }
   const long long total = (long long)n_subs * c.npts;
   const int thr = 256;
   const unsigned blocks = (unsigned)((total + thr - 1) / thr);

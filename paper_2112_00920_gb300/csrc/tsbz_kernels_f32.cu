@@ -13,3 +13,4 @@ template int launch_hxc_t<float>(const SubDev*, const int*, int, const CellDev&,
 template void launch_convert_in_t<float>(const double2*, void*, long long, void*);
 template void launch_convert_out_t<float>(const void*, double2*, long long, void*);
 template void launch_veff_frozen_t<float>(const SubDev*, int, const CellDev&, void*);
+template void launch_veff_keep_t<float>(const SubDev*, const CellDev*, int, int, void*);

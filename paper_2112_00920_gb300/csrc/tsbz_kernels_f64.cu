@@ -13,3 +13,4 @@ template int launch_hxc_t<double>(const SubDev*, const int*, int, const CellDev&
 template void launch_convert_in_t<double>(const double2*, void*, long long, void*);
 template void launch_convert_out_t<double>(const void*, double2*, long long, void*);
 template void launch_veff_frozen_t<double>(const SubDev*, int, const CellDev&, void*);
+template void launch_veff_keep_t<double>(const SubDev*, const CellDev*, int, int, void*);

@@ -417,7 +417,7 @@ __global__ void __launch_bounds__(256, 4) k_stage_zf(LaunchSet L, const float2* 
   const float* qt = reinterpret_cast<const float*>(L.qt_half) + 4 * u;
   const float q0 = qt[0], q1 = qt[1], q2 = qt[2];
   const float dg0 = c.hlapf[0][0] + c.hlapf[1][0] + c.hlapf[2][0] + qt[3];
-  const float hdt = (float)S.dt / (float)m;
+  const float hdt = (float)(S.dt * L.dt_scale) / (float)m;
   const float* veff = reinterpret_cast<const float*>(S.veff);
   const long long base0 = U.psi_off + (long long)b * c.npts + col;
   const float2* tb = tin + base0;

@@ -11,13 +11,18 @@ FP64_J_TOL = 1e-10      # err_J bar of the FP64 path
 FP64_RHO_TOL = 1e-12    # err_rho and err_norm bars of the FP64 path
 
 
-def gpu_run(cell, subs, precision="fp64", hxc="scf", v_frozen=None, fd_nd=4, steps=None):
+def gpu_run(cell, subs, precision="fp64", hxc="scf", v_frozen=None, fd_nd=4, steps=None, propagator="taylor4",
+            graphs=None):
     """subs: list of dict(mp, shift, psi=(n_k,n_b,...), dt, n_steps, field=Kick|Pulse|samples).
     The library computes its own k-points (Eq. 10) from (mp, shift).
     Returns (propagator, list of dict(J, J0m, rho, norms))."""
     from paper_2112_00920_gb300 import Propagator, shifted_kpoints
 
     P = Propagator(precision)
+    if propagator != "taylor4":
+        P.set_propagator(propagator)
+    if graphs is not None:
+        P.set_graphs(graphs)
     cid = P.add_cell_spec(cell, hxc=hxc, fd_nd=fd_nd)
     sids = [P.add_subsim(cid, s.get("k_gpu", shifted_kpoints(cell.a, s["mp"], s["shift"])), s["dt"], s["n_steps"])
             for s in subs]
@@ -40,13 +45,13 @@ def gpu_run(cell, subs, precision="fp64", hxc="scf", v_frozen=None, fd_nd=4, ste
     return P, out
 
 
-def oracle_run(cell, s, hxc="scf", v_frozen=None, steps=None):
+def oracle_run(cell, s, hxc="scf", v_frozen=None, steps=None, propagator="taylor4"):
     n = steps if steps is not None else s["n_steps"]
     f = s["field"]
     a = dynamics.field_samples(f, s["dt"], n) if isinstance(f, (W.Kick, W.Pulse)) else np.asarray(f)[: 2 * n + 1]
     k = s.get("k_orc", kpoints.kpoints_cartesian(cell.a, s["mp"], s["shift"]))
     return dynamics.propagate(cell, k, s["psi"], s["dt"], n, a, hxc=hxc, v_hxc_frozen=v_frozen,
-                              keep_state=False)
+                              keep_state=False, propagator=propagator)
 
 
 def compare(gpu, orc, j_tol, rho_tol, norm_tol=None):

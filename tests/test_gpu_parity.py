@@ -93,16 +93,17 @@ def test_parity_fp32_small(case):
     print(f"fp32 {case}:", errs)
 
 
-@pytest.mark.parametrize("precision,n,per_step", [("fp32", (8, 8, 8), 16), ("fp32", (16, 16, 16), 13),
+@pytest.mark.parametrize("precision,n,per_step", [("fp32", (8, 8, 8), 8), ("fp32", (16, 16, 16), 5),
                                                   ("fp32", (10, 12, 14), 21),
-                                                  ("fp32_tc", (8, 8, 8), 25), ("fp64", (8, 8, 8), 21)])
+                                                  ("fp32_tc", (8, 8, 8), 17), ("fp64", (8, 8, 8), 13)])
 def test_kernel_launches_per_step(precision, n, per_step):
     """Which kernel sequence a step runs (after the first): the fused single-precision
-    stage takes field + 4 stages + observation + finalize + 9 v_Hxc launches (stage 4
-    leaves the projections of the next step and of the current), and on 16^3 cells
-    whose atoms form z groups the four stages are one launch; the generic and
-    FP64 paths take a projection before each of the 4 stages and one for the
-    current; the tensor-core mode adds a ket launch before each stage."""
+    stage takes field + 4 stages + observation + finalize + v_Hxc (stage 4 leaves the
+    projections of the next step and of the current), and on 16^3 cells whose atoms
+    form z groups the four stages are one launch; v_Hxc is one launch on grids of
+    power-of-two axes up to 16 (9 otherwise); the generic and FP64 paths take a
+    projection before each of the 4 stages and one for the current; the
+    tensor-core mode adds a ket launch before each stage."""
     from paper_2112_00920_gb300 import Propagator, shifted_kpoints
     cell = W.cell_tiny(atoms="pair", n=n, a=(6.0, 6.0, 6.0), n_bands=4)
     s = random_subsim(cell, (1, 1, 1), (0.25, 0.25, 0.25), 0.08, 4, W.Kick(k0=0.01), seed=5)
@@ -295,6 +296,22 @@ def test_error_paths():
         P.propagate(-1)
     assert e.value.code == -1
     P.close()
+
+
+def test_bounded_wait_times_out_without_fault():
+    """Failure detection without a GPU fault: a bulk-copy barrier that no copy
+    completes makes the bounded device wait run out; the kernel records the
+    timeout and returns, the call reports TSBZ_ETIMEOUT, and the device keeps
+    working (the delivered case and a propagation afterwards succeed)."""
+    from paper_2112_00920_gb300 import _lib
+    rc, st = _lib.selftest_bounded_wait(0, polls=1000, deliver=False)
+    assert rc == -4 and (st & 2)
+    rc, st = _lib.selftest_bounded_wait(0, polls=1 << 20, deliver=True)
+    assert rc == 0 and st == 0
+    cell = _tiny_pair()
+    subs = [random_subsim(cell, (2, 1, 1), (0.25, 0.5, 0.0), 0.08, 2, W.Kick(k0=0.01), seed=3)]
+    _, g = gpu_run(cell, subs, precision="fp32")
+    compare(g[0], oracle_run(cell, subs[0]), 1e-4, 1e-5)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_tc"])

@@ -102,6 +102,68 @@ def test_free_electron_closed_form(field):
     np.testing.assert_allclose(res["rho"], rho_uniform, rtol=1e-12)
 
 
+@pytest.mark.parametrize("field", ["kick", "pulse"])
+def test_etrs_free_electron_closed_form(field):
+    """The ETRS step on plane waves in an empty cell: two half-step Taylor factors
+    with the kinetic energy at A(t_n) and A(t_{n+1}) and v_xc of the predictor density."""
+    cell = W.free_electron(W.cell_tiny(atoms="none", n=(8, 8, 8), a=(6.0, 6.5, 7.0), n_bands=4))
+    g = C.Grid(cell)
+    kc = kpoints.kpoints_cartesian(cell.a, (2, 2, 1), (0.0, 0.0, 0.0))
+    gints = analysis.lowest_plane_waves(g, kc, 4)
+    u0 = analysis.plane_wave_orbitals(g, gints)
+    # a long step, so that |T4|^2 departs from 1 and the two schemes differ visibly
+    dt, n = 0.45, 12
+    f = W.Kick(k0=0.05, direction=(0.6, 0.8, 0.0)) if field == "kick" else W.Pulse(e0=0.3, omega0=0.3, t_pulse=5.4)
+    a = dynamics.field_samples(f, dt, n)
+    res = dynamics.propagate(cell, kc, u0, dt, n, a, propagator="etrs")
+    jc, j0, w = analysis.free_electron_current(g, cell.occ, kc, gints, dt, n, a, propagator="etrs")
+    np.testing.assert_allclose(res["J"], jc, rtol=0, atol=1e-12 * np.max(np.abs(jc)))
+    np.testing.assert_allclose(res["norms"], w, rtol=1e-12)
+    # and it differs from the Taylor-4 step beyond round-off (the pin can tell them apart)
+    jt, _, _ = analysis.free_electron_current(g, cell.occ, kc, gints, dt, n, a)
+    assert np.max(np.abs(jt - jc)) > 1e-9 * np.max(np.abs(jc))
+
+
+def test_etrs_constant_h_is_two_half_taylor_steps():
+    """Frozen v_Hxc and a constant field: the predictor does not matter and one ETRS
+    step is the square of the dense half-step polynomial sum_{m<=4} (-i dt/2 H)^m/m!."""
+    cell = _tiny()
+    ops = dynamics.Operators(cell)
+    kc = np.array([[0.1, 0.2, -0.3]])
+    kick = W.Kick(k0=0.02, direction=(0.0, 0.6, 0.8))
+    dt = 0.08
+    a = dynamics.field_samples(kick, dt, 1)
+    u = W.random_complex((1, 3, 6, 6, 6), 13)
+    res = dynamics.propagate(cell, kc, u, dt, 1, a, hxc="frozen", v_hxc_frozen=np.zeros((6, 6, 6)),
+                             propagator="etrs")
+    q = kc[0] + a[1]
+    H = dense_h(cell, q, ops.vloc, ops.beta, ops.disp, ops.e_kb)
+    M = -0.5j * dt * H
+    half = np.eye(216) + M + M @ M / 2 + M @ M @ M / 6 + M @ M @ M @ M / 24
+    np.testing.assert_allclose(res["u"][0].reshape(3, -1).T, half @ half @ u[0].reshape(3, -1).T, atol=1e-12)
+
+
+def test_etrs_second_order_in_dt():
+    """Self-consistent v_Hxc under a pulse: the ETRS current at t = 0.96 converges
+    at second order or better in dt (error ratio >= 3.5 when dt halves)."""
+    cell = W.cell_tiny(atoms="pair", n=(6, 6, 6), a=(5.0, 5.0, 5.0), proj_half=3.0, n_bands=2)
+    g = C.Grid(cell)
+    kc = kpoints.kpoints_cartesian(cell.a, (1, 1, 1), (0.25, 0.5, 0.0))
+    u0 = W.random_orbitals(1, 2, cell.n, g.dv, seed=8)
+    pulse = W.Pulse(e0=0.3, omega0=1.5, t_pulse=0.96)
+    t_end = 0.96
+
+    def run(n):
+        dt = t_end / n
+        return dynamics.propagate(cell, kc, u0, dt, n, dynamics.field_samples(pulse, dt, n),
+                                  propagator="etrs")["J"][-1]
+
+    ref = run(96)
+    e1 = np.linalg.norm(run(6) - ref)
+    e2 = np.linalg.norm(run(12) - ref)
+    assert e1 / e2 >= 3.5, (e1, e2)
+
+
 def test_free_electron_drude_limit():
     g = C.Grid(W.free_electron(W.cell_a()))
     n_e = 32.0
