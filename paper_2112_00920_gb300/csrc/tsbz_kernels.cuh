@@ -831,11 +831,12 @@ __global__ void k_hxc_final(const SubDev* subs, const int* sub_ids, int n_subs, 
 }
 
 // ----------------------------------------------------------------------------
-// v_Hxc of one sub-simulation per CTA on small power-of-two grids (each axis
-// 2..16, at most 4096 points): rho -> 3-D FFT in shared memory (radix-2 line
-// transforms of each axis, one line per thread in registers), Poisson scaling
-// (G = 0 -> 0), inverse FFT, PZ81, v_eff.  The same FP64 arithmetic as the
-// multi-launch path with the O(N^2) line DFTs replaced by FFTs.
+// Hartree potential of one sub-simulation per CTA on small power-of-two grids
+// (each axis 2..16, at most 4096 points): rho -> 3-D FFT in shared memory
+// (radix-2 line transforms of each axis, one line per thread in registers),
+// Poisson scaling (G = 0 -> 0), inverse FFT, into the work array.  The same
+// FP64 arithmetic as the multi-launch path with the O(N^2) line DFTs replaced
+// by FFTs; PZ81 and v_eff are then formed point-parallel by k_hxc_final.
 // ----------------------------------------------------------------------------
 #define HXC_FFT_MAXN 16
 #define HXC_FFT_MAXPTS 4096
@@ -900,10 +901,9 @@ __device__ __forceinline__ void hxc_fft_any(double2* w, int npts, int n, int str
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_hxc_fft(const SubDev* subs, const int* sub_ids, CellDev c,
+static __global__ void __launch_bounds__(256) k_hxc_fft(const SubDev* subs, const int* sub_ids, CellDev c,
                                                   const double2* __restrict__ tw1, const double2* __restrict__ tw2,
-                                                  const double2* __restrict__ tw3) {
+                                                  const double2* __restrict__ tw3, double2* __restrict__ work) {
   extern __shared__ __align__(16) double2 hw[];
   const SubDev S = subs[sub_ids[blockIdx.x]];
   const int npts = c.npts, n12 = c.n1 * c.n2;
@@ -932,13 +932,9 @@ __global__ void __launch_bounds__(256) k_hxc_fft(const SubDev* subs, const int* 
   __syncthreads();
   hxc_fft_any(hw, npts, c.n1, 1, tw1, +1);
   __syncthreads();
-  for (int r = threadIdx.x; r < npts; r += blockDim.x) {
-    double v = 0.0;
-    if (S.hartree) v += hw[r].x;
-    if (S.xc) v += pz81_potential(S.rho[r]);
-    S.vhxc[r] = v;
-    reinterpret_cast<T*>(S.veff)[r] = (T)(c.vloc[r] + v);
-  }
+  // v_H of the sub-simulation; PZ81 and v_eff follow in k_hxc_final over all points
+  double2* out = work + (long long)blockIdx.x * npts;
+  for (int r = threadIdx.x; r < npts; r += blockDim.x) out[r] = hw[r];
 }
 
 __host__ __device__ inline bool hxc_fft_ok(int n) { return n == 2 || n == 4 || n == 8 || n == 16; }
@@ -1056,13 +1052,14 @@ int launch_hxc_t(const SubDev* subs_dev, const int* sub_ids_dev, int n_subs, con
                  double2* wb, double2* const tw[3], void* stream) {
   if (n_subs == 0) return 0;
   cudaStream_t st = (cudaStream_t)stream;
+  const long long total = (long long)n_subs * c.npts;
   if (hxc_fft_ok(c.n1) && hxc_fft_ok(c.n2) && hxc_fft_ok(c.n3) && c.npts <= HXC_FFT_MAXPTS) {
     const size_t sm = (size_t)c.npts * sizeof(double2);
-    if (sm > 48 * 1024) cudaFuncSetAttribute(k_hxc_fft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_hxc_fft<T><<<n_subs, 256, sm, st>>>(subs_dev, sub_ids_dev, c, tw[0], tw[1], tw[2]);
-    return 1;
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_hxc_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_hxc_fft<<<n_subs, 256, sm, st>>>(subs_dev, sub_ids_dev, c, tw[0], tw[1], tw[2], wa);
+    k_hxc_final<T><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(subs_dev, sub_ids_dev, n_subs, c, wa);
+    return 2;
   }
-  const long long total = (long long)n_subs * c.npts;
   const int thr = 256;
   const unsigned blocks = (unsigned)((total + thr - 1) / thr);
   int launches = 0;

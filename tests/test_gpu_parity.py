@@ -93,15 +93,15 @@ def test_parity_fp32_small(case):
     print(f"fp32 {case}:", errs)
 
 
-@pytest.mark.parametrize("precision,n,per_step", [("fp32", (8, 8, 8), 8), ("fp32", (16, 16, 16), 5),
+@pytest.mark.parametrize("precision,n,per_step", [("fp32", (8, 8, 8), 9), ("fp32", (16, 16, 16), 6),
                                                   ("fp32", (10, 12, 14), 21),
-                                                  ("fp32_tc", (8, 8, 8), 17), ("fp64", (8, 8, 8), 13)])
+                                                  ("fp32_tc", (8, 8, 8), 18), ("fp64", (8, 8, 8), 14)])
 def test_kernel_launches_per_step(precision, n, per_step):
     """Which kernel sequence a step runs (after the first): the fused single-precision
     stage takes field + 4 stages + observation + finalize + v_Hxc (stage 4 leaves the
     projections of the next step and of the current), and on 16^3 cells whose atoms
-    form z groups the four stages are one launch; v_Hxc is one launch on grids of
-    power-of-two axes up to 16 (9 otherwise); the generic and FP64 paths take a
+    form z groups the four stages are one launch; v_Hxc is two launches on grids of
+    power-of-two axes up to 16 (FFT Hartree, then PZ81 and v_eff; 9 otherwise); the generic and FP64 paths take a
     projection before each of the 4 stages and one for the current; the
     tensor-core mode adds a ket launch before each stage."""
     from paper_2112_00920_gb300 import Propagator, shifted_kpoints
