@@ -155,9 +155,23 @@ def test_autotune_restores_state_and_keeps_parity(precision):
     P.close()
 
 
+def _cube16(frac):
+    return W.cell_tiny(atoms="pair", n=(16, 16, 16), a=(8.0, 8.5, 9.0), n_bands=4,
+                       atom_frac=np.asarray(frac, dtype=np.float64))
+
+
+# 16^3 cells whose atoms form z groups of one atom (whole step runs), no usable
+# groups (6 distinct z planes) or a group of three (both take the per-atom kernels)
+_Z_ONE = [[0.1, 0.2, 0.3], [0.55, 0.6, 0.7]]
+_Z_SIX = [[0.05 * i + 0.1, 0.13 * i, 0.11 * i + 0.02] for i in range(6)]
+_Z_THREE = [[0.0, 0.0, 0.25], [0.5, 0.25, 0.25], [0.25, 0.75, 0.25]]
+
 VARIANT_CASES = [
     # (precision, cell factory, mp, number of variants)
     ("fp32", W.cell_a, (2, 1, 1), 3),                 # whole step / fused tensor-core stage / CUDA-core z-march
+    ("fp32", lambda: _cube16(_Z_ONE), (2, 1, 1), 3),  # z groups of one atom
+    ("fp32", lambda: _cube16(_Z_SIX), (2, 1, 1), 2),  # per-atom fused stage / z-march
+    ("fp32", lambda: _cube16(_Z_THREE), (1, 2, 1), 2),
     ("fp32", _tiny, (2, 2, 1), 2),                    # bulk-staged 8^3 stage / z-march
     ("fp32", lambda: W.cell_tiny(atoms="offgrid", n=(10, 12, 14), a=(7.0, 8.0, 9.0), n_bands=3), (3, 1, 1), 3),
     ("fp64", _tiny, (2, 2, 1), 3),                    # point-parallel: 8, 4, 16 bands per chunk
