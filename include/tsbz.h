@@ -206,6 +206,26 @@ int tsbz_set_profiling(tsbz_ctx* ctx, int on);
  * step counters and field samples from device memory. */
 int tsbz_set_graphs(tsbz_ctx* ctx, int on);
 
+/* Kohn-Sham ground state on the GPU (the step before the propagation;
+ * Sec. II.B step 2 starts every sub-simulation from converged orbitals): for
+ * every sub-simulation, the n_bands lowest states of h_k at A = 0 on each of
+ * its k-points with fixed occupations, self-consistent in rho on its own
+ * k-set (frozen cells keep their v_Hxc).  Chebyshev-filtered subspace
+ * iteration (filter of the given degree damping [lam + 0.1 Ha, b], lam the
+ * block's largest Ritz value and b an upper bound of the spectrum; about 48
+ * is a good degree; Cholesky-QR re-orthonormalisation)
+ * with Pulay density mixing (history 8, mixing parameter mix) from a uniform
+ * density, until dV sum |rho_out - rho_in| / N_e <= tol for every
+ * sub-simulation.  The loaded orbitals are the starting block and are
+ * replaced by an orthonormal basis of the converged occupied space (the
+ * density, the current and every propagated observable depend on that space
+ * only); rho, v_Hxc and J(0-) are then recomputed from them.  TSBZ_FP64
+ * contexts, at most 32 bands per cell, before the first step.  *iters_out and
+ * *err_out (nullable): iterations done and the last density error.  Returns
+ * TSBZ_ESTATE when max_iter iterations did not converge. */
+int tsbz_ground_state(tsbz_ctx* ctx, int max_iter, double tol, int degree, double mix, int* iters_out,
+                      double* err_out);
+
 /* Choose the time step (TSBZ_PROP_TAYLOR4 or TSBZ_PROP_ETRS).  The paper
  * leaves the propagator to its TDDFT code; ETRS costs three Taylor-4
  * expansions per step (predictor and two half steps) and keeps psi(t_n) and

@@ -88,6 +88,8 @@ _SIGS = {
     "tsbz_set_profiling": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "tsbz_set_graphs": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "tsbz_set_propagator": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
+    "tsbz_ground_state": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_double, _I, _D],
+                          ctypes.c_int),
     "tsbz_autotune": ([ctypes.c_void_p, ctypes.c_int, _I], ctypes.c_int),
     "tsbz_get_variant": ([ctypes.c_void_p, ctypes.c_int, _I, _I, _D, ctypes.c_int], ctypes.c_int),
     "tsbz_set_variant": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_int], ctypes.c_int),
@@ -378,6 +380,14 @@ class Propagator:
 
     def set_profiling(self, on: bool):
         self._check(self.lib.tsbz_set_profiling(self.ctx, 1 if on else 0), "tsbz_set_profiling")
+
+    def ground_state(self, max_iter: int = 80, tol: float = 1e-9, degree: int = 48, mix: float = 0.35):
+        """Solve the Kohn-Sham ground state of every sub-simulation on the GPU from the
+        loaded starting orbitals; returns (iterations, final density error)."""
+        it, err = ctypes.c_int(), ctypes.c_double()
+        self._check(self.lib.tsbz_ground_state(self.ctx, int(max_iter), float(tol), int(degree), float(mix),
+                                               ctypes.byref(it), ctypes.byref(err)), "tsbz_ground_state")
+        return it.value, err.value
 
     def set_propagator(self, name: str):
         """"taylor4" (default) or "etrs"."""

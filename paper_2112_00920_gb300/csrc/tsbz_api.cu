@@ -107,6 +107,7 @@ struct tsbz_ctx {
   int propagator = TSBZ_PROP_TAYLOR4;
   double dt_scale = 1.0;     // of the stage launches being issued (ETRS half steps: 1/2)
   void* psi_save = nullptr;  // psi(t_n) during an ETRS step (allocated on first use)
+  const double* d_filt = nullptr;  // ground-state solver: filter coefficients per unit (stage m = 0)
   double* d_jtile = nullptr; // per sub-simulation: [16][3] partial currents of the finalize
   int* d_jcount = nullptr;   // per sub-simulation: finalize tiles done
   double2* work_a = nullptr;
@@ -219,6 +220,7 @@ LaunchSet make_set(tsbz_ctx* ctx, HostCell& hc) {
   L.qt_half = ctx->qt_half;
   L.variant = hc.variant;
   L.dt_scale = ctx->dt_scale;
+  L.filt = ctx->d_filt;
   return L;
 }
 
@@ -1393,6 +1395,266 @@ int tsbz_autotune(tsbz_ctx* ctx, int budget_ms, int* n_tried) {
   drop_step_graph(ctx);
   if (n_tried) *n_tried = tried;
   return rc ? rc : rr;
+}
+
+int tsbz_ground_state(tsbz_ctx* ctx, int max_iter, double tol, int degree, double mix, int* iters_out,
+                      double* err_out) {
+  if (!ctx || max_iter < 1 || !(tol > 0.0) || degree < 2 || degree > 200 || !(mix > 0.0 && mix <= 1.0))
+    return TSBZ_EINVAL;
+  if (ctx->precision != TSBZ_FP64)
+    return set_err(ctx, TSBZ_EINVAL, "the ground-state solver runs in TSBZ_FP64 contexts");
+  if (!ctx->laid_out) return set_err(ctx, TSBZ_ESTATE, "load starting orbitals first");
+  for (auto& hs : ctx->subs) {
+    if (!hs.loaded) return set_err(ctx, TSBZ_ESTATE, "every sub-simulation needs starting orbitals");
+    if (hs.steps != 0) return set_err(ctx, TSBZ_ESTATE, "the ground state is solved before the first step");
+  }
+  int max_units = 0;
+  for (auto& hc : ctx->cells) {
+    if (hc.dev.n_bands > scf_max_bands())
+      return set_err(ctx, TSBZ_EINVAL, "the ground-state solver takes at most 32 bands per cell");
+    max_units = std::max(max_units, (int)hc.unit_ids.size());
+  }
+  int rc = ensure_ready(ctx);
+  if (rc) return rc;
+  const size_t ns = ctx->subs.size();
+  // scratch: Gram matrices, coefficients, bounds
+  void *dS = nullptr, *dH = nullptr, *dC = nullptr;
+  double *dlam = nullptr, *dfa = nullptr, *dfb = nullptr, *dfc = nullptr;
+  int* dbad = nullptr;
+  const size_t mat = (size_t)max_units * 32 * 32 * sizeof(double2);
+  auto cleanup = [&]() {
+    for (void* p : {dS, dH, dC, (void*)dlam, (void*)dfa, (void*)dfb, (void*)dfc, (void*)dbad}) dfree(ctx, p);
+    ctx->d_filt = nullptr;
+  };
+  if ((rc = dalloc(ctx, mat, &dS)) || (rc = dalloc(ctx, mat, &dH)) || (rc = dalloc(ctx, mat, &dC)) ||
+      (rc = dalloc_t(ctx, (size_t)max_units, &dlam)) || (rc = dalloc_t(ctx, 3 * (size_t)ctx->n_units, &dfa)) ||
+      (rc = dalloc_t(ctx, 3 * (size_t)ctx->n_units, &dfb)) || (rc = dalloc_t(ctx, 3 * (size_t)ctx->n_units, &dfc)) ||
+      (rc = dalloc_t(ctx, 1, &dbad))) {
+    cleanup();
+    return rc;
+  }
+  CK(cudaMemsetAsync(dbad, 0, sizeof(int), ctx->stream));
+  // h times the block in `out`: filter coefficients (1, 0, 0)
+  std::vector<double> ones(3 * ctx->n_units, 0.0);
+  for (long long u = 0; u < ctx->n_units; ++u) ones[3 * u] = 1.0;
+  CK(cudaMemcpyAsync(dfc, ones.data(), sizeof(double) * ones.size(), cudaMemcpyHostToDevice, ctx->stream));
+  auto apply = [&](HostCell& hc, const double* filt, void* in, void* out, void* prev) {
+    ctx->d_filt = filt;
+    LaunchSet L = make_set(ctx, hc);
+    launch_bra<double>(L, in, ctx->P, 0, 0, ctx->stream);
+    launch_stage<double>(L, in, out, prev, ctx->P, 0, ctx->stream);
+    ctx->launches += 2;
+  };
+  // Rayleigh-Ritz bound and orthonormalisation of the block in `y` (h y into `hy`)
+  std::vector<double> lam_u(ctx->n_units, 0.0);
+  auto orthonormalise = [&](void* y, void* hy) -> int {
+    for (auto& hc : ctx->cells) {
+      if (hc.unit_ids.empty()) continue;
+      apply(hc, dfc, y, hy, nullptr);
+      LaunchSet L = make_set(ctx, hc);
+      launch_scf_gram(L, y, hy, dS, dH, ctx->stream);
+      launch_scf_ortho(L.n_units, hc.dev.n_bands, dS, dH, dC, dlam, dbad, ctx->stream);
+      launch_scf_rotate(L, y, dC, ctx->stream);
+      ctx->launches += 3;
+      std::vector<double> lam(L.n_units);
+      CK(cudaMemcpyAsync(lam.data(), dlam, sizeof(double) * lam.size(), cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+      for (size_t i = 0; i < lam.size(); ++i) lam_u[hc.unit_ids[i]] = lam[i];
+    }
+    return TSBZ_OK;
+  };
+  // upper bound of the spectrum of h_k (A = 0) per unit: FD kinetic with the
+  // q terms, the largest v_eff of the sub-simulation, and sum_j |E_j|
+  auto upper_bound = [&](std::vector<double>& ub) -> int {
+    ub.assign(ctx->n_units, 0.0);
+    std::vector<double> kc(3 * ctx->n_units);
+    CK(cudaMemcpyAsync(kc.data(), ctx->kcart, sizeof(double) * kc.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    std::vector<std::vector<double>> vmax_sub(ns);
+    for (size_t s = 0; s < ns; ++s) {
+      const HostSub& hs = ctx->subs[s];
+      const CellDev& c = ctx->cells[hs.cell].dev;
+      std::vector<double> v(c.npts);
+      CK(cudaMemcpyAsync(v.data(), hs.veff, sizeof(double) * c.npts, cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+      double vm = v[0];
+      for (double x : v) vm = std::max(vm, x);
+      vmax_sub[s] = {vm};
+    }
+    for (size_t s = 0; s < ns; ++s) {
+      const HostSub& hs = ctx->subs[s];
+      const HostCell& hc = ctx->cells[hs.cell];
+      const CellDev& c = hc.dev;
+      double enl = 0.0;
+      if (c.use_proj) enl = c.n_atoms * (std::fabs(hc.desc.e_kb_s) + 3.0 * std::fabs(hc.desc.e_kb_p));
+      for (int k = 0; k < hs.n_k; ++k) {
+        const long long u = hs.unit0 + k;
+        double kin = 0.0, q2 = 0.0;
+        for (int ax = 0; ax < 3; ++ax) {
+          double lap = -c.lapw[ax][0], grd = 0.0;
+          for (int m = 1; m <= c.nd; ++m) {
+            lap += 2.0 * std::fabs(c.lapw[ax][m]);
+            grd += 2.0 * std::fabs(c.gradw[ax][m]);
+          }
+          const double q = kc[3 * u + ax];
+          kin += 0.5 * lap + std::fabs(q) * grd;
+          q2 += q * q;
+        }
+        ub[u] = 1.02 * (kin + 0.5 * q2 + vmax_sub[s][0] + enl) + 0.1;
+      }
+    }
+    return TSBZ_OK;
+  };
+  // density mixing (Pulay, as the reference solver), per sub-simulation
+  struct Mix {
+    std::vector<std::vector<double>> rin, res;
+  };
+  std::vector<Mix> mixes(ns);
+  std::vector<std::vector<double>> rho_in(ns);
+  for (size_t s = 0; s < ns; ++s) {
+    const HostSub& hs = ctx->subs[s];
+    const HostCell& hc = ctx->cells[hs.cell];
+    const double ne = hc.desc.occ * hc.desc.n_bands;
+    rho_in[s].assign(hc.dev.npts, ne / hc.dev.omega);
+    CK(cudaMemcpyAsync(hs.rho, rho_in[s].data(), sizeof(double) * hc.dev.npts, cudaMemcpyHostToDevice,
+                       ctx->stream));
+  }
+  run_hxc<double>(ctx);
+  run_field<double>(ctx, TSBZ_FIELD_J0MINUS);
+  if ((rc = orthonormalise(ctx->psi, ctx->tA))) {
+    cleanup();
+    return rc;
+  }
+  double err = 1e300;
+  int it = 0;
+  std::vector<double> ub, fa(3 * ctx->n_units), fb(3 * ctx->n_units);
+  for (it = 1; it <= max_iter; ++it) {
+    if ((rc = upper_bound(ub))) break;
+    for (long long u = 0; u < ctx->n_units; ++u) {
+      // the filter damps [a, b]: a a little above the block's largest Ritz value,
+      // so that the top occupied state is amplified against the first empty one
+      const double a = lam_u[u] + 0.1, b = std::max(ub[u], a + 1.0);
+      const double e = 0.5 * (b - a), cc = 0.5 * (b + a);
+      fa[3 * u] = 1.0 / e;
+      fa[3 * u + 1] = -cc / e;
+      fa[3 * u + 2] = 0.0;
+      fb[3 * u] = 2.0 / e;
+      fb[3 * u + 1] = -2.0 * cc / e;
+      fb[3 * u + 2] = -1.0;
+    }
+    CK(cudaMemcpyAsync(dfa, fa.data(), sizeof(double) * fa.size(), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(dfb, fb.data(), sizeof(double) * fb.size(), cudaMemcpyHostToDevice, ctx->stream));
+    // Chebyshev filter of the block: Y_1 = (h - c)/e Y_0, Y_{j+1} = 2 (h - c)/e Y_j - Y_{j-1}
+    void* buf[3] = {ctx->psi, ctx->tA, ctx->tB};
+    int prev = 0, cur = 1;
+    for (auto& hc : ctx->cells)
+      if (!hc.unit_ids.empty()) apply(hc, dfa, buf[0], buf[1], nullptr);
+    for (int j = 1; j < degree; ++j) {
+      const int next = 3 - prev - cur;
+      for (auto& hc : ctx->cells)
+        if (!hc.unit_ids.empty()) apply(hc, dfb, buf[cur], buf[next], buf[prev]);
+      prev = cur;
+      cur = next;
+    }
+    if ((rc = orthonormalise(buf[cur], buf[3 - prev - cur]))) break;
+    if (buf[cur] != ctx->psi)
+      CK(cudaMemcpyAsync(ctx->psi, buf[cur], ctx->psi_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    // output density, then the mixed input density and its v_Hxc
+    run_observe<double>(ctx, TSBZ_FIN_RHO);
+    err = 0.0;
+    for (size_t s = 0; s < ns; ++s) {
+      HostSub& hs = ctx->subs[s];
+      const HostCell& hc = ctx->cells[hs.cell];
+      const int np = hc.dev.npts;
+      std::vector<double> rout(np);
+      CK(cudaMemcpyAsync(rout.data(), hs.rho, sizeof(double) * np, cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+      const double ne = hc.desc.occ * hc.desc.n_bands;
+      double e = 0.0;
+      for (int r = 0; r < np; ++r) e += std::fabs(rout[r] - rho_in[s][r]);
+      e *= hc.dev.dv / ne;
+      err = std::max(err, e);
+      Mix& mx = mixes[s];
+      std::vector<double> f(np);
+      for (int r = 0; r < np; ++r) f[r] = rout[r] - rho_in[s][r];
+      mx.rin.push_back(rho_in[s]);
+      mx.res.push_back(f);
+      if (mx.rin.size() > 8) {
+        mx.rin.erase(mx.rin.begin());
+        mx.res.erase(mx.res.begin());
+      }
+      const int m = (int)mx.res.size();
+      // bordered system [B 1; 1 0][c; l] = [0; 1], B_ij = <f_i, f_j>
+      std::vector<double> A((m + 1) * (m + 1), 0.0), x(m + 1, 0.0);
+      for (int i = 0; i < m; ++i) {
+        for (int j = 0; j < m; ++j) {
+          double d = 0.0;
+          for (int r = 0; r < np; ++r) d += mx.res[i][r] * mx.res[j][r];
+          A[i * (m + 1) + j] = d;
+        }
+        A[i * (m + 1) + m] = 1.0;
+        A[m * (m + 1) + i] = 1.0;
+      }
+      x[m] = 1.0;
+      // Gaussian elimination with partial pivoting
+      bool solved = true;
+      const int n = m + 1;
+      for (int col = 0; col < n && solved; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < n; ++r)
+          if (std::fabs(A[r * n + col]) > std::fabs(A[piv * n + col])) piv = r;
+        if (std::fabs(A[piv * n + col]) < 1e-300) {
+          solved = false;
+          break;
+        }
+        if (piv != col) {
+          for (int k2 = 0; k2 < n; ++k2) std::swap(A[col * n + k2], A[piv * n + k2]);
+          std::swap(x[col], x[piv]);
+        }
+        for (int r = col + 1; r < n; ++r) {
+          const double fct = A[r * n + col] / A[col * n + col];
+          for (int k2 = col; k2 < n; ++k2) A[r * n + k2] -= fct * A[col * n + k2];
+          x[r] -= fct * x[col];
+        }
+      }
+      std::vector<double> coef(m, 0.0);
+      if (solved) {
+        for (int r = n - 1; r >= 0; --r) {
+          double t = x[r];
+          for (int k2 = r + 1; k2 < n; ++k2) t -= A[r * n + k2] * x[k2];
+          x[r] = t / A[r * n + r];
+        }
+        for (int i = 0; i < m; ++i) coef[i] = x[i];
+      } else {
+        coef[m - 1] = 1.0;
+      }
+      for (int r = 0; r < np; ++r) {
+        double v = 0.0;
+        for (int i = 0; i < m; ++i) v += coef[i] * (mx.rin[i][r] + mix * mx.res[i][r]);
+        rho_in[s][r] = std::max(v, 0.0);
+      }
+      CK(cudaMemcpyAsync(hs.rho, rho_in[s].data(), sizeof(double) * np, cudaMemcpyHostToDevice, ctx->stream));
+    }
+    if (err < tol) break;
+    run_hxc<double>(ctx);
+  }
+  int bad = 0;
+  CK(cudaMemcpyAsync(&bad, dbad, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  cleanup();
+  if (rc) return rc;
+  // the orbitals are the new ground state: rho, v_Hxc, J(0-) and J(0+) follow from them
+  for (auto& hs : ctx->subs) {
+    hs.need_init = true;
+    hs.need_j0plus = true;
+  }
+  ctx->p_next_valid = false;
+  drop_step_graph(ctx);
+  if (iters_out) *iters_out = std::min(it, max_iter);
+  if (err_out) *err_out = err;
+  if (bad) return set_err(ctx, TSBZ_ENONFINITE, "the block lost rank (overlap matrix not positive definite)");
+  if ((rc = ensure_ready(ctx))) return rc;
+  if ((rc = sync_and_check(ctx))) return rc;
+  return err < tol ? TSBZ_OK : set_err(ctx, TSBZ_ESTATE, "ground state not converged within max_iter");
 }
 
 int tsbz_set_propagator(tsbz_ctx* ctx, int propagator) {

@@ -121,6 +121,7 @@ struct LaunchSet {
   void* qt_half;          // [unit][4] in T: q_x, q_y, q_z, |q|^2 / 2 at t_n + dt/2
   int variant;            // kernel variant of this cell (0 = default; chosen by the autotuner)
   double dt_scale;        // the stage kernels advance by dt * dt_scale (1, or 1/2 in the ETRS half steps)
+  const double* filt;     // [unit][3] filter coefficients of the ground-state solver (stage m = 0), or null
 };
 
 #ifdef __CUDACC__
@@ -159,6 +160,13 @@ bool launch_observe_zf(const LaunchSet& L, const void* psi, double* rho_part, do
                        void* stream);
 void launch_stage_v(const LaunchSet& L, const void* tin, void* tout, void* psi, const void* V, int m, void* stream);
 // single-precision fused stage and projections (cells with at most 8 atoms, depth 8 or 16, n1 n2 <= 256)
+// Ground-state solver (tsbz_scf.cu).
+int scf_max_bands();
+void launch_scf_gram(const LaunchSet& L, const void* Y, const void* HY, void* S, void* H, void* stream);
+void launch_scf_ortho(int n_units, int nb, const void* S, const void* H, void* C, double* lam, int* bad,
+                      void* stream);
+void launch_scf_rotate(const LaunchSet& L, void* Y, const void* C, void* stream);
+
 bool sep_supported(const CellDev& c);
 int sep_variants(const CellDev& c);   // kernel variants of the single-precision path on this cell
 // The whole time step of every unit in one launch (16^3 cells with z groups,

@@ -285,10 +285,14 @@ __global__ void __launch_bounds__(TSBZ_PT) k_stage(LaunchSet L, const typename C
   const T q2h = qt[3];
   const T v = valid ? reinterpret_cast<const T*>(S.veff)[pp] : (T)0;
   const T diag = q2h + v;
-  const T hdt = (T)(S.dt * L.dt_scale) / (T)m;
+  const T hdt = (T)(S.dt * L.dt_scale) / (T)(m > 0 ? m : 1);
   const V* ph = (const V*)L.ph_half + (long long)u * L.ph_stride;
   const int nm = c.nmax;
   const V zero = cmk<V>((T)0, (T)0);
+  // m = 0: filter step of the ground-state solver, tout = c1 h t + c2 t + c3 prev
+  // with per-unit coefficients L.filt[3 u ..] and prev passed as psi
+  const T fc1 = m == 0 ? (T)L.filt[3 * u] : (T)0, fc2 = m == 0 ? (T)L.filt[3 * u + 1] : (T)0;
+  const T fc3 = m == 0 ? (T)L.filt[3 * u + 2] : (T)0;
   __shared__ T lw[3][TSBZ_MAX_ND + 1], gw[3][TSBZ_MAX_ND + 1];
   if (threadIdx.x < 3 * (TSBZ_MAX_ND + 1)) {
     const int ax = threadIdx.x / (TSBZ_MAX_ND + 1), mm = threadIdx.x % (TSBZ_MAX_ND + 1);
@@ -368,6 +372,15 @@ __global__ void __launch_bounds__(TSBZ_PT) k_stage(LaunchSet L, const typename C
       h.x += qg.y;
       h.y -= qg.x;
       h = cadd(h, ket[bl]);
+      if (m == 0) {
+        V o = cmk<V>(fc1 * h.x + fc2 * ce.x, fc1 * h.y + fc2 * ce.y);
+        if (fc3 != (T)0) {
+          const V pv = psi[base + pp];
+          o = cmk<V>(o.x + fc3 * pv.x, o.y + fc3 * pv.y);
+        }
+        tout[base + pp] = o;
+        continue;
+      }
       // t_m = (-i dt/m) h
       const V t = cmk<V>(hdt * h.y, -hdt * h.x);
       if (m < 4) tout[base + pp] = t;

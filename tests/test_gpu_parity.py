@@ -185,6 +185,36 @@ def test_parity_config1_fp64(config1_ground_state):
     assert np.max(np.abs(dj[:, 1:])) < 1e-6 * np.max(np.abs(dj[:, 0]))
 
 
+def test_gpu_ground_state_config1(config1_ground_state):
+    """The GPU ground-state solver on the config-1 k-set (cell A, 16^3, MP 2^3,
+    16 bands) from plane-wave starting orbitals: its density matches the oracle's
+    SCF (both converged to dV sum |rho_out - rho_in| / N_e <= 1e-8), and so does the
+    kicked current propagated from each ground state."""
+    import time
+    from paper_2112_00920_gb300 import Propagator, shifted_kpoints
+    sub, gs = config1_ground_state
+    cell = sub.cell
+    start = W.plane_wave_orbitals(cell.a, cell.n, W.plane_wave_set(cell.n_bands), 8)
+    P = Propagator("fp64")
+    cid = P.add_cell_spec(cell)
+    sid = P.add_subsim(cid, shifted_kpoints(cell.a, sub.mp, sub.shift), sub.dt, 10)
+    P.load_ground_state(sid, start)
+    t0 = time.perf_counter()
+    iters, err = P.ground_state(max_iter=80, tol=1e-8)
+    print(f"GPU SCF config 1: {iters} iterations, error {err:.2e}, {time.perf_counter() - t0:.2f} s")
+    rel = np.max(np.abs(P.density(sid) - gs["rho"])) / np.max(gs["rho"])
+    assert rel <= 1e-6, rel
+    P.set_kick(sid, sub.field.k0, sub.field.direction)
+    P.propagate(10)
+    J, j0 = P.current(sid)
+    P.close()
+    o = oracle_run(cell, dict(mp=sub.mp, shift=sub.shift, psi=gs["u"], dt=sub.dt, n_steps=10, field=sub.field))
+    dj, djo = J - j0[None, :], o["J"] - o["J0_minus"][None, :]
+    e = float(np.max(np.abs(dj - djo)) / np.max(np.abs(djo)))
+    print("density", rel, "dJ", e)
+    assert e <= 1e-5, e
+
+
 def test_parity_config1_fp32(config1_ground_state):
     """FP32 stencil/Taylor/projectors with FP64 rho/J: errors stay at float
     rounding (~1e-7 per step on each orbital, accumulated over 20 steps)."""
