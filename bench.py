@@ -38,7 +38,7 @@ import numpy as np  # noqa: E402
 
 METRIC = "orbital-steps/s (k·band·Δt), FP32/TC batched vs FP64 GPU; ε(ω) rel err vs oracle"
 UNIT = "orbital-steps/s"
-WORKLOAD = "two-step 64x4^3 shifted MP, Si-like 8-atom cubic cell, 16^3 grid, 16 bands (config 2 step)"
+WORKLOAD = "two-step 64x4^3 shifted MP, Si-like 8-atom cubic cell, 16^3 grid, 16 bands (one time step)"
 
 
 # ----------------------------------------------------------------------------
@@ -48,7 +48,7 @@ def _oracle_job(args):
     m, n_steps = args
     import workloads as W
     from oracle import dynamics
-    run = W.config2(n_steps=n_steps)
+    run = W.twostep_kick_run(n_steps=n_steps)
     sub = run.subsims[m]
     cell = sub.cell
     psi = W.plane_wave_orbitals(cell.a, cell.n, W.plane_wave_set(cell.n_bands), sub.mp[0] * sub.mp[1] * sub.mp[2])
@@ -215,7 +215,7 @@ def device_uuid(index: int) -> str | None:
 def build_propagator(precision, n_steps_cap, device=0, n_subsims=64):
     import workloads as W
     from paper_2112_00920_gb300 import Propagator, shifted_kpoints
-    run = W.config2(n_steps=n_steps_cap)
+    run = W.twostep_kick_run(n_steps=n_steps_cap)
     run.subsims = run.subsims[:n_subsims]
     cell = run.subsims[0].cell
     P = Propagator(precision, device=device)

@@ -30,7 +30,7 @@ def built_library():
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
 def test_hhg_workload_full_size_sampled(precision, tol):
     from paper_2112_00920_gb300 import Propagator, shifted_kpoints
-    run = W.config3(n_steps=2)
+    run = W.twostep_hhg_run(n_steps=2)
     cell = run.subsims[0].cell
     dt, n = run.subsims[0].dt, 2
     pulse = run.subsims[0].field

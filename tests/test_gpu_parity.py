@@ -165,17 +165,17 @@ def test_parity_frozen_fp64():
 
 
 @pytest.fixture(scope="module")
-def config1_ground_state():
-    run = W.config1()
+def mp2_ground_state():
+    run = W.mp2_kick_run()
     sub = run.subsims[0]
     k = kpoints.kpoints_cartesian(sub.cell.a, sub.mp, sub.shift)
     gs = scf.ground_state(sub.cell, k, seed=W.MASTER_SEED, tol=1e-8, eig_tol=1e-8)
     return sub, gs
 
 
-def test_parity_config1_fp64(config1_ground_state):
+def test_parity_mp2_fp64(mp2_ground_state):
     """Cell A, MP 2^3, SCF ground state, kick 0.005 x, dt 0.08 (20 of the 100 steps)."""
-    sub, gs = config1_ground_state
+    sub, gs = mp2_ground_state
     s = dict(mp=sub.mp, shift=sub.shift, psi=gs["u"], dt=sub.dt, n_steps=20, field=sub.field)
     _, g = gpu_run(sub.cell, [s])
     o = oracle_run(sub.cell, s)
@@ -185,14 +185,14 @@ def test_parity_config1_fp64(config1_ground_state):
     assert np.max(np.abs(dj[:, 1:])) < 1e-6 * np.max(np.abs(dj[:, 0]))
 
 
-def test_gpu_ground_state_config1(config1_ground_state):
-    """The GPU ground-state solver on the config-1 k-set (cell A, 16^3, MP 2^3,
+def test_gpu_ground_state_mp2(mp2_ground_state):
+    """The GPU ground-state solver on the MP 2^3 k-set of cell A (16^3,
     16 bands) from plane-wave starting orbitals: its density matches the oracle's
     SCF (both converged to dV sum |rho_out - rho_in| / N_e <= 1e-8), and so does the
     kicked current propagated from each ground state."""
     import time
     from paper_2112_00920_gb300 import Propagator, shifted_kpoints
-    sub, gs = config1_ground_state
+    sub, gs = mp2_ground_state
     cell = sub.cell
     start = W.plane_wave_orbitals(cell.a, cell.n, W.plane_wave_set(cell.n_bands), 8)
     P = Propagator("fp64")
@@ -201,7 +201,7 @@ def test_gpu_ground_state_config1(config1_ground_state):
     P.load_ground_state(sid, start)
     t0 = time.perf_counter()
     iters, err = P.ground_state(max_iter=80, tol=1e-8)
-    print(f"GPU SCF config 1: {iters} iterations, error {err:.2e}, {time.perf_counter() - t0:.2f} s")
+    print(f"GPU SCF, cell A MP 2^3: {iters} iterations, error {err:.2e}, {time.perf_counter() - t0:.2f} s")
     rel = np.max(np.abs(P.density(sid) - gs["rho"])) / np.max(gs["rho"])
     assert rel <= 1e-6, rel
     P.set_kick(sid, sub.field.k0, sub.field.direction)
@@ -215,10 +215,10 @@ def test_gpu_ground_state_config1(config1_ground_state):
     assert e <= 1e-5, e
 
 
-def test_parity_config1_fp32(config1_ground_state):
+def test_parity_mp2_fp32(mp2_ground_state):
     """FP32 stencil/Taylor/projectors with FP64 rho/J: errors stay at float
     rounding (~1e-7 per step on each orbital, accumulated over 20 steps)."""
-    sub, gs = config1_ground_state
+    sub, gs = mp2_ground_state
     s = dict(mp=sub.mp, shift=sub.shift, psi=gs["u"], dt=sub.dt, n_steps=20, field=sub.field)
     _, g = gpu_run(sub.cell, [s], precision="fp32")
     o = oracle_run(sub.cell, s)
@@ -227,12 +227,12 @@ def test_parity_config1_fp32(config1_ground_state):
     e_dj = float(np.max(np.abs(dj_g - dj_o)) / np.max(np.abs(dj_o)))
     errs = compare(g[0], o, 1e-4, 1e-5, 1e-5)
     assert e_dj < 1e-3, e_dj
-    print("fp32 config1:", errs, "err_dJ", e_dj)
+    print("fp32 mp2:", errs, "err_dJ", e_dj)
 
 
-def test_parity_config1_fp32_tc(config1_ground_state):
-    """Tensor-core mode on config 1 (SCF ground state, 20 steps)."""
-    sub, gs = config1_ground_state
+def test_parity_mp2_fp32_tc(mp2_ground_state):
+    """Tensor-core mode on cell A, MP 2^3 (SCF ground state, 20 steps)."""
+    sub, gs = mp2_ground_state
     s = dict(mp=sub.mp, shift=sub.shift, psi=gs["u"], dt=sub.dt, n_steps=20, field=sub.field)
     _, g = gpu_run(sub.cell, [s], precision="fp32_tc")
     o = oracle_run(sub.cell, s)
@@ -241,7 +241,7 @@ def test_parity_config1_fp32_tc(config1_ground_state):
     e_dj = float(np.max(np.abs(dj_g - dj_o)) / np.max(np.abs(dj_o)))
     errs = compare(g[0], o, TC_J_TOL, TC_RHO_TOL, TC_RHO_TOL)
     assert e_dj < 1e-3, e_dj
-    print("fp32_tc config1:", errs, "err_dJ", e_dj)
+    print("fp32_tc mp2:", errs, "err_dJ", e_dj)
 
 
 def test_free_electron_closed_form_gpu():
@@ -350,7 +350,7 @@ def test_full_two_step_workload_sampled(precision):
     (4096 k, 65 536 orbitals), plane-wave start, kick; two steps.  Sub-simulations
     are independent, so sampled ones are checked against the oracle run alone."""
     from paper_2112_00920_gb300 import Propagator, shifted_kpoints
-    run = W.config2(n_steps=2)
+    run = W.twostep_kick_run(n_steps=2)
     cell = run.subsims[0].cell
     gints = W.plane_wave_set(cell.n_bands)
     psi = W.plane_wave_orbitals(cell.a, cell.n, gints, 64)
@@ -380,8 +380,8 @@ def _eps(j, j0, dt, k0, omegas):
 def test_eps_error_vs_oracle():
     """eps(omega) over 0.1-20 eV (Eqs. 12-14) from each GPU path against the
     complex128 oracle: cell A on an 8^3 grid, MP 2^3, SCF ground state,
-    kick 0.005 x, 600 steps of dt = 0.08 (T_W = run length).  North-star
-    bar for the float/tensor-core path: err_eps <= 1e-4."""
+    kick 0.005 x, 600 steps of dt = 0.08 (T_W = run length).  Bar for the
+    single-precision and tensor-core paths: err_eps <= 1e-4."""
     cell = W.cell_a_coarse(n=8)
     k = kpoints.kpoints_cartesian(cell.a, (2, 2, 2), (0.0, 0.0, 0.0))
     gs = scf.ground_state(cell, k, seed=7, tol=1e-10, eig_tol=1e-10)

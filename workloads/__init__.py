@@ -226,30 +226,30 @@ def random_shifts(n: int, seed: int) -> list:
     return [tuple(float(v) for v in row) for row in rng.uniform(0.0, 1.0, size=(n, 3))]
 
 
-def config1(seed: int = MASTER_SEED, n_steps: int = 100) -> RunSpec:
+def mp2_kick_run(seed: int = MASTER_SEED, n_steps: int = 100) -> RunSpec:
     """Plain FP64 run: cell A, MP 2^3 (8 k), 16 bands, kick k0=0.005 x,
     dt=0.08, 100 steps."""
     c = cell_a(seed)
-    return RunSpec("config1-mp2-kick", [SubsimSpec(c, (2, 2, 2), (0.0, 0.0, 0.0), 0.08, n_steps, Kick())])
+    return RunSpec("mp2-kick", [SubsimSpec(c, (2, 2, 2), (0.0, 0.0, 0.0), 0.08, n_steps, Kick())])
 
 
-def config2(seed: int = MASTER_SEED, n_steps: int = 3000, hxc: str = "scf") -> RunSpec:
+def twostep_kick_run(seed: int = MASTER_SEED, n_steps: int = 3000, hxc: str = "scf") -> RunSpec:
     """Two-step linear response: the 16^3 k grid split into 64 shifted 4^3
     subgrids (4096 k), 16 bands, kick 0.005 x, dt=0.08, 3000 steps."""
     c = cell_a(seed)
     subs = [SubsimSpec(c, (4, 4, 4), s, 0.08, n_steps, Kick()) for s in lattice_shifts(4)]
-    return RunSpec("config2-twostep-64x4^3-kick", subs, hxc=hxc, shift_scheme="lattice")
+    return RunSpec("twostep-64x4^3-kick", subs, hxc=hxc, shift_scheme="lattice")
 
 
-def config3(seed: int = MASTER_SEED, n_steps: int = 41350) -> RunSpec:
+def twostep_hhg_run(seed: int = MASTER_SEED, n_steps: int = 41350) -> RunSpec:
     """Two-step HHG: 8 shifted 8^3 subgrids, sin^4 pulse along z,
     omega0=0.057, E0=0.005, T=1654, dt=0.04."""
     c = cell_a(seed)
     subs = [SubsimSpec(c, (8, 8, 8), s, 0.04, n_steps, Pulse()) for s in lattice_shifts(2)]
-    return RunSpec("config3-twostep-8x8^3-hhg", subs, shift_scheme="lattice")
+    return RunSpec("twostep-8x8^3-hhg", subs, shift_scheme="lattice")
 
 
-def config5(seed: int = MASTER_SEED, n_a: int = 180, n_b: int = 20, max_steps: int | None = None) -> RunSpec:
+def uneven_batch_run(seed: int = MASTER_SEED, n_a: int = 180, n_b: int = 20, max_steps: int | None = None) -> RunSpec:
     """Uneven batch: n_a cell-A and n_b cell-B sub-simulations with seeded
     subgrid sizes 2..6, random shifts, kick amplitudes log-uniform in
     [1e-4, 1e-2] along x and 500..5000 steps."""
@@ -268,7 +268,7 @@ def config5(seed: int = MASTER_SEED, n_a: int = 180, n_b: int = 20, max_steps: i
             steps = min(steps, max_steps)
         subs.append(SubsimSpec(ca if kind == "A" else cb, (nk, nk, nk), shifts[idx], 0.08, steps,
                                Kick(k0=k0)))
-    return RunSpec("config5-uneven", subs, shift_scheme="random")
+    return RunSpec("uneven-batch", subs, shift_scheme="random")
 
 
 def scf_start_vectors(n_k: int, n_vec: int, n_pts: int, seed: int, tag: int = 0) -> np.ndarray:
