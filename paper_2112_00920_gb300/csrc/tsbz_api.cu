@@ -977,6 +977,44 @@ int tsbz_init_cell(tsbz_ctx* ctx, const tsbz_cell_desc* d, int* cell_id) {
   c.d1f = ddf;
   c.pnormf = pnff;
   c.wkbf = wkff;
+  // projector boxes from the double Gaussian tables: the smallest periodic index
+  // range of each atom and axis that holds every nonzero factor
+  c.pbox = nullptr;
+  c.pbox_ok = 0;
+  if (c.use_proj) {
+    std::vector<int> box(6 * (size_t)d->n_atoms, 0);
+    bool ok = true;
+    const int nn[3] = {c.n1, c.n2, c.n3};
+    for (int a = 0; a < d->n_atoms; ++a)
+      for (int ax = 0; ax < 3; ++ax) {
+        const int n = nn[ax];
+        const double* gr = g1.data() + ((size_t)a * 3 + ax) * c.nmax;
+        int cnt = 0;
+        for (int i = 0; i < n; ++i) cnt += gr[i] != 0.0;
+        int start = 0, len = n;
+        if (cnt > 0 && cnt < n) {
+          // a start after which cnt consecutive (periodic) entries hold every nonzero
+          for (int s0 = 0; s0 < n; ++s0) {
+            if (gr[s0] == 0.0 || gr[(s0 + n - 1) % n] != 0.0) continue;
+            int inside = 0;
+            for (int j = 0; j < cnt; ++j) inside += gr[(s0 + j) % n] != 0.0;
+            if (inside == cnt) {
+              start = s0;
+              len = cnt;
+              break;
+            }
+          }
+        }
+        box[(a * 3 + ax) * 2] = start;
+        box[(a * 3 + ax) * 2 + 1] = len;
+        if (ax < 2 && len > 16) ok = false;
+      }
+    int* db = nullptr;
+    if ((rc = dalloc_t(ctx, box.size(), &db))) return rc;
+    CK(cudaMemcpy(db, box.data(), sizeof(int) * box.size(), cudaMemcpyHostToDevice));
+    c.pbox = db;
+    c.pbox_ok = ok ? 1 : 0;
+  }
   // z groups: atoms with bit-identical z rows of the float factor tables
   c.n_zg = 0;
   for (int i = 0; i < 8; ++i) c.zg_of[i] = c.zg_rep[i] = c.zg_mem[i] = 0;

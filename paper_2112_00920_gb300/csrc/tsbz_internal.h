@@ -49,6 +49,11 @@ struct CellDev {
   // Gaussian, displacement and phase rows for every q) form one z group; the
   // z contractions of the 16^3 fused stage run once per group (cells of at
   // most 8 atoms; n_zg = 0 otherwise)
+  // projector boxes: per atom and axis the periodic index range [start, start + len)
+  // outside which the Gaussian factor is zero ([n_atoms][3][2] ints), and whether
+  // every box is at most 16 x 16 points in x and y (the box-factorised projection)
+  const int* pbox;
+  int pbox_ok;
   int n_zg;
   int zg_of[8];       // group of atom a
   int zg_rep[8];      // first atom of group g

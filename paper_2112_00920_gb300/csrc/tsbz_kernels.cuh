@@ -254,6 +254,99 @@ __global__ void __launch_bounds__(256) k_bra(LaunchSet L, const typename Cplx<T>
 }
 
 // ----------------------------------------------------------------------------
+// bra on the projector boxes: the same P as k_bra, from the factorisation
+// C_row(r) = pn_t F^a_x(ix) F^a_y(iy) F^a_z(iz) d_x^i d_y^j d_z^k (F = g e^{i q d})
+// restricted to the atom's box (the Gaussian factor is zero outside it).  One CTA
+// per (atom, unit, band block), one thread per (x, y) column of the box (at most
+// 16 x 16): the column sums Z_k = sum_z F_z d_z^k t (k <= 1, or <= 2 for the
+// current), then the x and y weights, then a fixed-order CTA reduction.
+//   NW = 1: rows 4 a + t (t = s, p_x, p_y, p_z);  NW = 4: rows 4 (4 a + t) + alpha.
+// ----------------------------------------------------------------------------
+#define BRA_BOX_BANDS 8   // bands per CTA of k_bra_box
+
+template <typename T, int NW>
+__global__ void __launch_bounds__(256) k_bra_box(LaunchSet L, const typename Cplx<T>::type* __restrict__ src,
+                                                 typename Cplx<T>::type* __restrict__ P, int use_obs) {
+  using V = typename Cplx<T>::type;
+  constexpr int NR = 4 * NW;            // rows of the atom
+  constexpr int KD = NW == 1 ? 2 : 3;   // powers of d_z kept in the column sums
+  __shared__ V red[8][NR];
+  const CellDev& c = L.cell;
+  const int a = blockIdx.x;
+  const int u = L.unit_ids[blockIdx.y];
+  if (!unit_active(L, u)) return;
+  const UnitDev U = L.units[u];
+  const int* bx = c.pbox + a * 6;
+  const int sx = bx[0], lx = bx[1], sy = bx[2], ly = bx[3], sz = bx[4], lz = bx[5];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const bool live = t < lx * ly;
+  const int ix = (sx + (live ? t % lx : 0)) % c.n1, iy = (sy + (live ? t / lx : 0)) % c.n2;
+  const int nm = c.nmax, n12 = c.n1 * c.n2;
+  const V* ph = (const V*)(use_obs ? L.ph_obs : L.ph_half) + (long long)u * L.ph_stride + (long long)a * 3 * nm;
+  const T* ga = Tab<T>::g1(c) + (long long)a * 3 * nm;
+  const T* da = Tab<T>::d1(c) + (long long)a * 3 * nm;
+  const T* pn = Tab<T>::pnorm(c) + 4 * a;
+  // column weights F_x F_y and the displacements of the column
+  const V fxy = cscale(cmul(ph[ix], ph[nm + iy]), ga[ix] * ga[nm + iy]);
+  const T dx = da[ix], dy = da[nm + iy];
+  const int rows = c.n_proj * NW;
+  const long long off = (NW == 1) ? U.p_off : U.pa_off;
+  const int b_end = min(c.n_bands, (int)(blockIdx.z + 1) * BRA_BOX_BANDS);
+  for (int b = blockIdx.z * BRA_BOX_BANDS; b < b_end; ++b) {
+    const V* tb = src + U.psi_off + (long long)b * c.npts + iy * c.n1 + ix;
+    V z[KD];
+#pragma unroll
+    for (int k = 0; k < KD; ++k) z[k] = cmk<V>((T)0, (T)0);
+    if (live) {
+      for (int kz = 0; kz < lz; ++kz) {
+        const int iz = (sz + kz) % c.n3;
+        const V fz = cscale(ph[2 * nm + iz], ga[2 * nm + iz]);
+        const T dz = da[2 * nm + iz];
+        V w = cmul(fz, tb[(long long)iz * n12]);
+        z[0] = cadd(z[0], w);
+        w = cscale(w, dz);
+        z[1] = cadd(z[1], w);
+        if (KD > 2) z[KD - 1] = cadd(z[KD - 1], cscale(w, dz));
+      }
+    }
+    // row values of this column: monomial d_x^i d_y^j d_z^k with the column sums
+    V v[NR];
+#pragma unroll
+    for (int tt = 0; tt < 4; ++tt) {
+      const int ti = tt == 1, tj = tt == 2, tk = tt == 3;
+#pragma unroll
+      for (int al = 0; al < NW; ++al) {
+        const int i = ti + (NW == 4 && al == 1), j = tj + (NW == 4 && al == 2), k = tk + (NW == 4 && al == 3);
+        T wxy = (T)1;
+        if (i >= 1) wxy *= dx;
+        if (i >= 2) wxy *= dx;
+        if (j >= 1) wxy *= dy;
+        if (j >= 2) wxy *= dy;
+        v[tt * NW + al] = live ? cscale(cmul(fxy, z[k < KD ? k : KD - 1]), wxy) : cmk<V>((T)0, (T)0);
+      }
+    }
+    // fixed-order reduction over the columns: warp shuffles, then warps in order
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+      for (int o = 16; o > 0; o >>= 1) {
+        v[r].x += __shfl_xor_sync(0xffffffffu, v[r].x, o);
+        v[r].y += __shfl_xor_sync(0xffffffffu, v[r].y, o);
+      }
+    if (lane == 0)
+#pragma unroll
+      for (int r = 0; r < NR; ++r) red[warp][r] = v[r];
+    __syncthreads();
+    if (t < NR) {
+      V sum = cmk<V>((T)0, (T)0);
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum = cadd(sum, red[w][t]);
+      const int tt = t / NW;
+      P[off + (long long)b * rows + a * NR + t] = cscale(sum, (T)c.dv * pn[tt]);
+    }
+    __syncthreads();
+  }
+}
+
+// ----------------------------------------------------------------------------
 // stage m of the Taylor recurrence for all bands of one unit and TSBZ_PT points
 //   t_m = (-i dt/m) [ -1/2 lap t - i q.grad t + (|q|^2/2 + v_eff) t + V_NL t ]
 //   m = 1: write t_1                      m = 2: write t_2, psi += t_1 + t_2
@@ -319,6 +412,7 @@ __global__ void __launch_bounds__(TSBZ_PT) k_stage(LaunchSet L, const typename C
         const T* ga = Tab<T>::g1(c) + (long long)a * 3 * nm;
         const T* da = Tab<T>::d1(c) + (long long)a * 3 * nm;
         const T g = ga[ix] * ga[nm + iy] * ga[2 * nm + iz];
+        if (g == (T)0) continue;   // outside the atom's projector box the factor is exactly zero
         const T dx = da[ix], dy = da[nm + iy], dz = da[2 * nm + iz];
         const V* pa = ph + (long long)a * 3 * nm;
         const V fph = cmul(cmul(pa[ix], pa[nm + iy]), pa[2 * nm + iz]);
@@ -1011,6 +1105,15 @@ template <typename T>
 void launch_bra(const LaunchSet& L, const void* src, void* P, int with_d, int use_obs, void* stream) {
   using V = typename Cplx<T>::type;
   if (L.n_units == 0 || !L.cell.use_proj) return;
+  if (L.cell.pbox_ok) {
+    // projector boxes of at most 16 x 16 columns: the factorised bra on the boxes
+    dim3 gb(L.cell.n_atoms, L.n_units, (L.cell.n_bands + BRA_BOX_BANDS - 1) / BRA_BOX_BANDS);
+    if (with_d)
+      k_bra_box<T, 4><<<gb, 256, 0, (cudaStream_t)stream>>>(L, (const V*)src, (V*)P, use_obs);
+    else
+      k_bra_box<T, 1><<<gb, 256, 0, (cudaStream_t)stream>>>(L, (const V*)src, (V*)P, use_obs);
+    return;
+  }
   const int rows = L.cell.n_proj * (with_d ? 4 : 1);
   dim3 grid((rows + 31) / 32, (L.cell.n_bands + 15) / 16, L.n_units);
   if (with_d)
