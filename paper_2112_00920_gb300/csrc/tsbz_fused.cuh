@@ -778,21 +778,35 @@ __global__ void __launch_bounds__(FS_NP, 2) k_bra_fused(LaunchSet L, const float
 }
 
 // ----------------------------------------------------------------------------
-// Observation pass on 16^3 grids: one CTA per unit, bands in turn, each band
-// brought into shared memory by a bulk copy two bands ahead (double buffer).
+// Observation pass on 16^3 grids: one CTA per unit, bands in turn through a
+// ring of FO_SLOTS band buffers filled by bulk copies.  A slot's "full"
+// mbarrier completes when its band has landed, its "empty" mbarrier when all
+// warps are done with it; thread 0 refills a slot once it is empty, so warps
+// never meet at a CTA barrier between bands.
 // Per column and plane it accumulates occ sum_b |u|^2 (rho; over bands as an
 // unevaluated float pair s + e updated by the error-free two-sum, which keeps
 // the sum to about 2^-44 relative, i.e. FP64-grade, without FP64 arithmetic),
 // per thread sum Re(u* (-i grad u)) (FP32 within a band, FP64 over bands) and
-// per band sum |u|^2 (CTA sum in a fixed order).  The unit's sums go to point
-// tile 0 of the partial buffers and zeros to the other tiles.
+// per band sum |u|^2 (per-warp partials, added over warps in order at the
+// end).  The unit's sums go to point tile 0 of the partial buffers and zeros to
+// the other tiles.
 // ----------------------------------------------------------------------------
+#define FO_SLOTS 3
+#define FO_MAXB 128   // bands of the per-warp norm table
+
 struct FoSmem {
-  float2 buf[2][FS_NPTS];
-  float red[8];
+  float2 buf[FO_SLOTS][FS_NPTS];
+  float nrm[8][FO_MAXB];
   double redj[8][3];
-  unsigned long long mbar[2];
+  unsigned long long full[FO_SLOTS];
+  unsigned long long empty[FO_SLOTS];
+  int fail;
 };
+
+// One arrival of the calling thread on a shared-memory mbarrier.
+__device__ __forceinline__ void fo_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
+}
 
 __global__ void __launch_bounds__(FS_NP, 2) k_observe_fused(LaunchSet L, const float2* __restrict__ psi,
                                                             double* __restrict__ rho_part,
@@ -807,34 +821,35 @@ __global__ void __launch_bounds__(FS_NP, 2) k_observe_fused(LaunchSet L, const f
   const UnitDev U = L.units[u];
   const SubDev S = L.subs[U.sub];
   const int tid = threadIdx.x, col = tid, lane = tid & 31, warp = tid >> 5;
+  const int n_warps = (int)(blockDim.x >> 5);
   const int ix = col & (N - 1), iy = col / N;
   const int nb = c.n_bands;
   const float2* src = psi + U.psi_off;
-  const uint32_t bar0 = bk_smem(&sm.mbar[0]), bar1 = bk_smem(&sm.mbar[1]);
+  volatile int* fail = &sm.fail;
   if (tid == 0) {
-    bk_mbar_init(bar0, 1);
-    bk_mbar_init(bar1, 1);
+    for (int k = 0; k < FO_SLOTS; ++k) {
+      bk_mbar_init(bk_smem(&sm.full[k]), 1);
+      bk_mbar_init(bk_smem(&sm.empty[k]), (uint32_t)n_warps);
+    }
+    *fail = 0;
   }
   __syncthreads();
-  if (tid == 0) {
-    for (int k = 0; k < 2 && k < nb; ++k) {
-      const uint32_t bar = k ? bar1 : bar0;
-      bk_mbar_expect_tx(bar, FS_NPTS * (uint32_t)sizeof(float2));
-      bk_copy_g2s(bk_smem(sm.buf[k]), src + (long long)k * FS_NPTS, FS_NPTS * sizeof(float2), bar);
+  if (tid == 0)
+    for (int k = 0; k < FO_SLOTS && k < nb; ++k) {
+      bk_mbar_expect_tx(bk_smem(&sm.full[k]), FS_NPTS * (uint32_t)sizeof(float2));
+      bk_copy_g2s(bk_smem(sm.buf[k]), src + (long long)k * FS_NPTS, FS_NPTS * sizeof(float2), bk_smem(&sm.full[k]));
     }
-  }
   float rho[N], rho_e[N];
 #pragma unroll
   for (int z = 0; z < N; ++z) rho[z] = rho_e[z] = 0.f;
   double jx = 0.0, jy = 0.0, jz = 0.0;
-  const float2 zero = make_float2(0.f, 0.f);
-  const float2 neg1 = make_float2(-1.f, -1.f);
-  bool ok_all = true;
+  int issued = nb < FO_SLOTS ? nb : FO_SLOTS;   // bands whose copy thread 0 has issued
   for (int b = 0; b < nb; ++b) {
-    const int slot = b & 1;
-    const bool ok = bk_mbar_wait(slot ? bar1 : bar0, (uint32_t)((b >> 1) & 1), BK_WAIT_POLLS);
-    if (!__syncthreads_and(ok)) {
-      ok_all = false;
+    if (*fail) break;
+    const int slot = b % FO_SLOTS;
+    const uint32_t parity = (uint32_t)((b / FO_SLOTS) & 1);
+    if (!bk_mbar_wait(bk_smem(&sm.full[slot]), parity, BK_WAIT_POLLS)) {
+      *fail = 1;
       break;
     }
     const float2* tb = sm.buf[slot];
@@ -883,26 +898,29 @@ __global__ void __launch_bounds__(FS_NP, 2) k_observe_fused(LaunchSet L, const f
     jy += by;
     jz += bz;
     for (int off = 16; off > 0; off >>= 1) nbs += __shfl_xor_sync(0xffffffffu, nbs, off);
-    if (lane == 0) sm.red[warp] = nbs;
-    __syncthreads();   // band values read by every thread; norm partials in place
-    if (tid == 0) {
-      double sum = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += (double)sm.red[w];
-      nrm_part[U.nrm_off + b] = sum;
-      if (b + 2 < nb) {
-        // the buffer of band b is free: bring band b + 2 into it
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        const uint32_t bar = slot ? bar1 : bar0;
-        bk_mbar_expect_tx(bar, FS_NPTS * (uint32_t)sizeof(float2));
-        bk_copy_g2s(bk_smem(sm.buf[slot]), src + (long long)(b + 2) * FS_NPTS, FS_NPTS * sizeof(float2), bar);
+    if (lane == 0) {
+      sm.nrm[warp][b] = nbs;
+      fo_arrive(bk_smem(&sm.empty[slot]));   // the warp is done with this slot (reads ordered by the shuffles)
+    }
+    if (tid == 0 && b + FO_SLOTS < nb) {
+      // refill the slot with band b + FO_SLOTS once every warp is done with it
+      if (!bk_mbar_wait(bk_smem(&sm.empty[slot]), parity, BK_WAIT_POLLS)) {
+        *fail = 1;
+        break;
       }
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      bk_mbar_expect_tx(bk_smem(&sm.full[slot]), FS_NPTS * (uint32_t)sizeof(float2));
+      bk_copy_g2s(bk_smem(sm.buf[slot]), src + (long long)(b + FO_SLOTS) * FS_NPTS, FS_NPTS * sizeof(float2),
+                  bk_smem(&sm.full[slot]));
+      issued = b + FO_SLOTS + 1;
     }
   }
-  if (!ok_all) {
+  if (__syncthreads_or(*fail)) {
     if (tid == 0) {
       atomicOr(S.status, BK_STATUS_TIMEOUT);
-      bk_mbar_wait(bar0, 0, BK_WAIT_POLLS);
-      bk_mbar_wait(bar1, 0, BK_WAIT_POLLS);
+      // let every issued copy land before the CTA's shared memory is released
+      for (int k = (issued > FO_SLOTS ? issued - FO_SLOTS : 0); k < issued; ++k)
+        bk_mbar_wait(bk_smem(&sm.full[k % FO_SLOTS]), (uint32_t)((k / FO_SLOTS) & 1), BK_WAIT_POLLS);
     }
     return;
   }
@@ -921,8 +939,13 @@ __global__ void __launch_bounds__(FS_NP, 2) k_observe_fused(LaunchSet L, const f
   __syncthreads();
   if (tid < 3) {
     double sum = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += sm.redj[w][tid];
+    for (int w = 0; w < n_warps; ++w) sum += sm.redj[w][tid];
     jk_part[U.jk_off + tid] = sum;
+  }
+  for (int b = tid; b < nb; b += blockDim.x) {
+    double sum = 0.0;
+    for (int w = 0; w < n_warps; ++w) sum += (double)sm.nrm[w][b];
+    nrm_part[U.nrm_off + b] = sum;
   }
   for (int i = tid; i < 3 * (c.n_tiles - 1); i += blockDim.x) jk_part[U.jk_off + 3 + i] = 0.0;
   for (int i = tid; i < c.n_bands * (c.n_tiles - 1); i += blockDim.x) nrm_part[U.nrm_off + c.n_bands + i] = 0.0;

@@ -154,7 +154,7 @@ bool launch_step_fused(const LaunchSet& L, void* psi, void* P, void* Pa, int sam
 bool launch_observe_fused(const LaunchSet& L, const void* psi, double* rho_part, double* jk_part, double* nrm_part,
                           void* stream) {
   const CellDev& c = L.cell;
-  if (L.n_units == 0 || c.n1 != 16 || c.n2 != 16 || c.n3 != 16) return false;
+  if (L.n_units == 0 || c.n1 != 16 || c.n2 != 16 || c.n3 != 16 || c.n_bands > FO_MAXB) return false;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_observe_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(FoSmem));
