@@ -786,7 +786,8 @@ __global__ void __launch_bounds__(FS_NP, 2) k_bra_fused(LaunchSet L, const float
 // Per column and plane it accumulates occ sum_b |u|^2 (rho; over bands as an
 // unevaluated float pair s + e updated by the error-free two-sum, which keeps
 // the sum to about 2^-44 relative, i.e. FP64-grade, without FP64 arithmetic),
-// per thread sum Re(u* (-i grad u)) (FP32 within a band, FP64 over bands) and
+// per thread sum Re(u* (-i grad u)) (FP32 within a band; over bands again as a
+// two-sum float pair, so that GB300's narrow FP64 pipe is left alone) and
 // per band sum |u|^2 (per-warp partials, added over warps in order at the
 // end).  The unit's sums go to point tile 0 of the partial buffers and zeros to
 // the other tiles.
@@ -842,7 +843,7 @@ __global__ void __launch_bounds__(FS_NP, 2) k_observe_fused(LaunchSet L, const f
   float rho[N], rho_e[N];
 #pragma unroll
   for (int z = 0; z < N; ++z) rho[z] = rho_e[z] = 0.f;
-  double jx = 0.0, jy = 0.0, jz = 0.0;
+  float js[3] = {0.f, 0.f, 0.f}, je[3] = {0.f, 0.f, 0.f};   // current over bands: js + je per axis
   int issued = nb < FO_SLOTS ? nb : FO_SLOTS;   // bands whose copy thread 0 has issued
   for (int b = 0; b < nb; ++b) {
     if (*fail) break;
@@ -894,9 +895,15 @@ __global__ void __launch_bounds__(FS_NP, 2) k_observe_fused(LaunchSet L, const f
       by = __fmaf_rn(2.f * c.gradwf[1][mm], cy[mm - 1], by);
       bz = __fmaf_rn(2.f * c.gradwf[2][mm], czs[mm - 1], bz);
     }
-    jx += bx;
-    jy += by;
-    jz += bz;
+    {
+      const float bv[3] = {bx, by, bz};
+#pragma unroll
+      for (int ax = 0; ax < 3; ++ax) {
+        const float t = js[ax] + bv[ax], bb = t - js[ax];
+        je[ax] += (js[ax] - (t - bb)) + (bv[ax] - bb);
+        js[ax] = t;
+      }
+    }
     for (int off = 16; off > 0; off >>= 1) nbs += __shfl_xor_sync(0xffffffffu, nbs, off);
     if (lane == 0) {
       sm.nrm[warp][b] = nbs;
@@ -926,6 +933,7 @@ __global__ void __launch_bounds__(FS_NP, 2) k_observe_fused(LaunchSet L, const f
   }
 #pragma unroll
   for (int z = 0; z < N; ++z) rho_part[U.rho_off + (long long)z * NP + col] = c.occ * ((double)rho[z] + (double)rho_e[z]);
+  double jx = (double)js[0] + (double)je[0], jy = (double)js[1] + (double)je[1], jz = (double)js[2] + (double)je[2];
   for (int off = 16; off > 0; off >>= 1) {
     jx += __shfl_xor_sync(0xffffffffu, jx, off);
     jy += __shfl_xor_sync(0xffffffffu, jy, off);

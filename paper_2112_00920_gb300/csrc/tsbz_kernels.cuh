@@ -754,13 +754,18 @@ __global__ void __launch_bounds__(TSBZ_PT) k_observe(LaunchSet L, const typename
 // finalize: one CTA per sub-simulation.  rho (Eq. 3), norms, and the current
 // J = -(1/(Omega N_k)) sum_k sum_b occ [ dV Re<u|-i grad u> + q |u|^2
 //                                        + 2 sum_j E_j Im(conj(c_j) a_j) ]   (Eqs. 5-6)
-// summed in a fixed order (warp w takes units w, w+8, ...).
+// summed in a fixed order (warp w takes units w, w+8, ...).  The inputs are
+// read-only here and disjoint from the outputs (restrict), so that the loads of
+// a thread's chain of units and bands are issued ahead of the sums and stores.
 // ----------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_finalize(const SubDev* subs, const UnitDev* units, const CellDev* cells,
-                                                  const double* q_obs, const typename Cplx<T>::type* Pa,
-                                                  const double* rho_part, const double* jk_part,
-                                                  const double* nrm_part, const int* mask, int mode) {
+__global__ void __launch_bounds__(256) k_finalize(const SubDev* __restrict__ subs, const UnitDev* __restrict__ units,
+                                                  const CellDev* __restrict__ cells, const double* __restrict__ q_obs,
+                                                  const typename Cplx<T>::type* __restrict__ Pa,
+                                                  const double* __restrict__ rho_part,
+                                                  const double* __restrict__ jk_part,
+                                                  const double* __restrict__ nrm_part, const int* __restrict__ mask,
+                                                  int mode) {
   using V = typename Cplx<T>::type;
   __shared__ double red[8][3];
   const int s = blockIdx.x;
@@ -771,11 +776,17 @@ __global__ void __launch_bounds__(256) k_finalize(const SubDev* subs, const Unit
   const double inv_nk = 1.0 / S.n_k;
   const int chunk = (c.npts + (int)gridDim.y - 1) / (int)gridDim.y;
   const int r_end = min(c.npts, ((int)blockIdx.y + 1) * chunk);
+  // the units of a sub-simulation are consecutive, n_bgroups * npts doubles apart
+  const double* rho_s = rho_part + units[S.unit0].rho_off;
+  const long long ustride = (long long)c.n_bgroups * c.npts;
   for (int r = (int)blockIdx.y * chunk + threadIdx.x; r < r_end; r += blockDim.x) {
     double acc = 0.0;
-    for (int kl = 0; kl < S.n_k; ++kl) {
-      const long long off = units[S.unit0 + kl].rho_off;
-      for (int g = 0; g < c.n_bgroups; ++g) acc += rho_part[off + (long long)g * c.npts + r];
+    if (c.n_bgroups == 1) {
+#pragma unroll 8
+      for (int kl = 0; kl < S.n_k; ++kl) acc += rho_s[kl * ustride + r];
+    } else {
+      for (int kl = 0; kl < S.n_k; ++kl)
+        for (int g = 0; g < c.n_bgroups; ++g) acc += rho_s[kl * ustride + (long long)g * c.npts + r];
     }
     S.rho[r] = acc * inv_nk;
   }
@@ -795,6 +806,7 @@ __global__ void __launch_bounds__(256) k_finalize(const SubDev* subs, const Unit
     double jk[3] = {0.0, 0.0, 0.0}, jn[3] = {0.0, 0.0, 0.0}, nsum = 0.0;
     for (int i = lane; i < c.n_tiles * c.n_bgroups; i += 32)
       for (int ax = 0; ax < 3; ++ax) jk[ax] += jk_part[U.jk_off + 3LL * i + ax];
+#pragma unroll 4
     for (int b = 0; b < c.n_bands; ++b) {
       double nb = 0.0;
       for (int t = lane; t < c.n_tiles; t += 32) nb += nrm_part[U.nrm_off + (long long)t * c.n_bands + b];
