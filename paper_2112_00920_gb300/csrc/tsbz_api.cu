@@ -108,7 +108,8 @@ struct tsbz_ctx {
   double dt_scale = 1.0;     // of the stage launches being issued (ETRS half steps: 1/2)
   void* psi_save = nullptr;  // psi(t_n) during an ETRS step (allocated on first use)
   const double* d_filt = nullptr;  // ground-state solver: filter coefficients per unit (stage m = 0)
-  double* d_jtile = nullptr; // per sub-simulation: [16][3] partial currents of the finalize
+  double* d_jtile = nullptr; // per sub-simulation: [TSBZ_FIN_MAX_TILES][3] partial currents of the finalize
+  int fin_tiles = 16;        // CTAs per sub-simulation of the finalize
   int* d_jcount = nullptr;   // per sub-simulation: finalize tiles done
   double2* work_a = nullptr;
   double2* work_b = nullptr;
@@ -237,6 +238,13 @@ int layout(tsbz_ctx* ctx) {
     hc.hxc_subs.clear();
     ph_stride = std::max<long long>(ph_stride, (long long)hc.dev.n_atoms * 3 * hc.dev.nmax);
   }
+  // finalize tiles: 16 per sub-simulation; with units that take a whole CTA
+  // each, as many as the largest such sub-simulation has k-points (at most
+  // TSBZ_FIN_MAX_TILES)
+  int fin_units = 16;
+  for (size_t s = 0; s < ctx->subs.size(); ++s)
+    if (fin_wide(ctx->cells[ctx->subs[s].cell].dev)) fin_units = std::max(fin_units, ctx->subs[s].n_k);
+  ctx->fin_tiles = std::min(TSBZ_FIN_MAX_TILES, fin_units);
   for (size_t s = 0; s < ctx->subs.size(); ++s) {
     HostSub& hs = ctx->subs[s];
     HostCell& hc = ctx->cells[hs.cell];
@@ -295,7 +303,7 @@ int layout(tsbz_ctx* ctx) {
   if ((rc = dalloc_t(ctx, ctx->subs.size(), &ctx->d_status))) return rc;
   if ((rc = dalloc_t(ctx, ctx->subs.size(), &ctx->d_mask))) return rc;
   if ((rc = dalloc_t(ctx, ctx->subs.size(), &ctx->d_active))) return rc;
-  if ((rc = dalloc_t(ctx, 48 * ctx->subs.size(), &ctx->d_jtile))) return rc;
+  if ((rc = dalloc_t(ctx, 3LL * TSBZ_FIN_MAX_TILES * ctx->subs.size(), &ctx->d_jtile))) return rc;
   if ((rc = dalloc_t(ctx, ctx->subs.size(), &ctx->d_jcount))) return rc;
   if ((rc = dalloc_t(ctx, std::max<long long>(work_max, 1), &ctx->work_a))) return rc;
   if ((rc = dalloc_t(ctx, std::max<long long>(work_max, 1), &ctx->work_b))) return rc;
@@ -338,7 +346,7 @@ int layout(tsbz_ctx* ctx) {
     d.status = ctx->d_status + s;
     d.active = ctx->d_active + s;
     d.veff_save = hs.veff_save;
-    d.jtile = ctx->d_jtile + 48 * s;
+    d.jtile = ctx->d_jtile + 3LL * TSBZ_FIN_MAX_TILES * s;
     d.jcount = ctx->d_jcount + s;
     CK(cudaMemsetAsync(hs.vhxc, 0, sizeof(double) * c.npts, ctx->stream));
     CK(cudaMemsetAsync(hs.J, 0, sizeof(double) * 3 * (hs.max_steps + 1), ctx->stream));
@@ -438,7 +446,8 @@ template <typename T> int run_observe(tsbz_ctx* ctx, int fin_mode) {
   }
   ev_start(ctx, FAM_FIN);
   launch_finalize_t<T>(ctx->d_subs, (int)ctx->subs.size(), ctx->d_units, ctx->d_cells, ctx->q_obs, ctx->Pa,
-                       ctx->rho_part, ctx->jk_part, ctx->nrm_part, ctx->d_mask, fin_mode, ctx->stream);
+                       ctx->rho_part, ctx->jk_part, ctx->nrm_part, ctx->d_mask, fin_mode, ctx->fin_tiles,
+                       ctx->stream);
   ev_stop(ctx);
   ++ctx->launches;
   return TSBZ_OK;

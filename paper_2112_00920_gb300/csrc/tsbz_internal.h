@@ -18,6 +18,7 @@
 #define TSBZ_MAX_VARIANTS 4  // kernel variants a cell can be tuned over
 #define TSBZ_PT 128        // points per CTA in the point-parallel kernels
 #define TSBZ_BG 32         // max bands per band group in the point-parallel kernels
+#define TSBZ_FIN_MAX_TILES 128   // most CTAs per sub-simulation of the finalize
 
 struct CellDev {
   int n1, n2, n3, npts, nmax;
@@ -61,6 +62,12 @@ struct CellDev {
   int zg_mem[8];
 };
 
+// Whether the finalize spreads one unit over a whole CTA (units with many
+// bands x projectors) rather than over one warp.
+__host__ __device__ inline bool fin_wide(const CellDev& c) {
+  return (long long)c.n_bands * (c.n_proj + c.n_tiles) > 4096;
+}
+
 struct UnitDev {
   long long psi_off;   // complex elements
   long long p_off;     // complex elements (P)
@@ -92,7 +99,7 @@ struct SubDev {
   int* status;         // non-zero: non-finite current seen
   int* active;         // 1 while the sub-simulation advances in the current step
   void* veff_save;     // [npts] in T: the other v_eff of an ETRS step (null otherwise)
-  double* jtile;       // [16][3] per-tile partial sums of the current (finalize)
+  double* jtile;       // [TSBZ_FIN_MAX_TILES][3] per-tile partial sums of the current (finalize)
   int* jcount;         // tiles of the finalize done (reset by the last one)
 };
 
@@ -149,7 +156,7 @@ void launch_observe(const LaunchSet& L, const void* psi, double* rho_part, doubl
 template <typename T>
 void launch_finalize_t(const SubDev* subs, int n_subs, const UnitDev* units, const CellDev* cells_dev,
                        const double* q_obs, const void* Pa, const double* rho_part, const double* jk_part,
-                       const double* nrm_part, const int* mask, int mode, void* stream);
+                       const double* nrm_part, const int* mask, int mode, int n_tiles, void* stream);
 template <typename T>
 int launch_hxc_t(const SubDev* subs_dev, const int* sub_ids_dev, int n_subs, const CellDev& c, double2* wa,
                  double2* wb, double2* const tw[3], void* stream);

@@ -257,20 +257,47 @@ __global__ void __launch_bounds__(256) k_bra(LaunchSet L, const typename Cplx<T>
 // bra on the projector boxes: the same P as k_bra, from the factorisation
 // C_row(r) = pn_t F^a_x(ix) F^a_y(iy) F^a_z(iz) d_x^i d_y^j d_z^k (F = g e^{i q d})
 // restricted to the atom's box (the Gaussian factor is zero outside it).  One CTA
-// per (atom, unit, band block), one thread per (x, y) column of the box (at most
-// 16 x 16): the column sums Z_k = sum_z F_z d_z^k t (k <= 1, or <= 2 for the
-// current), then the x and y weights, then a fixed-order CTA reduction.
+// per (atom, unit, block of BRA_BOX_BANDS bands), one thread per (x, y) column of
+// the box (at most 16 x 16).  Bands go through in sub-blocks of BB_SUB: per
+// column the sums Z_k = sum_z F_z d_z^k t (k <= 1, or <= 2 for the current) of
+// all bands of the sub-block in one z loop (F_z, d_z read once per plane), then
+// the x and y weights give the sub-block's row values, which one warp
+// reduce-scatter and one fixed-order sum over the warps add up.
 //   NW = 1: rows 4 a + t (t = s, p_x, p_y, p_z);  NW = 4: rows 4 (4 a + t) + alpha.
 // ----------------------------------------------------------------------------
 #define BRA_BOX_BANDS 8   // bands per CTA of k_bra_box
+
+template <typename T, int NW> struct BraBoxShape {
+  static constexpr int NR = 4 * NW;                                // rows of the atom
+  static constexpr int KD = NW == 1 ? 2 : 3;                       // powers of d_z in the column sums
+  static constexpr int SUB = (sizeof(T) == 8 ? 4 : 8) / NW;      // bands per sub-block (NW = 1 or 4)
+  static constexpr int NF = 2 * SUB * NR;                          // real values per thread (32 or 64)
+};
+
+// Sum of x[0..NF) over the 32 lanes of a warp, scattered: afterwards lane l holds
+// in x[0..NF/32) the sums of the values NF/32 * l + e (fixed butterfly order).
+template <typename T, int NF>
+__device__ __forceinline__ void warp_reduce_scatter(T (&x)[NF], int lane) {
+  static_assert(NF == 32 || NF == 64, "32 or 64 values");
+#pragma unroll
+  for (int o = 16, n = NF; o > 0; o >>= 1, n >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < n / 2; ++i) {
+      const T keep = up ? x[n / 2 + i] : x[i];
+      const T send = up ? x[i] : x[n / 2 + i];
+      x[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+}
 
 template <typename T, int NW>
 __global__ void __launch_bounds__(256) k_bra_box(LaunchSet L, const typename Cplx<T>::type* __restrict__ src,
                                                  typename Cplx<T>::type* __restrict__ P, int use_obs) {
   using V = typename Cplx<T>::type;
-  constexpr int NR = 4 * NW;            // rows of the atom
-  constexpr int KD = NW == 1 ? 2 : 3;   // powers of d_z kept in the column sums
-  __shared__ V red[8][NR];
+  using SH = BraBoxShape<T, NW>;
+  constexpr int NR = SH::NR, KD = SH::KD, SUB = SH::SUB, NF = SH::NF, PL = NF / 32;
+  __shared__ T red[8][NF];
   const CellDev& c = L.cell;
   const int a = blockIdx.x;
   const int u = L.unit_ids[blockIdx.y];
@@ -279,6 +306,7 @@ __global__ void __launch_bounds__(256) k_bra_box(LaunchSet L, const typename Cpl
   const int* bx = c.pbox + a * 6;
   const int sx = bx[0], lx = bx[1], sy = bx[2], ly = bx[3], sz = bx[4], lz = bx[5];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int n_warps = (int)(blockDim.x >> 5);
   const bool live = t < lx * ly;
   const int ix = (sx + (live ? t % lx : 0)) % c.n1, iy = (sy + (live ? t / lx : 0)) % c.n2;
   const int nm = c.nmax, n12 = c.n1 * c.n2;
@@ -291,56 +319,68 @@ __global__ void __launch_bounds__(256) k_bra_box(LaunchSet L, const typename Cpl
   const T dx = da[ix], dy = da[nm + iy];
   const int rows = c.n_proj * NW;
   const long long off = (NW == 1) ? U.p_off : U.pa_off;
-  const int b_end = min(c.n_bands, (int)(blockIdx.z + 1) * BRA_BOX_BANDS);
-  for (int b = blockIdx.z * BRA_BOX_BANDS; b < b_end; ++b) {
-    const V* tb = src + U.psi_off + (long long)b * c.npts + iy * c.n1 + ix;
-    V z[KD];
+  const int b_begin = blockIdx.z * BRA_BOX_BANDS;
+  const int b_end = min(c.n_bands, b_begin + BRA_BOX_BANDS);
+  for (int b0 = b_begin; b0 < b_end; b0 += SUB) {
+    const V* tb = src + U.psi_off + (long long)b0 * c.npts + iy * c.n1 + ix;
+    V z[SUB][KD];
 #pragma unroll
-    for (int k = 0; k < KD; ++k) z[k] = cmk<V>((T)0, (T)0);
+    for (int bl = 0; bl < SUB; ++bl)
+#pragma unroll
+      for (int k = 0; k < KD; ++k) z[bl][k] = cmk<V>((T)0, (T)0);
     if (live) {
+#pragma unroll 2
       for (int kz = 0; kz < lz; ++kz) {
         const int iz = (sz + kz) % c.n3;
         const V fz = cscale(ph[2 * nm + iz], ga[2 * nm + iz]);
         const T dz = da[2 * nm + iz];
-        V w = cmul(fz, tb[(long long)iz * n12]);
-        z[0] = cadd(z[0], w);
-        w = cscale(w, dz);
-        z[1] = cadd(z[1], w);
-        if (KD > 2) z[KD - 1] = cadd(z[KD - 1], cscale(w, dz));
+#pragma unroll
+        for (int bl = 0; bl < SUB; ++bl) {
+          if (b0 + bl < b_end) {
+            V w = cmul(fz, tb[(long long)bl * c.npts + (long long)iz * n12]);
+            z[bl][0] = cadd(z[bl][0], w);
+            w = cscale(w, dz);
+            z[bl][1] = cadd(z[bl][1], w);
+            if (KD > 2) z[bl][KD - 1] = cadd(z[bl][KD - 1], cscale(w, dz));
+          }
+        }
       }
     }
-    // row values of this column: monomial d_x^i d_y^j d_z^k with the column sums
-    V v[NR];
+    // row values of this column, (band, row) in order, as real pairs:
+    // monomial d_x^i d_y^j d_z^k times the column sums
+    T x[NF];
 #pragma unroll
-    for (int tt = 0; tt < 4; ++tt) {
-      const int ti = tt == 1, tj = tt == 2, tk = tt == 3;
+    for (int bl = 0; bl < SUB; ++bl)
 #pragma unroll
-      for (int al = 0; al < NW; ++al) {
-        const int i = ti + (NW == 4 && al == 1), j = tj + (NW == 4 && al == 2), k = tk + (NW == 4 && al == 3);
-        T wxy = (T)1;
-        if (i >= 1) wxy *= dx;
-        if (i >= 2) wxy *= dx;
-        if (j >= 1) wxy *= dy;
-        if (j >= 2) wxy *= dy;
-        v[tt * NW + al] = live ? cscale(cmul(fxy, z[k < KD ? k : KD - 1]), wxy) : cmk<V>((T)0, (T)0);
+      for (int tt = 0; tt < 4; ++tt) {
+        const int ti = tt == 1, tj = tt == 2, tk = tt == 3;
+#pragma unroll
+        for (int al = 0; al < NW; ++al) {
+          const int i = ti + (NW == 4 && al == 1), j = tj + (NW == 4 && al == 2), k = tk + (NW == 4 && al == 3);
+          T wxy = (T)1;
+          if (i >= 1) wxy *= dx;
+          if (i >= 2) wxy *= dx;
+          if (j >= 1) wxy *= dy;
+          if (j >= 2) wxy *= dy;
+          const V vv = live ? cscale(cmul(fxy, z[bl][k < KD ? k : KD - 1]), wxy) : cmk<V>((T)0, (T)0);
+          const int r = bl * NR + tt * NW + al;
+          x[2 * r] = vv.x;
+          x[2 * r + 1] = vv.y;
+        }
       }
-    }
-    // fixed-order reduction over the columns: warp shuffles, then warps in order
+    // fixed-order reduction over the columns: warp reduce-scatter, then warps in order
+    warp_reduce_scatter<T, NF>(x, lane);
 #pragma unroll
-    for (int r = 0; r < NR; ++r)
-      for (int o = 16; o > 0; o >>= 1) {
-        v[r].x += __shfl_xor_sync(0xffffffffu, v[r].x, o);
-        v[r].y += __shfl_xor_sync(0xffffffffu, v[r].y, o);
-      }
-    if (lane == 0)
-#pragma unroll
-      for (int r = 0; r < NR; ++r) red[warp][r] = v[r];
+    for (int e = 0; e < PL; ++e) red[warp][PL * lane + e] = x[e];
     __syncthreads();
-    if (t < NR) {
-      V sum = cmk<V>((T)0, (T)0);
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum = cadd(sum, red[w][t]);
-      const int tt = t / NW;
-      P[off + (long long)b * rows + a * NR + t] = cscale(sum, (T)c.dv * pn[tt]);
+    if (t < NF) {
+      T sum = (T)0;
+      for (int w = 0; w < n_warps; ++w) sum += red[w][t];
+      const int r = (t >> 1) % NR, bl = (t >> 1) / NR, b = b0 + bl;
+      if (b < b_end) {
+        const T sc = (T)c.dv * pn[r / NW];
+        reinterpret_cast<T*>(P + off + (long long)b * rows + a * NR + r)[t & 1] = sum * sc;
+      }
     }
     __syncthreads();
   }
@@ -392,6 +432,15 @@ __global__ void __launch_bounds__(TSBZ_PT) k_stage(LaunchSet L, const typename C
     lw[ax][mm] = (T)(-0.5 * c.lapw[ax][mm]);
     gw[ax][mm] = (T)c.gradw[ax][mm];
   }
+  // the atoms whose projector box holds the point (bit a), found once for all
+  // band chunks when there are at most 64; outside a box the factor is exactly zero
+  const bool use_mask = c.use_proj && c.n_atoms <= 64;
+  unsigned long long amask = 0ull;
+  if (use_mask && valid)
+    for (int a = 0; a < c.n_atoms; ++a) {
+      const T* ga = Tab<T>::g1(c) + (long long)a * 3 * nm;
+      if (ga[ix] * ga[nm + iy] * ga[2 * nm + iz] != (T)0) amask |= 1ull << a;
+    }
   for (int b0 = 0; b0 < c.n_bands; b0 += BC) {
     __syncthreads();
     if (c.use_proj) {
@@ -408,7 +457,10 @@ __global__ void __launch_bounds__(TSBZ_PT) k_stage(LaunchSet L, const typename C
 #pragma unroll
     for (int bl = 0; bl < BC; ++bl) ket[bl] = zero;
     if (c.use_proj) {
-      for (int a = 0; a < c.n_atoms; ++a) {
+      // atoms in increasing order: the set bits of the mask, else every atom with the box test
+      unsigned long long mk = amask;
+      for (int a = use_mask ? (mk ? __ffsll((long long)mk) - 1 : c.n_atoms) : 0; a < c.n_atoms;
+           a = use_mask ? ((mk &= mk - 1) ? __ffsll((long long)mk) - 1 : c.n_atoms) : a + 1) {
         const T* ga = Tab<T>::g1(c) + (long long)a * 3 * nm;
         const T* da = Tab<T>::d1(c) + (long long)a * 3 * nm;
         const T g = ga[ix] * ga[nm + iy] * ga[2 * nm + iz];
@@ -751,10 +803,10 @@ __global__ void __launch_bounds__(TSBZ_PT) k_observe(LaunchSet L, const typename
 }
 
 // ----------------------------------------------------------------------------
-// finalize: one CTA per sub-simulation.  rho (Eq. 3), norms, and the current
+// finalize: n_tiles CTAs per sub-simulation.  rho (Eq. 3), norms, and the current
 // J = -(1/(Omega N_k)) sum_k sum_b occ [ dV Re<u|-i grad u> + q |u|^2
 //                                        + 2 sum_j E_j Im(conj(c_j) a_j) ]   (Eqs. 5-6)
-// summed in a fixed order (warp w takes units w, w+8, ...).  The inputs are
+// summed in a fixed order.  The inputs are
 // read-only here and disjoint from the outputs (restrict), so that the loads of
 // a thread's chain of units and bands are issued ahead of the sums and stores.
 // ----------------------------------------------------------------------------
@@ -767,7 +819,6 @@ __global__ void __launch_bounds__(256) k_finalize(const SubDev* __restrict__ sub
                                                   const double* __restrict__ nrm_part, const int* __restrict__ mask,
                                                   int mode) {
   using V = typename Cplx<T>::type;
-  __shared__ double red[8][3];
   const int s = blockIdx.x;
   const SubDev S = subs[s];
   if ((mode == TSBZ_FIN_STEP || mode == TSBZ_FIN_RHO) && !*S.active) return;   // budget spent: nothing of this step
@@ -790,24 +841,31 @@ __global__ void __launch_bounds__(256) k_finalize(const SubDev* __restrict__ sub
     }
     S.rho[r] = acc * inv_nk;
   }
-  // current and norms: the units kl = tile + ntile j are this CTA's (warp w takes
-  // every 8th of them); the partial sums of the tiles are added in tile order by
-  // the CTA that finishes last, which also writes J and advances the step
+  // current and norms of the units kl = tile + ntile j.  Small units (few
+  // bands x projectors): warp w of the CTA takes every n_warps-th of them, lanes
+  // share a unit.  Large units: the CTA takes them one at a time over all its
+  // threads (warp w takes the band norms w, w + n_warps, ...).  Either way the
+  // partial sums are added in a fixed order (lanes, warps in order, units in
+  // increasing kl); the CTA that finishes last adds the tiles' partial currents
+  // in tile order, writes J and advances the step.
   const int tile = blockIdx.y, ntile = gridDim.y;
   const int step = *S.step;
   const bool write_j = mode != TSBZ_FIN_RHO &&
                        ((mode == TSBZ_FIN_STEP) || (mask != nullptr && mask[s] != 0 &&
                                                     (mode == TSBZ_FIN_J0MINUS || step == 0)));
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double jw[3] = {0.0, 0.0, 0.0};
-  for (int kl = tile + ntile * warp; kl < S.n_k; kl += ntile * 8) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, n_warps = (int)(blockDim.x >> 5);
+  const bool wide = fin_wide(c);
+  const int u_first = wide ? tile : tile + ntile * warp, u_step = wide ? ntile : ntile * n_warps;
+  const int b_first = wide ? warp : 0, b_step = wide ? n_warps : 1;
+  const int e_first = wide ? (int)threadIdx.x : lane, e_step = wide ? (int)blockDim.x : 32;
+  __shared__ double red[8][4];
+  double jw[3] = {0.0, 0.0, 0.0};   // this warp's units (small), thread 0: this CTA's units (large)
+  for (int kl = u_first; kl < S.n_k; kl += u_step) {
     const UnitDev U = units[S.unit0 + kl];
     const int u = S.unit0 + kl;
     double jk[3] = {0.0, 0.0, 0.0}, jn[3] = {0.0, 0.0, 0.0}, nsum = 0.0;
-    for (int i = lane; i < c.n_tiles * c.n_bgroups; i += 32)
-      for (int ax = 0; ax < 3; ++ax) jk[ax] += jk_part[U.jk_off + 3LL * i + ax];
 #pragma unroll 4
-    for (int b = 0; b < c.n_bands; ++b) {
+    for (int b = b_first; b < c.n_bands; b += b_step) {
       double nb = 0.0;
       for (int t = lane; t < c.n_tiles; t += 32) nb += nrm_part[U.nrm_off + (long long)t * c.n_bands + b];
       for (int off = 16; off > 0; off >>= 1) nb += __shfl_xor_sync(0xffffffffu, nb, off);
@@ -815,9 +873,12 @@ __global__ void __launch_bounds__(256) k_finalize(const SubDev* __restrict__ sub
       if (lane == 0) S.norms[kl * c.n_bands + b] = nb;
       nsum += nb;  // identical in every lane
     }
+    for (int i = e_first; i < c.n_tiles * c.n_bgroups; i += e_step)
+      for (int ax = 0; ax < 3; ++ax) jk[ax] += jk_part[U.jk_off + 3LL * i + ax];
     if (c.use_proj) {
       const int np = c.n_proj;
-      for (int i = lane; i < c.n_bands * np; i += 32) {
+#pragma unroll 4
+      for (int i = e_first; i < c.n_bands * np; i += e_step) {
         const int j = i % np;
         const V* pr = Pa + U.pa_off + 4LL * i;
         const double ar = pr[0].x, ai = pr[0].y;
@@ -829,22 +890,43 @@ __global__ void __launch_bounds__(256) k_finalize(const SubDev* __restrict__ sub
         }
       }
     }
+    double v[3];
     for (int ax = 0; ax < 3; ++ax) {
-      double v = c.dv * jk[ax] + jn[ax];
-      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-      jw[ax] += c.occ * (v + q_obs[3 * u + ax] * nsum);
+      v[ax] = c.dv * jk[ax] + jn[ax];
+      for (int off = 16; off > 0; off >>= 1) v[ax] += __shfl_xor_sync(0xffffffffu, v[ax], off);
     }
+    if (!wide) {
+      for (int ax = 0; ax < 3; ++ax) jw[ax] += c.occ * (v[ax] + q_obs[3 * u + ax] * nsum);
+      continue;
+    }
+    if (lane == 0) {
+      for (int ax = 0; ax < 3; ++ax) red[warp][ax] = v[ax];
+      red[warp][3] = nsum;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sum[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int w = 0; w < n_warps; ++w)
+        for (int k = 0; k < 4; ++k) sum[k] += red[w][k];
+      for (int ax = 0; ax < 3; ++ax) jw[ax] += c.occ * (sum[ax] + q_obs[3 * u + ax] * sum[3]);
+    }
+    __syncthreads();
   }
-  if (lane == 0)
-    for (int ax = 0; ax < 3; ++ax) red[warp][ax] = jw[ax];
+  if (!wide) {
+    // the warps' sums in warp order
+    if (lane == 0)
+      for (int ax = 0; ax < 3; ++ax) red[warp][ax] = jw[ax];
+    __syncthreads();
+    if (threadIdx.x == 0)
+      for (int ax = 0; ax < 3; ++ax) {
+        double t = 0.0;
+        for (int w = 0; w < n_warps; ++w) t += red[w][ax];
+        jw[ax] = t;
+      }
+  }
   __shared__ int last;
-  __syncthreads();
   if (threadIdx.x == 0) {
-    for (int ax = 0; ax < 3; ++ax) {
-      double t = 0.0;
-      for (int w = 0; w < 8; ++w) t += red[w][ax];
-      S.jtile[3 * tile + ax] = t;
-    }
+    for (int ax = 0; ax < 3; ++ax) S.jtile[3 * tile + ax] = jw[ax];
     __threadfence();
     last = atomicAdd(S.jcount, 1) == ntile - 1;
   }
@@ -1167,12 +1249,13 @@ void launch_observe(const LaunchSet& L, const void* psi, double* rho_part, doubl
 template <typename T>
 void launch_finalize_t(const SubDev* subs, int n_subs, const UnitDev* units, const CellDev* cells_dev,
                        const double* q_obs, const void* Pa, const double* rho_part, const double* jk_part,
-                       const double* nrm_part, const int* mask, int mode, void* stream) {
+                       const double* nrm_part, const int* mask, int mode, int n_tiles, void* stream) {
   using V = typename Cplx<T>::type;
   if (n_subs == 0) return;
-  // 16 tiles per sub-simulation: density points, and units for the current and the norms
-  k_finalize<T><<<dim3(n_subs, 16), 256, 0, (cudaStream_t)stream>>>(subs, units, cells_dev, q_obs, (const V*)Pa,
-                                                                    rho_part, jk_part, nrm_part, mask, mode);
+  // n_tiles (16 .. TSBZ_FIN_MAX_TILES) tiles per sub-simulation: density points, and units for the
+  // current and the norms
+  k_finalize<T><<<dim3(n_subs, n_tiles), 256, 0, (cudaStream_t)stream>>>(subs, units, cells_dev, q_obs, (const V*)Pa,
+                                                                         rho_part, jk_part, nrm_part, mask, mode);
 }
 
 template <typename T>

@@ -7,7 +7,7 @@ template void launch_stage<float>(const LaunchSet&, const void*, void*, void*, c
 template void launch_observe<float>(const LaunchSet&, const void*, double*, double*, double*, void*);
 template void launch_finalize_t<float>(const SubDev*, int, const UnitDev*, const CellDev*, const double*,
                                         const void*, const double*, const double*, const double*, const int*, int,
-                                        void*);
+                                        int, void*);
 template int launch_hxc_t<float>(const SubDev*, const int*, int, const CellDev&, double2*, double2*,
                                   double2* const[3], void*);
 template void launch_convert_in_t<float>(const double2*, void*, long long, void*);

@@ -7,7 +7,7 @@ template void launch_stage<double>(const LaunchSet&, const void*, void*, void*, 
 template void launch_observe<double>(const LaunchSet&, const void*, double*, double*, double*, void*);
 template void launch_finalize_t<double>(const SubDev*, int, const UnitDev*, const CellDev*, const double*,
                                         const void*, const double*, const double*, const double*, const int*, int,
-                                        void*);
+                                        int, void*);
 template int launch_hxc_t<double>(const SubDev*, const int*, int, const CellDev&, double2*, double2*,
                                   double2* const[3], void*);
 template void launch_convert_in_t<double>(const double2*, void*, long long, void*);
