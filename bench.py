@@ -336,7 +336,13 @@ def main():
                     help="run only the warm-up and timed steps (for profiler launch lists and captures)")
     ap.add_argument("--subsims", type=int, default=64,
                     help="number of the 64 shifted subgrids to run (profiling of a reduced case)")
+    ap.add_argument("--workload", default="twostep64", choices=["twostep64"] + sorted(SIDE_WORKLOADS),
+                    help="twostep64: the benchmark; the others time a side workload (one JSON line, "
+                         "no baselines) for the large-cell path")
     args = ap.parse_args()
+    if args.workload != "twostep64":
+        run_side_workload(args)
+        return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -562,6 +568,67 @@ def main():
         print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------
+# Side workloads of the large-cell (point-parallel) path; not the benchmark
+# ----------------------------------------------------------------------------
+SIDE_WORKLOADS = {
+    "cell-b-mp2": "2x2x2 supercell (32^3 grid, 64 atoms, 128 bands), one sub-simulation on a shifted 2^3 "
+                  "MP grid (8 k-points), kick 0.005 along x, default kernel variant",
+    "uneven": "uneven batch: 18 8-atom 16^3 cells and 2 32^3 supercells with 2^3..6^3 shifted subgrids, "
+              "kicks 1e-4..1e-2, autotuned (20 s budget)",
+}
+
+
+def run_side_workload(args):
+    import torch
+    import workloads as W
+    from paper_2112_00920_gb300 import Propagator, build_library, shifted_kpoints
+    build_library()
+    cap = args.warmup + args.steps + 40
+    P = Propagator(args.precision)
+    if args.workload == "cell-b-mp2":
+        cb = W.cell_b()
+        subs = [W.SubsimSpec(cb, (2, 2, 2), (0.5, 0.5, 0.5), 0.08, cap, W.Kick(k0=0.005))]
+    else:
+        subs = W.uneven_batch_run(n_a=18, n_b=2, max_steps=cap).subsims
+    cells, sids, n_orb, n_pb = {}, [], 0, 0
+    for s in subs:
+        if s.cell.name not in cells:
+            cells[s.cell.name] = P.add_cell_spec(s.cell)
+        sids.append(P.add_subsim(cells[s.cell.name], shifted_kpoints(s.cell.a, s.mp, s.shift), s.dt, cap))
+    for s, sid in zip(subs, sids):
+        c = s.cell
+        nk = s.mp[0] * s.mp[1] * s.mp[2]
+        psi = torch.from_numpy(W.plane_wave_orbitals(c.a, c.n, W.plane_wave_set(c.n_bands), nk)).cuda()
+        P.load_ground_state(sid, psi)
+        del psi
+        P.set_kick(sid, s.field.k0, s.field.direction)
+        n_orb += nk * c.n_bands
+        n_pb += nk * c.n_bands * c.n_pts
+    P.propagate(args.warmup)
+    tuned = 0
+    if args.workload == "uneven":
+        tuned = P.autotune(budget_ms=20000)
+        P.propagate(1)
+    P.set_profiling(True)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    P.propagate(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    fam = {k: v / args.steps for k, v in P.timings().items()}
+    print(json.dumps({"workload": args.workload, "description": SIDE_WORKLOADS[args.workload],
+                      "precision": args.precision, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": ms, "orbital_steps_per_s": n_orb / (ms / 1e3),
+                      "point_band_steps_per_s": n_pb / (ms / 1e3), "family_ms_per_step": fam,
+                      "variants": {name: P.variant(cid) for name, cid in cells.items()},
+                      "variants_timed": tuned}))
+    P.close()
 
 
 def run_reference(args):
