@@ -23,7 +23,7 @@ Modules (each function cites the paper passage it follows):
 Parity pinning status of every function is listed in the test modules
 ``tests/test_oracle_*.py``; the v_loc/projector tables are pinned by
 symmetry, normalisation, Fourier-coefficient and isolated-atom checks, and
-the SCF ground state is parity unpinned (no paper values exist; it is an
-input to both sides and only its residuals are checked).
+the SCF ground state by the free-electron closed form and a brute-force
+dense-matrix SCF on a tiny cell (no paper values exist for it).
 """
 from . import fd, kpoints, cell, hxc, hamiltonian, scf, dynamics, analysis  # noqa: F401

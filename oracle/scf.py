@@ -7,9 +7,13 @@ fixed occupations (the n_bands lowest states of every k, f = 2), h_k at
 A = 0, a block LOBPCG eigensolver per k with a kinetic preconditioner,
 and Pulay (DIIS) density mixing until dV sum |rho_out - rho_in| / N_e <= tol.
 
-Parity unpinned: no paper values exist for this synthetic material.  The
-ground state is an input to both the oracle's and the GPU's propagation;
-tests check its eigen-residuals with the stencil Hamiltonian.
+Pinned (tests/test_oracle_scf.py) against results outside this module's
+eigensolver and mixing: the free-electron closed form (the lowest plane waves
+of the explicit stencil matrix, a constant v_xc, a uniform density) and a
+brute-force SCF (explicit Hamiltonian matrix, dense Hermitian eigensolver,
+plain linear mixing) on a tiny gapped cell.  No paper values exist for this
+synthetic material; tests also check the eigen-residuals with the stencil
+Hamiltonian.
 """
 from __future__ import annotations
 
