@@ -722,7 +722,11 @@ __global__ void __launch_bounds__(256, 4) k_stage_z(LaunchSet L, const typename 
 // and band norms.  grid (point tiles, units, band groups), TSBZ_PT threads.
 // At one grid point the sums over the bands of the group are formed in T
 // (their terms are products of T orbitals); every sum over grid points,
-// k-points and sub-simulations is double.
+// k-points and sub-simulations is double.  The current's local part is only
+// needed summed over the periodic grid, where
+//   sum_r Re(u* (-i grad_ax) u) = 2 sum_m w_m sum_r Im(conj(u(r)) u(r + m e_ax)),
+// so each point loads its forward neighbours only (the tile partials differ
+// from the gradient form's, their total does not).
 // ----------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(TSBZ_PT) k_observe(LaunchSet L, const typename Cplx<T>::type* __restrict__ psi,
@@ -757,20 +761,20 @@ __global__ void __launch_bounds__(TSBZ_PT) k_observe(LaunchSet L, const typename
       const V ce = tb[pp];
       n2 = ce.x * ce.x + ce.y * ce.y;
       rho += n2;
-      V g[3];
-      for (int ax = 0; ax < 3; ++ax) g[ax] = cmk<V>((T)0, (T)0);
+      T cx = (T)0, cy = (T)0, cz = (T)0;
       const int rowb = iz * n12 + iy * c.n1;
       for (int mm = 1; mm <= c.nd; ++mm) {
-        rfma(g[0], gw[0][mm], csub(tb[rowb + wrap_idx(ix + mm, c.n1)], tb[rowb + wrap_idx(ix - mm, c.n1)]));
-        rfma(g[1], gw[1][mm], csub(tb[iz * n12 + wrap_idx(iy + mm, c.n2) * c.n1 + ix],
-                                   tb[iz * n12 + wrap_idx(iy - mm, c.n2) * c.n1 + ix]));
-        rfma(g[2], gw[2][mm], csub(tb[wrap_idx(iz + mm, c.n3) * n12 + iy * c.n1 + ix],
-                                   tb[wrap_idx(iz - mm, c.n3) * n12 + iy * c.n1 + ix]));
+        const V xu = tb[rowb + wrap_idx(ix + mm, c.n1)];
+        const V yu = tb[iz * n12 + wrap_idx(iy + mm, c.n2) * c.n1 + ix];
+        const V zu = tb[wrap_idx(iz + mm, c.n3) * n12 + iy * c.n1 + ix];
+        // Im(conj(u) v) = u_r v_i - u_i v_r
+        cx += gw[0][mm] * (ce.x * xu.y - ce.y * xu.x);
+        cy += gw[1][mm] * (ce.x * yu.y - ce.y * yu.x);
+        cz += gw[2][mm] * (ce.x * zu.y - ce.y * zu.x);
       }
-      // Re(conj(u) (-i g)) = u_r g_i - u_i g_r
-      jx += ce.x * g[0].y - ce.y * g[0].x;
-      jy += ce.x * g[1].y - ce.y * g[1].x;
-      jz += ce.x * g[2].y - ce.y * g[2].x;
+      jx += (T)2 * cx;
+      jy += (T)2 * cy;
+      jz += (T)2 * cz;
     }
     red_n[b - b_begin][threadIdx.x] = n2;
   }
