@@ -258,3 +258,25 @@ def test_two_step_exactness_frozen_potential():
     assert np.max(np.abs(dfull[:, 0])) > 1e-6
     np.testing.assert_allclose(avg, dfull, atol=1e-12 * np.max(np.abs(dfull)) + 1e-17)
     np.testing.assert_allclose(np.mean(rhos, axis=0), full["rho"], rtol=1e-12)
+
+
+def test_local_current_correlation_form():
+    """On the periodic grid the kinetic part of <u|pi|u> (Eqs. 5-6), summed over
+    the grid, equals 2 sum_m (d_m / h) sum_r Im(conj(u(r)) u(r + m e_ax)): the
+    form in which the GPU observation kernels accumulate it (forward neighbours
+    only).  Checked per band and axis on a ragged grid with random orbitals."""
+    from oracle.cell import Grid
+    from oracle.dynamics import grad_fd
+    from oracle import fd
+    cell = W.cell_tiny(n=(8, 10, 12), a=(6.0, 7.0, 8.0), n_bands=3)
+    grid = Grid(cell)
+    u = W.random_orbitals(1, 3, cell.n, grid.dv, seed=9)[0]
+    g = grad_fd(grid, u)
+    kin = np.real(np.sum(np.conj(u)[None] * (-1j) * g, axis=(-3, -2, -1)))   # (3, n_b)
+    _, d = fd.weights_float(4)
+    corr = np.zeros_like(kin)
+    for ax, axis in enumerate((-1, -2, -3)):
+        for m in range(1, 5):
+            fwd = np.roll(u, -m, axis=axis)                                    # u(r + m e_ax)
+            corr[ax] += 2.0 * d[m] / grid.h[ax] * np.sum(np.imag(np.conj(u) * fwd), axis=(-3, -2, -1))
+    np.testing.assert_allclose(corr, kin, rtol=0, atol=1e-12 * np.max(np.abs(kin)))
