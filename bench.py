@@ -44,29 +44,97 @@ WORKLOAD = "two-step 64x4^3 shifted MP, Si-like 8-atom cubic cell, 16^3 grid, 16
 # ----------------------------------------------------------------------------
 # CPU oracle timing (reference arm and cpu_baseline)
 # ----------------------------------------------------------------------------
-def _oracle_job(args):
-    m, n_steps = args
+def _oracle_worker(conn, m, max_steps):
+    """One host process holding one sub-simulation of the two-step workload
+    (shifted 4^3 subgrid m: 64 k-points x 16 bands, plane-wave start, kick).
+    Commands: ("step", n) propagates n time steps with the oracle and returns
+    (propagate-only seconds, orbital-steps); ("quit", 0) ends the process.
+    The oracle's propagate() also evaluates rho, v_Hxc, J(0-) and J(0+) of its
+    start state; that fixed part is measured once (a call with no steps) and
+    subtracted, so the returned time is that of the time steps alone."""
     import workloads as W
-    from oracle import dynamics
-    run = W.twostep_kick_run(n_steps=n_steps)
-    sub = run.subsims[m]
+    from oracle import dynamics, kpoints
+    run = W.twostep_kick_run(n_steps=max_steps)
+    sub = run.subsims[m % len(run.subsims)]
     cell = sub.cell
-    psi = W.plane_wave_orbitals(cell.a, cell.n, W.plane_wave_set(cell.n_bands), sub.mp[0] * sub.mp[1] * sub.mp[2])
-    t0 = time.perf_counter()
-    dynamics._run_one((sub, psi, "scf", None))
-    return time.perf_counter() - t0, psi.shape[0] * psi.shape[1] * n_steps
+    nk = sub.mp[0] * sub.mp[1] * sub.mp[2]
+    u = W.plane_wave_orbitals(cell.a, cell.n, W.plane_wave_set(cell.n_bands), nk)
+    k = kpoints.kpoints_cartesian(cell.a, sub.mp, sub.shift)
+    ops = dynamics.Operators(cell)
+    a_all = dynamics.field_samples(sub.field, sub.dt, max_steps)
+    fixed = []
+    for _ in range(2):
+        t0 = time.perf_counter()
+        dynamics.propagate(cell, k, u, sub.dt, 0, a_all[:1], ops=ops, keep_state=False)
+        fixed.append(time.perf_counter() - t0)
+    t_fixed = min(fixed)
+    step = 0
+    conn.send(("ready", t_fixed))
+    while True:
+        cmd, n = conn.recv()
+        if cmd != "step":
+            break
+        t0 = time.perf_counter()
+        res = dynamics.propagate(cell, k, u, sub.dt, n, a_all[2 * step: 2 * (step + n) + 1], ops=ops)
+        dt_wall = time.perf_counter() - t0
+        u = res["u"]
+        step += n
+        conn.send((max(dt_wall - t_fixed, 1e-9), nk * cell.n_bands * n))
+    conn.close()
 
 
-def oracle_sample(workers: int, n_steps: int = 1):
-    """Each worker propagates one sub-simulation (64 k x 16 bands) for n_steps
-    with the oracle; returns (orbital-steps, wall seconds)."""
-    import multiprocessing as mp
-    jobs = [(m % 64, n_steps) for m in range(workers)]
-    t0 = time.perf_counter()
-    with mp.get_context("spawn").Pool(workers) as pool:
-        res = pool.map(_oracle_job, jobs)
-    wall = time.perf_counter() - t0
-    return sum(r[1] for r in res), wall
+class OraclePool:
+    """`workers` host processes, one sub-simulation each (spawned, one BLAS
+    thread per process), stepped together: the CPU oracle timed on a bounded
+    sample of the benchmark workload."""
+
+    def __init__(self, workers: int, max_steps: int):
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        self.conns, self.procs = [], []
+        for m in range(workers):
+            a, b = ctx.Pipe()
+            p = ctx.Process(target=_oracle_worker, args=(b, m, max_steps), daemon=True)
+            p.start()
+            self.conns.append(a)
+            self.procs.append(p)
+        self.t_fixed = [c.recv()[1] for c in self.conns]
+
+    def step(self, n: int = 1):
+        """All workers advance n steps at once; returns (orbital-steps, wall
+        seconds of the parallel step = the slowest worker's propagate time)."""
+        for c in self.conns:
+            c.send(("step", n))
+        res = [c.recv() for c in self.conns]
+        return sum(r[1] for r in res), max(r[0] for r in res)
+
+    def close(self):
+        for c in self.conns:
+            try:
+                c.send(("quit", 0))
+            except (BrokenPipeError, OSError):
+                pass
+        for p in self.procs:
+            p.join(timeout=30)
+
+
+def oracle_baseline(workers: int, steps: int, warmup: int = 1):
+    """cpu_baseline: `workers` processes (one per host core) x `steps` timed
+    time steps after `warmup`, then one process alone for a 1-core figure."""
+    pool = OraclePool(workers, warmup + steps)
+    try:
+        if warmup:
+            pool.step(warmup)
+        units, wall = pool.step(steps)
+    finally:
+        pool.close()
+    one = OraclePool(1, 2)
+    try:
+        one.step(1)
+        u1, w1 = one.step(1)
+    finally:
+        one.close()
+    return units / wall, units, wall, u1 / w1
 
 
 def host_cores() -> int:
@@ -212,11 +280,32 @@ def device_uuid(index: int) -> str | None:
 # ----------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------
-def build_propagator(precision, n_steps_cap, device=0, n_subsims=64):
+def benchmark_run(n_steps_cap, world=1, n_subsims=64):
+    """The benchmark's sub-simulations over `world` ranks (weak scaling: 64 per
+    rank).  Block 0 is the two-step run of 64 lattice-shifted 4^3 subgrids of
+    the 16^3 Monkhorst-Pack grid (Eq. 10); block j >= 1 is the same set with
+    every shift moved by h_j / 4, h_j the j-th Halton point (bases 2, 3, 5), i.e.
+    a 16^3 grid displaced by a fraction h_j of its spacing, so that the blocks
+    together form one larger two-step sample (Eq. 9)."""
+    import dataclasses
     import workloads as W
-    from paper_2112_00920_gb300 import Propagator, shifted_kpoints
+    from paper_2112_00920_gb300 import halton
     run = W.twostep_kick_run(n_steps=n_steps_cap)
-    run.subsims = run.subsims[:n_subsims]
+    base = run.subsims[:n_subsims]
+    subs = list(base)
+    if world > 1:
+        h = np.asarray(halton(world - 1)).reshape(world - 1, 3)
+        for j in range(1, world):
+            subs += [dataclasses.replace(sp, shift=tuple(float(v) for v in np.asarray(sp.shift) + h[j - 1] / 4.0))
+                     for sp in base]
+    run.subsims = subs
+    return run
+
+
+def build_propagator(precision, n_steps_cap, device=0, n_subsims=64, block=None, world=1):
+    from paper_2112_00920_gb300 import Propagator, shifted_kpoints
+    run = benchmark_run(n_steps_cap, world, n_subsims)
+    run.subsims = run.subsims[block[0]:block[1]] if block is not None else run.subsims[:n_subsims]
     cell = run.subsims[0].cell
     P = Propagator(precision, device=device)
     cid = P.add_cell_spec(cell)
@@ -227,7 +316,7 @@ def build_propagator(precision, n_steps_cap, device=0, n_subsims=64):
 STAGE_KERNEL = {
     "fp32": "k_stage_fused (z-march stencil + tensor-core projector contractions + Taylor accumulate), one launch "
             "per Taylor stage",
-    "fp32_tc": "k_stage_zf (z-march stencil + non-local term + Taylor accumulate)",
+    "fp32_tc": "k_stage_zb (z-march stencil + non-local term + Taylor accumulate)",
     "fp64": "k_stage (stencil + ket + Taylor accumulate)",
 }
 STEP_KERNEL = ("k_step_fused (the four Taylor stages of a time step in one launch: z-march stencil, tensor-core "
@@ -237,7 +326,7 @@ STEP_KERNEL = ("k_step_fused (the four Taylor stages of a time step in one launc
 # gradient pairs 3 axes x 4 x (2 + 4 + 2 + 4) = 144, q.grad 10, diagonal 3,
 # combination 4, (-i dt/m) 2, accumulation 2.
 FLOPS_LOCAL_PER_POINT_STAGE = 165
-FP32_LANES_PER_SM, N_SM = 128, 152
+FP32_LANES_PER_SM = 128
 # DRAM bytes of one k_step_fused launch from an ncu capture (dram__bytes_read.sum
 # + dram__bytes_write.sum) on the reduced workload (8 of the 64 subgrids, 8192
 # orbitals), scaled by the orbital count to the full workload.  Valid only for
@@ -254,17 +343,34 @@ def _file_sha1(path: str) -> str | None:
         return None
 
 
-def step_roofline(step_ms, n_orb, cell, elem, peaks, subsims, clocks):
+def alu_peaks(device):
+    """Measured FMA peaks of this GPU (tsbz_probe_alu_peak), TFLOP/s, with the
+    SM count and the nominal FP32 figure from the unit counts beside them."""
+    import torch
+    from paper_2112_00920_gb300._lib import probe_alu_peak
+    props = torch.cuda.get_device_properties(device)
+    out = {"sm_count": int(props.multi_processor_count)}
+    for kind, iters in (("ffma", 20000), ("ffma2", 10000), ("dfma", 300)):
+        f, ms = probe_alu_peak(device, kind, iters)
+        out[kind + "_tflops"] = f / 1e12
+        out[kind + "_ms"] = ms
+    return out
+
+
+def step_roofline(step_ms, n_orb, cell, elem, peaks, subsims, clocks, alu):
     """Roofline of k_step_fused.  It reads and writes psi once per step, so its
     HBM traffic is 2 arrays (plus P and Pa) and it is bound by its arithmetic
-    issue, not by HBM: the ALU roofline (FP32 lanes x 2 flop x max SM clock)
-    is the primary one, the HBM figures are given beside it."""
+    issue, not by HBM: the ALU roofline is the primary one, against the FP32
+    FMA peak measured on this GPU (the faster of the scalar and the packed
+    FP32x2 FMA probe); the HBM figures are given beside it."""
     npts = cell.n_pts
     n_proj = 4 * cell.n_atoms
     flops = 4.0 * FLOPS_LOCAL_PER_POINT_STAGE * npts * n_orb
     byts = float(n_orb) * (2 * elem * npts + 6 * n_proj * elem)
     mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = N_SM * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    nominal = alu["sm_count"] * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    best = "ffma2" if alu["ffma2_tflops"] >= alu["ffma_tflops"] else "ffma"
+    peak = alu[best + "_tflops"]
     achieved = flops / (step_ms / 1e3) / 1e12
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     gbs = byts / (step_ms / 1e3) / 1e9
@@ -275,8 +381,10 @@ def step_roofline(step_ms, n_orb, cell, elem, peaks, subsims, clocks):
     return {"kernel": STEP_KERNEL, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic, "algorithmic_flops_per_launch": flops,
             "algorithmic_bytes_per_launch": byts,
-            "peak_source": f"{N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {mhz:.0f} MHz "
-                           "(max SM clock, MEASURED_PEAKS.json)",
+            "peak_source": f"measured on this GPU: {best.upper()} probe (tsbz_probe_alu_peak), "
+                           f"{alu['sm_count']} SMs; nominal {alu['sm_count']} SMs x {FP32_LANES_PER_SM} FP32 "
+                           f"lanes x 2 flop x {mhz:.0f} MHz = {nominal:.1f} TFLOP/s",
+            "alu_peaks_measured": alu,
             "launches_per_step": 1,
             "hbm": {"achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)"},
@@ -313,12 +421,58 @@ def eps_check(precision, device):
     return float(np.max(np.abs(out[precision] - out["fp64"])) / np.max(np.abs(out["fp64"])))
 
 
-def stage_bytes_per_launch(elem: int, n_orb: int, npts: int) -> float:
+def stage_bytes_per_launch(elem: int, n_orb: int, npts: int, reads_v: bool = False) -> float:
     """Algorithmic DRAM bytes of the Taylor stage kernel, averaged over its
     four launches per step: m=1 reads t0 and writes t1 (2 arrays), m=2 and
     m=3 read t, read and write psi and write t (4 arrays), m=4 reads t and
-    reads and writes psi (3 arrays): 13 arrays / 4 launches."""
-    return 13.0 / 4.0 * elem * n_orb * npts
+    reads and writes psi (3 arrays): 13 arrays / 4 launches.  A stage kernel
+    that takes the non-local term V = V_NL t_{m-1} as an input array (the
+    dense tensor-core mode) also reads V in each launch: 17 arrays / 4."""
+    return (17.0 if reads_v else 13.0) / 4.0 * elem * n_orb * npts
+
+
+def stencil_roofline(device, n_subsims, hbm, peaks_src, steps=3):
+    """HBM roofline of the per-stage stencil kernel (stencil + local potential
+    + non-local input + Taylor accumulation, one launch per Taylor stage): the
+    dense tensor-core mode on the benchmark workload, whose stage kernel
+    (k_stage_zb) reads t_{m-1} and V and writes t_m and psi.  Events on the
+    launching stream around every stage launch (tsbz_get_timings)."""
+    import torch
+    import workloads as W
+    P, sids, run = build_propagator("fp32_tc", steps + 3, device=device, n_subsims=n_subsims)
+    cell = run.subsims[0].cell
+    psi = torch.from_numpy(W.plane_wave_orbitals(cell.a, cell.n, W.plane_wave_set(cell.n_bands), 64)).to(
+        f"cuda:{device}")
+    for sid in sids:
+        P.load_ground_state(sid, psi)
+    del psi
+    P.set_kick(-1, 0.005, (1.0, 0.0, 0.0))
+    P.propagate(1)
+    n_var = P.variant(0)[1]
+    per_variant = []
+    for v in range(n_var):
+        P.set_variant(0, v)
+        P.propagate(1)
+        P.set_profiling(True)
+        P.propagate(steps)
+        fam = P.timings()
+        P.set_profiling(False)
+        per_variant.append(fam["stage"] / (4 * steps))
+    P.close()
+    best = int(np.argmin(per_variant))
+    stage_ms = per_variant[best]
+    byts = stage_bytes_per_launch(8, run.n_orbitals, cell.n_pts, reads_v=True)
+    gbs = byts / (stage_ms / 1e3) / 1e9
+    names = ["k_stage_zb<false> (band of t_{m-1} bulk-copied to shared memory, V and psi read per plane)",
+             "k_stage_zb<true> (bands of t_{m-1}, V and psi bulk-copied to shared memory)",
+             "k_stage_zf (halo plane per z, two CTA barriers per plane)"]
+    return {"kernel": names[best] + ": one Taylor stage = FD stencil + local potential + non-local term V "
+                                    "(an input array) + Taylor accumulation",
+            "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "traffic": None,
+            "algorithmic_bytes_per_launch": byts, "ms_per_launch": stage_ms, "peak_source": peaks_src,
+            "variant": best, "ms_per_launch_by_variant": dict(zip(names[:n_var], per_variant)),
+            "note": "fp32_tc mode on the benchmark workload; 17 arrays of 2 GiB per 4 launches (t_{m-1} and V "
+                    "read by all 4, t_m written by 3, psi read and written by 3)"}
 
 
 def main():
@@ -331,9 +485,13 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--etrs-steps", type=int, default=3,
                     help="steps of the ETRS propagator timed on the same workload (0: skip)")
+    ap.add_argument("--stencil-steps", type=int, default=3,
+                    help="steps of the dense tensor-core mode timed for the per-stage stencil roofline (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-run", action="store_true",
                     help="run only the warm-up and timed steps (for profiler launch lists and captures)")
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="profiler runs: force this kernel variant of the cell (default: the library's default)")
     ap.add_argument("--subsims", type=int, default=64,
                     help="number of the 64 shifted subgrids to run (profiling of a reduced case)")
     ap.add_argument("--workload", default="twostep64", choices=["twostep64"] + sorted(SIDE_WORKLOADS),
@@ -357,11 +515,15 @@ def main():
     # CPU baseline first (before any CUDA context exists in this process)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        workers = max(1, min(host_cores(), 16))
-        units, wall = oracle_sample(workers, 1)
-        cpu = {"value": units / wall, "unit": UNIT, "cores": workers, "kind": "oracle",
-               "sample": f"{workers} sub-simulations x 1 step (64 k x 16 bands each, numpy complex128, "
-                         f"one process per core, BLAS 1 thread), {wall:.1f} s wall, {cpu_model()}"}
+        workers = host_cores()
+        val, units, wall, one_core = oracle_baseline(workers, steps=2)
+        cpu = {"value": val, "unit": UNIT, "cores": workers, "kind": "oracle",
+               "sample": f"{workers} of the 64 sub-simulations (64 k x 16 bands each, numpy complex128, one "
+                         f"process per host core, BLAS 1 thread) x 2 time steps after 1 untimed step: "
+                         f"{units} orbital-steps in {wall:.1f} s of propagate time (set-up, J(0-) and "
+                         f"J(0+) excluded); {cpu_model()}",
+               "one_core": {"value": one_core, "unit": UNIT,
+                            "sample": "1 sub-simulation x 1 time step, one process alone"}}
 
     import torch
     import torch.distributed as dist
@@ -376,42 +538,59 @@ def main():
     # room for the autotuner's trial steps (undone afterwards) within the step budget
     tune_room = 5 * 3 + 1
     cap = args.warmup + 2 * args.steps + 1 + tune_room
-    P, sids, run = build_propagator(args.precision, cap, device=local_rank, n_subsims=args.subsims)
-    cell = run.subsims[0].cell
-    n_orb = run.n_orbitals
-    gints = W.plane_wave_set(cell.n_bands)
-    psi_host = W.plane_wave_orbitals(cell.a, cell.n, gints, 64)
-    psi_dev = torch.from_numpy(psi_host).to(f"cuda:{local_rank}")
-    for sid in sids:
-        P.load_ground_state(sid, psi_dev)
-    P.set_kick(-1, 0.005, (1.0, 0.0, 0.0))
-    P.propagate(args.warmup)
-    # the autotuner picks each cell's kernel variant on this workload (trial steps undone);
-    # profiler runs keep the default variant so that their launch lists hold only the timed steps
-    n_tried = 0
-    if not args.profile_run:
-        n_tried = P.autotune(budget_ms=5000)
-    tuned_variant, tuned_n, tuned_ms = P.variant(0)
-    P.propagate(1)   # first step after tuning (forms the projections if the variant changed)
-    stream = torch.cuda.current_stream()
-    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    P.set_profiling(True)
-    l0 = P.launches()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local_rank, device_uuid(local_rank)) as clk:
-        start.record(stream)
-        P.propagate(args.steps)
-        end.record(stream)
+    # weak scaling: every rank advances its own block of 64 sub-simulations (the
+    # shifted subgrids are independent, Eq. 9); the ranks meet once, for the
+    # final two-step average of dJ (one all-reduce after the timed region)
+    from paper_2112_00920_gb300.distributed import run_sharded
+    P = sids = run = cell = n_orb = psi_host = psi_dev = n_tried = None
+    tuned_variant = tuned_n = tuned_ms = stream = ms = launches = fam = clk = J_avg = None
+
+    def run_block(b, e):
+        nonlocal P, sids, run, cell, n_orb, psi_host, psi_dev, n_tried
+        nonlocal tuned_variant, tuned_n, tuned_ms, stream, ms, launches, fam, clk, J_avg
+        P, sids, run = build_propagator(args.precision, cap, device=local_rank, n_subsims=args.subsims,
+                                        block=(b, e), world=world)
+        cell = run.subsims[0].cell
+        n_orb = run.n_orbitals
+        gints = W.plane_wave_set(cell.n_bands)
+        psi_host = W.plane_wave_orbitals(cell.a, cell.n, gints, 64)
+        psi_dev = torch.from_numpy(psi_host).to(f"cuda:{local_rank}")
+        for sid in sids:
+            P.load_ground_state(sid, psi_dev)
+        P.set_kick(-1, 0.005, (1.0, 0.0, 0.0))
+        P.propagate(args.warmup)
+        # the autotuner picks each cell's kernel variant on this workload (trial steps undone);
+        # profiler runs keep the default variant so that their launch lists hold only the timed steps
+        n_tried = 0
+        if not args.profile_run:
+            n_tried = P.autotune(budget_ms=5000)
+        elif args.variant >= 0:
+            P.set_variant(0, args.variant)
+        tuned_variant, tuned_n, tuned_ms = P.variant(0)
+        P.propagate(1)   # first step after tuning (forms the projections if the variant changed)
+        stream = torch.cuda.current_stream()
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        P.set_profiling(True)
+        l0 = P.launches()
+        if world > 1:
+            dist.barrier()
         torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    ms = start.elapsed_time(end)
-    launches = P.launches() - l0
-    fam = P.timings()
-    P.set_profiling(False)
-    J_avg, _ = P.current(-1)
+        with ClockSampler(local_rank, device_uuid(local_rank)) as clk:
+            start.record(stream)
+            P.propagate(args.steps)
+            end.record(stream)
+            torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        ms = start.elapsed_time(end)
+        launches = P.launches() - l0
+        fam = P.timings()
+        P.set_profiling(False)
+        J_avg, _ = P.current(-1)
+        return J_avg * (e - b)
+
+    n_global = args.subsims * world
+    J_two_step, block = run_sharded([1.0] * n_global, run_block)
     ms_t = torch.tensor([ms], device=f"cuda:{local_rank}")
     if world > 1:
         dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
@@ -431,15 +610,17 @@ def main():
     whole = args.precision == "fp32" and variant == 0 and n_var == 3
     fam_ms = {k: v / args.steps for k, v in fam.items()}
     if whole:
-        roof = step_roofline(fam["stage"] / args.steps, n_orb, cell, elem, peaks, args.subsims, clk.summary())
+        roof = step_roofline(fam["stage"] / args.steps, n_orb, cell, elem, peaks, args.subsims, clk.summary(),
+                             alu_peaks(local_rank))
     else:
         stage_ms = fam["stage"] / (4 * args.steps)
-        bytes_launch = stage_bytes_per_launch(elem, n_orb, cell.n_pts)
+        bytes_launch = stage_bytes_per_launch(elem, n_orb, cell.n_pts, reads_v=args.precision == "fp32_tc")
         achieved = bytes_launch / (stage_ms / 1e3) / 1e9
         roof = {"kernel": STAGE_KERNEL[args.precision], "bound": "hbm", "achieved": achieved,
                 "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
                 "algorithmic_bytes_per_launch": bytes_launch,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)" if peaks else "fallback 6.8 TB/s"}
+    hbm_src = "MEASURED_PEAKS.json hbm_gbs (burst copy)" if peaks else "fallback 6.8 TB/s"
     roof["family_ms_per_step"] = fam_ms
 
     if args.profile_run:
@@ -477,6 +658,10 @@ def main():
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t_e2e
     P2.close()
+    if world > 1:
+        e2e_t = torch.tensor([e2e_s], device=f"cuda:{local_rank}")
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+        e2e_s = float(e2e_t.item())
     e2e = {"value": n_orb * args.steps * world / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": int(psi_host.nbytes * len(sids2) / args.steps),
            "d2h_bytes_per_step": int(J_e2e.nbytes / max(args.steps, 1)),
@@ -513,6 +698,11 @@ def main():
                 "ms_per_step": etrs_ms / args.etrs_steps,
                 "propagator": "ETRS: Taylor-4 predictor for rho(t+dt), then two Taylor-4 half steps"}
 
+    # the per-stage stencil kernel of the dense tensor-core mode, HBM roofline
+    stencil = None
+    if args.stencil_steps > 0:
+        stencil = stencil_roofline(local_rank, args.subsims, hbm, hbm_src, steps=args.stencil_steps)
+
     # plain FP64 GPU path on the same workload (comparison)
     fp64 = None
     if args.precision != "fp64" and args.fp64_steps > 0:
@@ -548,8 +738,9 @@ def main():
                                                    "with fp32 accumulation; fp64 rho/J/Hartree",
                                         "fp64": "fp64 throughout"}[args.precision],
                           "l2": "inputs larger than L2 (psi 2 GiB in fp32), no flush needed",
-                          "parallelism": f"replica x{world} (independent shifts per GPU)"},
-               "roofline": roof, "e2e": e2e, "gpu_launches": launches,
+                          "parallelism": f"shift blocks x{world} (64 independent sub-simulations per GPU, "
+                                         "one final all-reduce of dJ)"},
+               "roofline": roof, "roofline_stencil": stencil, "e2e": e2e, "gpu_launches": launches,
                "graph_replay_value": graph_value,
                "autotune": {"variant": tuned_variant, "n_variants": tuned_n, "variants_timed": n_tried,
                             "ms_per_step": tuned_ms,
@@ -562,7 +753,8 @@ def main():
                "eps_check": "cell A (16^3 grid), MP 2^3, plane-wave start, kick 0.005 x, 600 steps, "
                             "eps over 0.1-20 eV vs the FP64 GPU path (FP64 GPU vs oracle: err_J <= 1e-10)",
                "fp32_over_fp64": (value / world / fp64["value"]) if fp64 else None,
-               "two_step_dJx_last": float(J_avg[-1, 0])}
+               "two_step_dJx_last": float(J_two_step[-1, 0]),
+               "two_step_subsims": n_global}
         if cpu is not None:
             out["cpu_baseline"] = cpu
         print(json.dumps(out))
@@ -578,6 +770,9 @@ SIDE_WORKLOADS = {
                   "MP grid (8 k-points), kick 0.005 along x, default kernel variant",
     "uneven": "uneven batch: 18 8-atom 16^3 cells and 2 32^3 supercells with 2^3..6^3 shifted subgrids, "
               "kicks 1e-4..1e-2, autotuned (20 s budget)",
+    "hhg": "two-step HHG run: 8 shifted 8^3 subgrids of the 8-atom 16^3 cell (4096 k, 65 536 orbitals), the "
+           "sin^4 pulse of Eq. 15 along z (E0 0.005, w0 0.057, T 1654), dt 0.04, self-consistent v_Hxc, "
+           "plane-wave start; A(t) changes every step, timed from the middle of the pulse",
 }
 
 
@@ -588,9 +783,13 @@ def run_side_workload(args):
     build_library()
     cap = args.warmup + args.steps + 40
     P = Propagator(args.precision)
+    t_start = 0
     if args.workload == "cell-b-mp2":
         cb = W.cell_b()
         subs = [W.SubsimSpec(cb, (2, 2, 2), (0.5, 0.5, 0.5), 0.08, cap, W.Kick(k0=0.005))]
+    elif args.workload == "hhg":
+        subs = W.twostep_hhg_run().subsims
+        t_start = int(round(0.5 * subs[0].field.t_pulse / subs[0].dt))   # middle of the pulse
     else:
         subs = W.uneven_batch_run(n_a=18, n_b=2, max_steps=cap).subsims
     cells, sids, n_orb, n_pb = {}, [], 0, 0
@@ -604,7 +803,13 @@ def run_side_workload(args):
         psi = torch.from_numpy(W.plane_wave_orbitals(c.a, c.n, W.plane_wave_set(c.n_bands), nk)).cuda()
         P.load_ground_state(sid, psi)
         del psi
-        P.set_kick(sid, s.field.k0, s.field.direction)
+        if isinstance(s.field, W.Pulse):
+            from paper_2112_00920_gb300 import pulse_samples
+            f = s.field
+            a = pulse_samples(f.e0, f.omega0, f.t_pulse, f.direction, s.dt, t_start + cap)
+            P.set_field(sid, a[2 * t_start:])
+        else:
+            P.set_kick(sid, s.field.k0, s.field.direction)
         n_orb += nk * c.n_bands
         n_pb += nk * c.n_bands * c.n_pts
     P.propagate(args.warmup)
@@ -616,34 +821,55 @@ def run_side_workload(args):
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    l0 = P.launches()
     e0.record(stream)
     P.propagate(args.steps)
     e1.record(stream)
     torch.cuda.synchronize()
+    lps = (P.launches() - l0) / args.steps
     ms = e0.elapsed_time(e1) / args.steps
     fam = {k: v / args.steps for k, v in P.timings().items()}
-    print(json.dumps({"workload": args.workload, "description": SIDE_WORKLOADS[args.workload],
-                      "precision": args.precision, "steps": args.steps, "warmup": args.warmup,
-                      "ms_per_step": ms, "orbital_steps_per_s": n_orb / (ms / 1e3),
-                      "point_band_steps_per_s": n_pb / (ms / 1e3), "family_ms_per_step": fam,
-                      "variants": {name: P.variant(cid) for name, cid in cells.items()},
-                      "variants_timed": tuned}))
+    out = {"workload": args.workload, "description": SIDE_WORKLOADS[args.workload],
+           "precision": args.precision, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms, "orbital_steps_per_s": n_orb / (ms / 1e3),
+           "point_band_steps_per_s": n_pb / (ms / 1e3), "family_ms_per_step": fam,
+           "variants": {name: P.variant(cid) for name, cid in cells.items()},
+           "variants_timed": tuned, "launches_per_step": lps}
+    if args.workload == "hhg" and args.precision == "fp32":
+        v = P.variant(cells[subs[0].cell.name])
+        if v[0] == 0 and v[1] == 3:
+            peaks = {}
+            try:
+                peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+            except OSError:
+                pass
+            out["roofline"] = step_roofline(fam["stage"], n_orb, subs[0].cell, 8, peaks, 0, {},
+                                            alu_peaks(torch.cuda.current_device()))
+    print(json.dumps(out))
     P.close()
 
 
 def run_reference(args):
-    workers = max(1, min(host_cores(), 16))
-    for _ in range(args.warmup):
-        oracle_sample(workers, 1)
-    units = 0
-    wall = 0.0
-    for _ in range(args.steps):
-        u, w = oracle_sample(workers, 1)
-        units += u
-        wall += w
+    """The CPU oracle on this host's cores: one process per core, each holding
+    one sub-simulation of the benchmark workload; a bench step is one time
+    step of all of them (propagate time only)."""
+    workers = host_cores()
+    pool = OraclePool(workers, args.warmup + args.steps)
+    try:
+        for _ in range(args.warmup):
+            pool.step(1)
+        units = 0
+        wall = 0.0
+        for _ in range(args.steps):
+            u, w = pool.step(1)
+            units += u
+            wall += w
+    finally:
+        pool.close()
     value = units / wall
-    sample = (f"per step: {workers} sub-simulations x 1 time step (64 k x 16 bands each) with the numpy "
-              f"complex128 oracle, one process per core; {cpu_model()}")
+    sample = (f"per step: {workers} of the 64 sub-simulations (64 k x 16 bands each) x 1 time step with the "
+              f"numpy complex128 oracle, one process per host core, BLAS 1 thread, propagate time only; "
+              f"{cpu_model()}")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",

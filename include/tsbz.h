@@ -270,6 +270,18 @@ int tsbz_set_variant(tsbz_ctx* ctx, int cell_id, int variant);
  * *status_out (nullable) receives the kernel's status word. */
 int tsbz_selftest_bounded_wait(int device, int polls, int deliver, int* status_out);
 
+/* Arithmetic throughput probe (instrumentation; the paper has no counterpart):
+ * the peak rate of fused multiply-adds on `device`, against which the
+ * ALU-bound kernels of this library are measured.  kind 0 = FP32 FMA,
+ * 1 = packed FP32x2 FMA (two FMAs per instruction), 2 = FP64 FMA.  One
+ * untimed launch of a grid that fills every SM with independent FMA chains,
+ * then the fastest of three timed launches (CUDA events); `iters` (1 .. 2^24)
+ * sets the work per launch (64 FMAs per chain and iteration, 8 chains per
+ * thread).  *flops_per_s receives 2 x FMAs / second, *ms_out (nullable) the
+ * launch time.  Synchronous; uses the legacy default stream and a small
+ * device allocation.  Returns TSBZ_OK, TSBZ_EINVAL, TSBZ_ENOMEM or TSBZ_ECUDA. */
+int tsbz_probe_alu_peak(int device, int kind, int iters, double* flops_per_s, double* ms_out);
+
 const char* tsbz_last_error(tsbz_ctx* ctx);
 void tsbz_destroy(tsbz_ctx* ctx);
 
@@ -306,7 +318,10 @@ int tsbz_pulse_samples(double e0, double w0, double t_pulse, const double dir[3]
  *  - Work is queued on cuda_stream (NULL = legacy default stream); the call
  *    returns without synchronising.  The first call on a device looks up the
  *    buffer's device address once for that device; make that first call
- *    before any stream capture.
+ *    before any stream capture.  The address stays cached for the life of
+ *    the process: after a cudaDeviceReset (or any reset of the device's
+ *    primary context) the cached address is stale, so do not call this
+ *    entry point again in that process.
  *  - All calls share the one buffer: calls that overlap on the GPU (other
  *    streams, other threads) race and must be serialised by the caller.
  *  - Returns TSBZ_OK, TSBZ_EINVAL or TSBZ_ECUDA. */

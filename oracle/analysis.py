@@ -67,6 +67,10 @@ def dielectric_statistics(dj_components, dt, k0, omegas, t_w=None):
 
 
 def hhg_spectrum(j_component, dt, t_pulse, omegas):
+    """Eqs. 16-17: I(w) = w^2 |dt sum_n w_n e^{i w t_n} W(t_n) J(t_n)|^2 with
+    W(t) = sin^4(pi t/T_L) on (0, T_L), zero elsewhere, trapezoid weights w_n
+    and t_n = n dt.  Pinned by closed-form transforms of sinusoidal currents
+    (tests/test_oracle_analysis.py)."""
     n1 = j_component.shape[0]
     t = np.arange(n1) * dt
     win = np.where((t > 0) & (t < t_pulse), np.sin(np.pi * t / t_pulse) ** 4, 0.0)

@@ -94,6 +94,7 @@ _SIGS = {
     "tsbz_get_variant": ([ctypes.c_void_p, ctypes.c_int, _I, _I, _D, ctypes.c_int], ctypes.c_int),
     "tsbz_set_variant": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "tsbz_selftest_bounded_wait": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, _I], ctypes.c_int),
+    "tsbz_probe_alu_peak": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D], ctypes.c_int),
     "tsbz_last_error": ([ctypes.c_void_p], ctypes.c_char_p),
     "tsbz_destroy": ([ctypes.c_void_p], None),
     "tsbz_shifted_kpoints": ([_D, _I, _D, _D, ctypes.c_size_t], ctypes.c_int),
@@ -167,6 +168,18 @@ def selftest_bounded_wait(device: int = 0, polls: int = 1000, deliver: bool = Fa
     return rc, st.value
 
 
+def probe_alu_peak(device: int, kind: str, iters: int = 20000):
+    """Peak FMA throughput of the device (tsbz_probe_alu_peak): kind "ffma"
+    (FP32), "ffma2" (packed FP32x2) or "dfma" (FP64).  Returns (flop/s, ms)."""
+    lib = load()
+    k = {"ffma": 0, "ffma2": 1, "dfma": 2}[kind]
+    f, ms = ctypes.c_double(), ctypes.c_double()
+    rc = lib.tsbz_probe_alu_peak(int(device), k, int(iters), ctypes.byref(f), ctypes.byref(ms))
+    if rc:
+        raise TsbzError(rc, "tsbz_probe_alu_peak")
+    return f.value, ms.value
+
+
 def density_noalloc(psi, occ, rho=None, stream=None):
     """rho(r) = (1/n_k) sum_k sum_b occ |u(r)|^2 of a complex128 CUDA tensor
     psi (n_k, n_b, n3, n2, n1), through tsbz_density_noalloc: the library
@@ -179,11 +192,15 @@ def density_noalloc(psi, occ, rho=None, stream=None):
     n_k, n_b, n3, n2, n1 = psi.shape
     if rho is None:
         rho = torch.empty((n3, n2, n1), dtype=torch.float64, device=psi.device)
-    if stream is None:
-        stream = torch.cuda.current_stream(psi.device).cuda_stream
-    nn = (ctypes.c_int * 3)(n1, n2, n3)
-    rc = lib.tsbz_density_noalloc(ctypes.c_void_p(psi.data_ptr()), n_k, n_b, nn, float(occ),
-                                  ctypes.c_void_p(rho.data_ptr()), ctypes.c_void_p(stream))
+    assert rho.device == psi.device and rho.dtype == torch.float64 and rho.is_contiguous()
+    assert rho.numel() == n3 * n2 * n1
+    # the library looks up its static buffer on the current device: make it psi's
+    with torch.cuda.device(psi.device):
+        if stream is None:
+            stream = torch.cuda.current_stream(psi.device).cuda_stream
+        nn = (ctypes.c_int * 3)(n1, n2, n3)
+        rc = lib.tsbz_density_noalloc(ctypes.c_void_p(psi.data_ptr()), n_k, n_b, nn, float(occ),
+                                      ctypes.c_void_p(rho.data_ptr()), ctypes.c_void_p(stream))
     if rc:
         raise TsbzError(rc, "tsbz_density_noalloc")
     return rho

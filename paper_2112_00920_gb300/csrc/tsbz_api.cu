@@ -735,10 +735,13 @@ int sync_and_check(tsbz_ctx* ctx) {
 //   point-parallel path (FP64, and FP32 on shapes without a z-march kernel):
 //     bands per staged projection chunk 8 (0), 4 (1), 16 (2, when its shared
 //     memory fits);
+//   FP32_TC on 16^3 grids: stage with the band of t bulk-staged in shared
+//     memory and V, psi read per plane (0) or bulk-staged too (1), z-march
+//     stage with a halo plane per z (2);
 //   everything else: one variant.
 int n_variants(const tsbz_ctx* ctx, const HostCell& hc) {
   const CellDev& c = hc.dev;
-  if (ctx->precision == TSBZ_FP32_TC) return 1;
+  if (ctx->precision == TSBZ_FP32_TC) return (c.n1 == 16 && c.n2 == 16 && c.n3 == 16) ? 3 : 1;
   if (ctx->precision == TSBZ_FP32 && sep_supported(c)) return sep_variants(c);
   const size_t big = (size_t)16 * (c.n_proj > 0 ? c.n_proj : 1) * ctx->elem_size();
   return big <= 160 * 1024 ? 3 : 2;

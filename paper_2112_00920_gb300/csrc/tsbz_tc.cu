@@ -31,8 +31,25 @@ void launch_ket_tc(const LaunchSet& L, const void* P, void* V, void* stream) {
 void launch_stage_v(const LaunchSet& L, const void* tin, void* tout, void* psi, const void* V, int m, void* stream) {
   if (L.n_units == 0) return;
   const int n12 = L.cell.n1 * L.cell.n2;
+  if (L.cell.n1 == ZB_N && L.cell.n2 == ZB_N && L.cell.n3 == ZB_N && L.variant < 2) {
+    // band of t_{m-1} (variant 1: with V and psi) bulk-staged in shared memory, barrier-free z-march
+    static bool zb_attr = false;
+    if (!zb_attr) {
+      cudaFuncSetAttribute(k_stage_zb<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 + 3 * ZB_N * ZB_NP * 8);
+      cudaFuncSetAttribute(k_stage_zb<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 + ZB_N * ZB_NP * 8);
+      zb_attr = true;
+    }
+    dim3 grid(L.cell.n_bands, L.n_units);
+    if (L.variant == 1)
+      k_stage_zb<true><<<grid, ZB_NP, 128 + 3 * ZB_N * ZB_NP * sizeof(float2), (cudaStream_t)stream>>>(
+          L, (const float2*)tin, (float2*)tout, (float2*)psi, (const float2*)V, m);
+    else
+      k_stage_zb<false><<<grid, ZB_NP, 128 + ZB_N * ZB_NP * sizeof(float2), (cudaStream_t)stream>>>(
+          L, (const float2*)tin, (float2*)tout, (float2*)psi, (const float2*)V, m);
+    return;
+  }
   if (n12 <= 256 && L.cell.n3 == 16) {
-    // 2.5-D z-march, depth 16 unrolled, packed arithmetic
+    // 2.5-D z-march, depth 16 unrolled, packed arithmetic, halo plane per z
     const int threads = ((n12 + 31) / 32) * 32;
     dim3 grid(L.cell.n_bands, L.n_units);
     const size_t pad = (size_t)(L.cell.n1 + 2 * TC_ND) * (L.cell.n2 + 2 * TC_ND) * sizeof(float2);

@@ -1,4 +1,4 @@
-// Tensor-core projector contractions (split-BF16, FP32 accumulate) and the
+// Tensor-core projector contractions (scaled split-FP16, FP32 accumulate) and the
 // fused Taylor stage of the single-precision tensor-core mode.
 //
 // Projector values of one k-point, C_j(r) = conj(beta~_j(r)) = pnorm_j F_x F_y F_z w_j,
@@ -18,15 +18,15 @@
 //        with Wt built from W = E P so that V[pt][b] = Re V_b, V[pt][16+b] = Im V_b.
 // Limits of this mode per cell: bands <= 16, projectors <= 32, grid edges <= 32.
 #pragma once
-#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "tsbz_bulk.cuh"
 #include "tsbz_internal.h"
 #include "tsbz_zmarch.cuh"
 
-#define TC_W_PITCH 72      // bf16 per Wt row
+#define TC_W_PITCH 72      // FP16 values per Wt row
 #define TC_D_PITCH 33      // floats per row of the final bra combination
 #define TC_ND 4            // stencil half-width of the fused stage
 #define TC_NMAX 32         // largest grid edge
@@ -49,9 +49,9 @@ __device__ __forceinline__ void tc_split2(float x, float y, uint32_t& hi, uint32
   lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
-__device__ __forceinline__ uint32_t tc_ld32(const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+__device__ __forceinline__ uint32_t tc_ld32(const __half* p) { return *reinterpret_cast<const uint32_t*>(p); }
 
-__device__ __forceinline__ void tc_st16(__nv_bfloat16* p, uint32_t bits) {
+__device__ __forceinline__ void tc_st16(__half* p, uint32_t bits) {
   *reinterpret_cast<unsigned short*>(p) = (unsigned short)(bits & 0xFFFFu);
 }
 
@@ -63,7 +63,7 @@ __device__ __forceinline__ void tc_mma(float (&d)[4], const uint32_t (&a)[4], ui
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-__device__ __forceinline__ void tc_ldsm_x4_trans(uint32_t (&r)[4], const __nv_bfloat16* row_ptr) {
+__device__ __forceinline__ void tc_ldsm_x4_trans(uint32_t (&r)[4], const __half* row_ptr) {
   const uint32_t addr = (uint32_t)__cvta_generic_to_shared(row_ptr);
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
@@ -77,14 +77,14 @@ __device__ __forceinline__ void tc_ldsm_x4_trans(uint32_t (&r)[4], const __nv_bf
 // synchronisation only; CTA barriers occur once, in the final reduction.
 // ============================================================================
 #define TW_PTS 16          // points per warp step
-#define TW_CPITCH 72       // bf16 per projector row (64 + 8)
-#define TW_TPITCH 24       // bf16 per orbital row (16 + 8)
+#define TW_CPITCH 72       // FP16 values per projector row (64 + 8)
+#define TW_TPITCH 24       // FP16 values per orbital row (16 + 8)
 
 struct TwTile {
-  __nv_bfloat16 c_hi[TW_PTS * TW_CPITCH];
-  __nv_bfloat16 c_lo[TW_PTS * TW_CPITCH];
-  __nv_bfloat16 t_hi[32 * TW_TPITCH];
-  __nv_bfloat16 t_lo[32 * TW_TPITCH];
+  __half c_hi[TW_PTS * TW_CPITCH];
+  __half c_lo[TW_PTS * TW_CPITCH];
+  __half t_hi[32 * TW_TPITCH];
+  __half t_lo[32 * TW_TPITCH];
 };
 
 struct TwSmem {
@@ -92,8 +92,8 @@ struct TwSmem {
   float2 fac[TC_NA * 3 * TC_NMAX];
   float dis[TC_NA * 3 * TC_NMAX];
   float pn[TC_NA * 4];
-  __nv_bfloat16 wk_hi[32 * TC_W_PITCH];
-  __nv_bfloat16 wk_lo[32 * TC_W_PITCH];
+  __half wk_hi[32 * TC_W_PITCH];
+  __half wk_lo[32 * TC_W_PITCH];
 };
 
 __device__ __forceinline__ void tw_load_tables(TwSmem& sm, const CellDev& c, const float2* ph) {
@@ -188,8 +188,8 @@ __device__ __forceinline__ void tw_bra_step(const TwTile& wt, float (&acc)[4][4]
   uint32_t bh[4][2], bl[4][2];
 #pragma unroll
   for (int nt = 0; nt < 4; ++nt) {
-    const __nv_bfloat16* ph = wt.t_hi + (8 * nt + g) * TW_TPITCH + 2 * t;
-    const __nv_bfloat16* pl = wt.t_lo + (8 * nt + g) * TW_TPITCH + 2 * t;
+    const __half* ph = wt.t_hi + (8 * nt + g) * TW_TPITCH + 2 * t;
+    const __half* pl = wt.t_lo + (8 * nt + g) * TW_TPITCH + 2 * t;
     bh[nt][0] = tc_ld32(ph);
     bh[nt][1] = tc_ld32(ph + 8);
     bl[nt][0] = tc_ld32(pl);
@@ -479,6 +479,140 @@ __global__ void __launch_bounds__(256, 4) k_stage_zf(LaunchSet L, const float2* 
     v_cur = v_nxt;
     p_cur = p_nxt;
     e_cur = e_nxt;
+  }
+}
+
+// ----------------------------------------------------------------------------
+// The same Taylor stage on 16^3 grids with the band of t_{m-1} staged in
+// shared memory by bulk copies (issued by one thread at the start of the CTA,
+// completed on one mbarrier with a bounded wait), so that the z-march runs
+// without a CTA barrier: x and y neighbours are shared-memory loads at
+// per-thread addresses plus compile-time plane offsets, z neighbours a
+// register queue.  VP = true stages the bands of V = V_NL t_{m-1} and (m >= 2)
+// psi in shared memory as well (96 KiB: the CTA's whole input in flight at
+// once, 2 CTAs per SM); VP = false reads them per plane from global memory,
+// two planes ahead (32 KiB of shared memory, 3 CTAs per SM).  Algorithmic
+// bytes per launch: t_{m-1} and V read; t_m written (m < 4); psi read and
+// written (m >= 2).  Same arithmetic per point as k_stage_zf.
+// ----------------------------------------------------------------------------
+#define ZB_N 16
+#define ZB_NP 256
+
+template <bool VP>
+__global__ void __launch_bounds__(ZB_NP, VP ? 2 : 3) k_stage_zb(LaunchSet L, const float2* __restrict__ tin,
+                                                               float2* __restrict__ tout, float2* __restrict__ psi,
+                                                               const float2* __restrict__ V, int m) {
+  constexpr int ND = TC_ND, N = ZB_N, NP = ZB_NP;
+  extern __shared__ __align__(128) unsigned char zbraw[];
+  unsigned long long* mbar = reinterpret_cast<unsigned long long*>(zbraw);
+  float2* st = reinterpret_cast<float2*>(zbraw + 128);
+  float2* sv = st + N * NP;
+  float2* sp = sv + N * NP;
+  const CellDev& c = L.cell;
+  const int b = blockIdx.x;
+  const int u = L.unit_ids[blockIdx.y];
+  if (!unit_active(L, u)) return;
+  const UnitDev U = L.units[u];
+  const SubDev S = L.subs[U.sub];
+  const int col = threadIdx.x, ix = col & (N - 1), iy = col / N;
+  const long long base = U.psi_off + (long long)b * (N * NP);
+  const uint32_t bar = bk_smem(mbar);
+  constexpr uint32_t band_bytes = (uint32_t)(N * NP * sizeof(float2));
+  if (col == 0) {
+    bk_mbar_init(bar, 1);
+    bk_mbar_expect_tx(bar, band_bytes * (VP ? (m >= 2 ? 3u : 2u) : 1u));
+    bk_copy_g2s(bk_smem(st), tin + base, band_bytes, bar);
+    if (VP) {
+      bk_copy_g2s(bk_smem(sv), V + base, band_bytes, bar);
+      if (m >= 2) bk_copy_g2s(bk_smem(sp), psi + base, band_bytes, bar);
+    }
+  }
+  const float2 zero = make_float2(0.f, 0.f);
+  const float2* gv = V + base + col;
+  const float2* gp = psi + base + col;
+  float2 vq[2], pq[2];   // V and psi of the next two planes (VP = false)
+  if (!VP) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      vq[k] = gv[k * NP];
+      pq[k] = m >= 2 ? gp[k * NP] : zero;
+    }
+  }
+  const float2* cz = st + col;
+  const float2* xp[ND];
+  const float2* xm[ND];
+  const float2* yp[ND];
+  const float2* ym[ND];
+#pragma unroll
+  for (int mm = 1; mm <= ND; ++mm) {
+    xp[mm - 1] = st + iy * N + ((ix + mm) & (N - 1));
+    xm[mm - 1] = st + iy * N + ((ix - mm) & (N - 1));
+    yp[mm - 1] = st + ((iy + mm) & (N - 1)) * N + ix;
+    ym[mm - 1] = st + ((iy - mm) & (N - 1)) * N + ix;
+  }
+  const float* qt = reinterpret_cast<const float*>(L.qt_half) + 4 * u;
+  const float q0 = qt[0], q1 = qt[1], q2 = qt[2];
+  const float dg0 = c.hlapf[0][0] + c.hlapf[1][0] + c.hlapf[2][0] + qt[3];
+  const float hdt = (float)(S.dt * L.dt_scale) / (float)m;
+  const float* veff = reinterpret_cast<const float*>(S.veff) + col;
+  __syncthreads();   // the barrier is initialised before anyone polls it
+  const bool ok = bk_mbar_wait(bar, 0, BK_WAIT_POLLS);
+  if (!__syncthreads_and(ok)) {
+    if (col == 0) {
+      atomicOr(S.status, BK_STATUS_TIMEOUT);
+      bk_mbar_wait(bar, 0, BK_WAIT_POLLS);   // let the copies in flight land before the CTA exits
+    }
+    return;
+  }
+  const float2 neg1 = make_float2(-1.f, -1.f);
+  float2 qv[N + 2 * ND];   // t(z) for z = -ND .. N - 1 + ND (periodic)
+#pragma unroll
+  for (int k = 0; k < 2 * ND; ++k) qv[k] = cz[((k - ND + N) & (N - 1)) * NP];
+  float2* to = tout + base + col;
+  float2* po = psi + base + col;
+#pragma unroll
+  for (int z = 0; z < N; ++z) {
+    qv[z + 2 * ND] = cz[((z + ND) & (N - 1)) * NP];
+    float2 vz, pz;
+    if (VP) {
+      vz = sv[z * NP + col];
+      pz = m >= 2 ? sp[z * NP + col] : zero;
+    } else {
+      vz = vq[z & 1];
+      pz = pq[z & 1];
+      if (z + 2 < N) {
+        vq[z & 1] = gv[(z + 2) * NP];
+        pq[z & 1] = m >= 2 ? gp[(z + 2) * NP] : zero;
+      }
+    }
+    const float2 ce = qv[z + ND];
+    const float dg = dg0 + veff[z * NP];
+    float2 h = __fmul2_rn(make_float2(dg, dg), ce);
+    float2 gx = zero, gy = zero, gz = zero;
+#pragma unroll
+    for (int mm = 1; mm <= ND; ++mm) {
+      const float2 xu = xp[mm - 1][z * NP], xd = xm[mm - 1][z * NP];
+      const float2 yu = yp[mm - 1][z * NP], yd = ym[mm - 1][z * NP];
+      const float2 zu = qv[z + ND + mm], zd = qv[z + ND - mm];
+      h = f2fma(c.hlap2[0][mm], __fadd2_rn(xu, xd), h);
+      h = f2fma(c.hlap2[1][mm], __fadd2_rn(yu, yd), h);
+      h = f2fma(c.hlap2[2][mm], __fadd2_rn(zu, zd), h);
+      gx = f2fma(c.gradw2[0][mm], f2fma(neg1, xd, xu), gx);
+      gy = f2fma(c.gradw2[1][mm], f2fma(neg1, yd, yu), gy);
+      gz = f2fma(c.gradw2[2][mm], f2fma(neg1, zd, zu), gz);
+    }
+    float2 qg = __fmul2_rn(make_float2(q0, q0), gx);
+    qg = f2fma(make_float2(q1, q1), gy, qg);
+    qg = f2fma(make_float2(q2, q2), gz, qg);
+    const float hr = h.x + qg.y + vz.x;
+    const float hi = h.y - qg.x + vz.y;
+    const float2 t = make_float2(hdt * hi, -hdt * hr);
+    if (m < 4) to[z * NP] = t;
+    if (m == 2) {
+      po[z * NP] = __fadd2_rn(pz, __fadd2_rn(ce, t));
+    } else if (m >= 3) {
+      po[z * NP] = __fadd2_rn(pz, t);
+    }
   }
 }
 

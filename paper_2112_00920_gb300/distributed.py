@@ -55,3 +55,24 @@ def two_step_average(dj_sum, n_local: int, group=None):
     dist.all_reduce(buf, op=dist.ReduceOp.SUM, group=group)
     out = buf.cpu().numpy()
     return out[:-1].reshape(local.shape) / out[-1]
+
+
+def rank_world(group=None):
+    """(rank, world size) of the process group, (0, 1) without one."""
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        return dist.get_rank(group), dist.get_world_size(group)
+    return 0, 1
+
+
+def run_sharded(costs, run_block, group=None):
+    """The two-step scheme over ranks: this rank runs its cost-balanced block
+    [begin, end) of the sub-simulations through run_block(begin, end), which
+    returns the sum over the block of dJ_m(t) as an (n_t, 3) array, and the
+    ranks then form the average over all sub-simulations (Eq. 9) with one
+    all-reduce.  Returns (average dJ (n_t, 3), (begin, end))."""
+    rank, world = rank_world(group)
+    begin, end = shard_ranges(costs, world)[rank]
+    dj_sum = run_block(begin, end)
+    return two_step_average(dj_sum, end - begin, group), (begin, end)
+

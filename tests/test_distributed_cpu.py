@@ -47,13 +47,21 @@ def _per_shift_dj():
 
 def _worker(rank, world, port, dj_all, q):
     import torch.distributed as dist
-    from paper_2112_00920_gb300.distributed import shard_ranges, two_step_average
+    from paper_2112_00920_gb300.distributed import run_sharded
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
-    b, e = shard_ranges([1.0] * dj_all.shape[0], world)[rank]
-    avg = two_step_average(dj_all[b:e].sum(axis=0), e - b)
-    q.put((rank, avg))
+    seen = []
+
+    def run_block(b, e):
+        # the benchmark propagates its block through the library here; the test
+        # takes the oracle's per-shift currents of the block
+        seen.append((b, e))
+        return dj_all[b:e].sum(axis=0)
+
+    avg, block = run_sharded([1.0] * dj_all.shape[0], run_block)
+    assert seen == [block]
+    q.put((rank, avg, block))
     dist.destroy_process_group()
 
 
@@ -71,5 +79,7 @@ def test_two_step_average_across_two_gloo_ranks():
         p.join(timeout=60)
         assert p.exitcode == 0
     ref = dj_all.mean(axis=0)
-    for _, avg in res:
+    blocks = sorted(r[2] for r in res)
+    assert blocks[0][0] == 0 and blocks[0][1] == blocks[1][0] and blocks[1][1] == dj_all.shape[0]
+    for _, avg, _ in res:
         np.testing.assert_allclose(avg, ref, rtol=0, atol=1e-15 * np.max(np.abs(ref)) + 1e-20)

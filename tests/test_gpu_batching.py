@@ -13,12 +13,10 @@ import pytest
 import workloads as W
 from oracle.cell import Grid
 
-from gpu_common import FP64_J_TOL, FP64_RHO_TOL, compare, oracle_run, random_subsim
+from gpu_common import FP32_J_TOL, FP32_RHO_TOL, FP64_J_TOL, FP64_RHO_TOL, compare, oracle_run, random_subsim
 
 pytestmark = pytest.mark.gpu
-
-FP32_J_TOL, FP32_RHO_TOL = 1e-4, 1e-5
-BARS = {"fp64": (FP64_J_TOL, FP64_RHO_TOL), "fp32": (FP32_J_TOL, FP32_RHO_TOL)}
+BARS = {"fp64": (FP64_J_TOL, FP64_RHO_TOL), "fp32": (FP32_J_TOL, FP32_RHO_TOL), "fp32_tc": (FP32_J_TOL, FP32_RHO_TOL)}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -175,6 +173,8 @@ VARIANT_CASES = [
     ("fp32", _tiny, (2, 2, 1), 2),                    # bulk-staged 8^3 stage / z-march
     ("fp32", lambda: W.cell_tiny(atoms="offgrid", n=(10, 12, 14), a=(7.0, 8.0, 9.0), n_bands=3), (3, 1, 1), 3),
     ("fp64", _tiny, (2, 2, 1), 3),                    # point-parallel: 8, 4, 16 bands per chunk
+    ("fp32_tc", W.cell_a, (2, 1, 1), 3),              # bulk-staged stencil stage (t; t, V, psi) / halo-plane z-march
+    ("fp32_tc", lambda: W.cell_tiny(atoms="offgrid", n=(10, 12, 16), a=(7.0, 8.0, 9.0), n_bands=3), (3, 1, 1), 1),
 ]
 
 

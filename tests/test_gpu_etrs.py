@@ -6,7 +6,7 @@ import pytest
 
 import workloads as W
 
-from gpu_common import FP64_J_TOL, FP64_RHO_TOL, compare, gpu_run, oracle_run, random_subsim
+from gpu_common import FP32_J_TOL, FP32_RHO_TOL, FP64_J_TOL, FP64_RHO_TOL, compare, gpu_run, oracle_run, random_subsim
 
 pytestmark = pytest.mark.gpu
 
@@ -19,7 +19,7 @@ def built_library():
     build_library()
 
 
-BARS = {"fp64": (FP64_J_TOL, FP64_RHO_TOL), "fp32": (1e-4, 1e-5)}
+BARS = {"fp64": (FP64_J_TOL, FP64_RHO_TOL), "fp32": (FP32_J_TOL, FP32_RHO_TOL)}
 
 CASES = {
     # 8^3 pair cell, self-consistent v_Hxc, a pulse (A changes within every step)

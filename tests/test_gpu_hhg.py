@@ -27,7 +27,8 @@ def built_library():
     build_library()
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+# fp32: measured max relative orbital error 3.2e-7 on GB300, bar 10x
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 3.2e-6)])
 def test_hhg_workload_full_size_sampled(precision, tol):
     from paper_2112_00920_gb300 import Propagator, shifted_kpoints
     run = W.twostep_hhg_run(n_steps=2)
@@ -62,11 +63,12 @@ def test_hhg_workload_full_size_sampled(precision, tol):
         print(precision, "subgrid", m, "k", kk.tolist(), "max rel orbital error", err)
         assert err <= tol
         nr = P.norms(sids[m])[kk]
-        assert np.max(np.abs(nr - o["norms"])) <= (1e-12 if precision == "fp64" else 1e-5)
+        assert np.max(np.abs(nr - o["norms"])) <= (1e-12 if precision == "fp64" else 1e-6)
     P.close()
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("fp32", 1e-4)])
+# fp32: measured 1.3e-7 of the spectrum maximum on GB300, bar 10x
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("fp32", 1.3e-6)])
 def test_hhg_spectrum_vs_oracle(precision, tol):
     """A short sin^4 pulse (E0 = 0.05, w0 = 0.5, T_L = 20 au, polarisation z) on
     cell A's 8^3 grid with 2 k-points, dt = 0.04, 500 steps (one pulse);

@@ -1,0 +1,60 @@
+"""The failure of one k-point per sub-simulation (Sec. III.A, discussion of
+Fig. 4) on the GPU: every sub-simulation solves its own ground state with
+the library's SCF (tsbz_ground_state), is kicked and propagated, and the
+library forms the two-step average of each run (tsbz_get_current with
+sub-simulation -1, Eq. 9).  The three runs of tests/nk1_common.py (MP 4^3
+reference, 8 x 2^3, 64 x 1) match the oracle's stored averages
+(tests/golden/nk1_tiny8_dJ.txt) within the agreement of the two SCF
+solutions, and the GPU results meet the same criterion: 8 k-points per
+sub-simulation are close to the reference, one k-point per sub-simulation
+is not."""
+import os
+
+import numpy as np
+import pytest
+
+import nk1_common as NK
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "nk1_tiny8_dJ.txt")
+# both SCF solutions are converged to dV sum |rho_out - rho_in| / N_e <= 1e-10;
+# the kicked responses then agree to about 1e-8 of their maximum
+PARITY_TOL = 1e-6
+
+
+def _gpu_two_step(name):
+    from paper_2112_00920_gb300 import Propagator, shifted_kpoints
+    cell = NK.cell()
+    P = Propagator("fp64")
+    cid = P.add_cell_spec(cell)
+    for mp, shift in NK.RUNS[name]:
+        nk = mp[0] * mp[1] * mp[2]
+        sid = P.add_subsim(cid, shifted_kpoints(cell.a, mp, shift), NK.DT, NK.N_STEPS)
+        P.load_ground_state(sid, W.plane_wave_orbitals(cell.a, cell.n, W.plane_wave_set(cell.n_bands), nk))
+    iters, err = P.ground_state(max_iter=200, tol=1e-10)
+    assert err <= 1e-10, (name, iters, err)
+    P.set_kick(-1, NK.K0, (1.0, 0.0, 0.0))
+    P.propagate(NK.N_STEPS)
+    dj, _ = P.current(-1)
+    P.close()
+    return dj, iters
+
+
+def test_one_kpoint_per_subsimulation_fails_gpu():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2112_00920_gb300 import build_library
+    build_library()
+    gold = np.loadtxt(GOLD)
+    orc = {name: gold[:, 1 + 3 * i: 4 + 3 * i] for i, name in enumerate(("mp4", "nk8", "nk1"))}
+    gpu = {}
+    for name in ("mp4", "nk8", "nk1"):
+        gpu[name], iters = _gpu_two_step(name)
+        e = float(np.max(np.abs(gpu[name] - orc[name])) / np.max(np.abs(orc[name])))
+        print(f"{name}: {iters} SCF iterations, two-step dJ vs oracle {e:.2e}")
+        assert e <= PARITY_TOL, (name, e)
+    e_gpu = NK.check_failure(gpu)
+    e_orc = NK.eps_errors(orc)
+    print("err_eps vs MP 4^3, GPU:", e_gpu, "oracle:", e_orc)

@@ -15,7 +15,8 @@ import workloads as W
 from oracle import analysis, dynamics, kpoints, scf
 from oracle.cell import Grid, local_potential
 
-from gpu_common import FP64_J_TOL, FP64_RHO_TOL, compare, gpu_run, oracle_run, random_subsim
+from gpu_common import (FP32_J_TOL, FP32_NORM_TOL, FP32_RHO_TOL, FP64_J_TOL, FP64_RHO_TOL, compare, gpu_run,
+                        oracle_run, random_subsim)
 
 pytestmark = pytest.mark.gpu
 
@@ -43,7 +44,6 @@ def test_cell_tables_match_oracle():
         P.close()
 
 
-TC_J_TOL, TC_RHO_TOL = 1e-4, 1e-5   # split-BF16 projector products (~2^-17 per product) + float orbitals
 
 
 @pytest.mark.parametrize("case", ["tiny", "ragged"])
@@ -59,7 +59,7 @@ def test_parity_fp32_tc_small(case):
         subs = [random_subsim(cell, (5, 1, 1), (0.1, 0.2, 0.3), 0.05, 6, pulse, seed=2)]
     _, g = gpu_run(cell, subs, precision="fp32_tc")
     o = oracle_run(cell, subs[0])
-    errs = compare(g[0], o, TC_J_TOL, TC_RHO_TOL)
+    errs = compare(g[0], o, FP32_J_TOL, FP32_RHO_TOL, FP32_NORM_TOL)
     print(f"fp32_tc {case}:", errs)
 
 
@@ -89,7 +89,7 @@ def test_parity_fp32_small(case):
     subs = [random_subsim(cell, mp, shift, dt, 6, field, seed=21)]
     _, g = gpu_run(cell, subs, precision="fp32")
     o = oracle_run(cell, subs[0])
-    errs = compare(g[0], o, 1e-4, 1e-5, 1e-5)
+    errs = compare(g[0], o, FP32_J_TOL, FP32_RHO_TOL, FP32_NORM_TOL)
     print(f"fp32 {case}:", errs)
 
 
@@ -225,8 +225,9 @@ def test_parity_mp2_fp32(mp2_ground_state):
     dj_g = g[0]["J"] - g[0]["J0m"]
     dj_o = o["J"] - o["J0_minus"]
     e_dj = float(np.max(np.abs(dj_g - dj_o)) / np.max(np.abs(dj_o)))
-    errs = compare(g[0], o, 1e-4, 1e-5, 1e-5)
-    assert e_dj < 1e-3, e_dj
+    # 20 steps from the SCF ground state: measured err_J 7.0e-7, err_dJ 7.0e-7 (GB300); bars 10x
+    errs = compare(g[0], o, 7e-6, FP32_RHO_TOL, FP32_NORM_TOL)
+    assert e_dj < 7e-6, e_dj
     print("fp32 mp2:", errs, "err_dJ", e_dj)
 
 
@@ -239,8 +240,9 @@ def test_parity_mp2_fp32_tc(mp2_ground_state):
     dj_g = g[0]["J"] - g[0]["J0m"]
     dj_o = o["J"] - o["J0_minus"]
     e_dj = float(np.max(np.abs(dj_g - dj_o)) / np.max(np.abs(dj_o)))
-    errs = compare(g[0], o, TC_J_TOL, TC_RHO_TOL, TC_RHO_TOL)
-    assert e_dj < 1e-3, e_dj
+    # measured err_J 1.1e-6, err_dJ 1.2e-6 (GB300); bars 10x
+    errs = compare(g[0], o, 1.2e-5, FP32_RHO_TOL, FP32_NORM_TOL)
+    assert e_dj < 1.2e-5, e_dj
     print("fp32_tc mp2:", errs, "err_dJ", e_dj)
 
 
@@ -341,7 +343,7 @@ def test_bounded_wait_times_out_without_fault():
     cell = _tiny_pair()
     subs = [random_subsim(cell, (2, 1, 1), (0.25, 0.5, 0.0), 0.08, 2, W.Kick(k0=0.01), seed=3)]
     _, g = gpu_run(cell, subs, precision="fp32")
-    compare(g[0], oracle_run(cell, subs[0]), 1e-4, 1e-5)
+    compare(g[0], oracle_run(cell, subs[0]), FP32_J_TOL, FP32_RHO_TOL, FP32_NORM_TOL)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_tc"])
@@ -370,7 +372,8 @@ def test_full_two_step_workload_sampled(precision):
         if precision == "fp64":
             compare(g, o, FP64_J_TOL, FP64_RHO_TOL)
         else:
-            print(precision, m, compare(g, o, 1e-4, 1e-5, 1e-5))
+            # two steps from plane waves: measured err_J 4.2e-7 (fp32), 2.8e-6 (fp32_tc) on GB300; bars 10x
+            print(precision, m, compare(g, o, 5e-6 if precision == "fp32" else 3e-5, FP32_RHO_TOL, FP32_NORM_TOL))
 
 
 def _eps(j, j0, dt, k0, omegas):

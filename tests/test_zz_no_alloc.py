@@ -5,7 +5,8 @@ framework's memory pool or a pre-sized arena, or must avoid cudaMalloc's
 device synchronisation); for them the library offers a density call whose
 scratch is a static device buffer.  This test calls it through the C ABI
 twice in a row, on two different orbital sets (the second needs several
-k-chunks of the buffer), and checks each result against the context entry
+k-chunks of the buffer), and checks each result against the oracle's
+density (Eq. 3 with the k average of Eq. 7) and against the context entry
 point tsbz_get_density on the same orbitals, within the FP64 parity
 tolerance of the other GPU tests.  This file is collected last.
 """
@@ -14,6 +15,7 @@ import pytest
 
 import workloads as W
 from oracle.cell import Grid
+from oracle.scf import density_from
 
 pytestmark = pytest.mark.gpu
 
@@ -42,14 +44,17 @@ def test_density_noalloc_matches_get_density():
     n_ks = [8, 50]   # 50 k of 5760 points needs two chunks of the 262144-double buffer
     psis = [W.random_orbitals(nk, c.n_bands, c.n, Grid(c).dv, seed=21, tag=i)
             for i, (c, nk) in enumerate(zip(cells, n_ks))]
+    orcs = [density_from(c, p) for c, p in zip(cells, psis)]
     refs = [_context_density(c, p) for c, p in zip(cells, psis)]
     devs = [torch.from_numpy(p).cuda() for p in psis]
     outs = [density_noalloc(d, c.occ) for d, c in zip(devs, cells)]   # two calls in a row
     torch.cuda.synchronize()
-    for out, ref in zip(outs, refs):
+    for out, orc, ref in zip(outs, orcs, refs):
         got = out.cpu().numpy()
+        assert np.max(np.abs(got - orc)) <= RHO_TOL * np.max(np.abs(orc))
         assert np.max(np.abs(got - ref)) <= RHO_TOL * np.max(np.abs(ref))
-    # the buffer keeps the last call's contents: repeating the first call gives the same density
+    # bitwise repeatability: the buffer still holds the second call's partial sums,
+    # and repeating the first call overwrites them and gives the same density bit for bit
     again = density_noalloc(devs[0], cells[0].occ)
     torch.cuda.synchronize()
     np.testing.assert_array_equal(again.cpu().numpy(), outs[0].cpu().numpy())
