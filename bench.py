@@ -320,7 +320,8 @@ STAGE_KERNEL = {
     "fp64": "k_stage (stencil + ket + Taylor accumulate)",
 }
 STEP_KERNEL = ("k_step_fused (the four Taylor stages of a time step in one launch: z-march stencil, tensor-core "
-               "projector contractions, Taylor accumulation in registers)")
+               "projector z contractions (tcgen05 + TMEM in variant 0, mma.sync in variant 3), Taylor "
+               "accumulation in registers)")
 # FP32 arithmetic of the local part of h, the Taylor scaling and the psi sum,
 # per grid point, orbital and Taylor stage (complex values): Laplacian and
 # gradient pairs 3 axes x 4 x (2 + 4 + 2 + 4) = 144, q.grad 10, diagonal 3,
@@ -368,6 +369,8 @@ def step_roofline(step_ms, n_orb, cell, elem, peaks, subsims, clocks, alu):
     flops = 4.0 * FLOPS_LOCAL_PER_POINT_STAGE * npts * n_orb
     byts = float(n_orb) * (2 * elem * npts + 6 * n_proj * elem)
     mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    if alu is None:   # no probe: the nominal figure from the unit counts (152 SMs)
+        alu = {"sm_count": 152, "ffma_tflops": 152 * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12, "ffma2_tflops": 0.0}
     nominal = alu["sm_count"] * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
     best = "ffma2" if alu["ffma2_tflops"] >= alu["ffma_tflops"] else "ffma"
     peak = alu[best + "_tflops"]
@@ -439,7 +442,8 @@ def stencil_roofline(device, n_subsims, hbm, peaks_src, steps=3):
     launching stream around every stage launch (tsbz_get_timings)."""
     import torch
     import workloads as W
-    P, sids, run = build_propagator("fp32_tc", steps + 3, device=device, n_subsims=n_subsims)
+    # step budget: one step, then per variant one untimed and `steps` timed steps
+    P, sids, run = build_propagator("fp32_tc", 2 + 3 * (steps + 1), device=device, n_subsims=n_subsims)
     cell = run.subsims[0].cell
     psi = torch.from_numpy(W.plane_wave_orbitals(cell.a, cell.n, W.plane_wave_set(cell.n_bands), 64)).to(
         f"cuda:{device}")
@@ -607,11 +611,12 @@ def main():
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     elem = 16 if args.precision == "fp64" else 8
     variant, n_var, _ = P.variant(0)
-    whole = args.precision == "fp32" and variant == 0 and n_var == 3
+    whole = args.precision == "fp32" and variant in (0, 3) and n_var == 4
     fam_ms = {k: v / args.steps for k, v in fam.items()}
     if whole:
-        roof = step_roofline(fam["stage"] / args.steps, n_orb, cell, elem, peaks, args.subsims, clk.summary(),
-                             alu_peaks(local_rank))
+        # profiler runs skip the FMA probe so that their launch lists hold the step's kernels only
+        alu = alu_peaks(local_rank) if not args.profile_run else None
+        roof = step_roofline(fam["stage"] / args.steps, n_orb, cell, elem, peaks, args.subsims, clk.summary(), alu)
     else:
         stage_ms = fam["stage"] / (4 * args.steps)
         bytes_launch = stage_bytes_per_launch(elem, n_orb, cell.n_pts, reads_v=args.precision == "fp32_tc")
@@ -732,7 +737,8 @@ def main():
                           "orbitals_per_gpu": n_orb, "grid": "16^3", "bands": 16, "dt": 0.08,
                           "precision": {"fp32": "fp32 stencil/Taylor; projector contractions factorised per "
                                                 "axis, the z contractions as three-product TF32 tensor-core "
-                                                "GEMMs (mma.sync) with fp32 accumulation; fp64 rho/J/Hartree",
+                                                "GEMMs (tcgen05, accumulators in tensor memory; mma.sync in "
+                                                "variant 3) with fp32 accumulation; fp64 rho/J/Hartree",
                                         "fp32_tc": "fp32 stencil/Taylor; dense projector GEMMs as scaled "
                                                    "split-FP16 three-product tensor-core products (mma.sync) "
                                                    "with fp32 accumulation; fp64 rho/J/Hartree",
@@ -744,8 +750,9 @@ def main():
                "graph_replay_value": graph_value,
                "autotune": {"variant": tuned_variant, "n_variants": tuned_n, "variants_timed": n_tried,
                             "ms_per_step": tuned_ms,
-                            "variants": "0 whole step in one launch, 1 fused stage per launch, "
-                                        "2 z-march stage with CUDA-core projections" if tuned_n == 3 else None},
+                            "variants": "0 whole step in one launch (z contractions on tcgen05), 1 fused stage "
+                                        "per launch (tcgen05), 2 z-march stage with CUDA-core projections, 3 whole "
+                                        "step with the z contractions on mma.sync" if tuned_n == 4 else None},
                "clocks": clk.summary(),
                "fp64_gpu": fp64,
                "etrs": etrs,
@@ -770,6 +777,12 @@ SIDE_WORKLOADS = {
                   "MP grid (8 k-points), kick 0.005 along x, default kernel variant",
     "uneven": "uneven batch: 18 8-atom 16^3 cells and 2 32^3 supercells with 2^3..6^3 shifted subgrids, "
               "kicks 1e-4..1e-2, autotuned (20 s budget)",
+    "config5": "uneven batched two-step run at full size: 180 8-atom 16^3 cells (16 bands) and 20 2x2x2 "
+               "supercells (32^3 grid, 64 atoms, 128 bands) with seeded 2^3..6^3 shifted subgrids (19 197 "
+               "k-points, 482 208 orbitals), kicks 1e-4..1e-2 along x; plane-wave start orbitals (throughput "
+               "only: no ground states for the supercells); default kernel variants (the autotuner's state "
+               "snapshot would not fit beside the 185 GB of single-precision state); the seeded 518..4952 step "
+               "budgets are capped to the steps run, since the step counts do not change the cost of a step",
     "hhg": "two-step HHG run: 8 shifted 8^3 subgrids of the 8-atom 16^3 cell (4096 k, 65 536 orbitals), the "
            "sin^4 pulse of Eq. 15 along z (E0 0.005, w0 0.057, T 1654), dt 0.04, self-consistent v_Hxc, "
            "plane-wave start; A(t) changes every step, timed from the middle of the pulse",
@@ -790,6 +803,19 @@ def run_side_workload(args):
     elif args.workload == "hhg":
         subs = W.twostep_hhg_run().subsims
         t_start = int(round(0.5 * subs[0].field.t_pulse / subs[0].dt))   # middle of the pulse
+    elif args.workload == "config5":
+        subs = W.uneven_batch_run(max_steps=cap).subsims
+        # device memory: three single-precision orbital arrays (psi and the two
+        # Taylor-term buffers) plus projections, partial sums and the largest
+        # complex128 upload; refuse rather than run the device out of memory
+        orb_bytes = sum(s.mp[0] * s.mp[1] * s.mp[2] * s.cell.n_bands * s.cell.n_pts * 8 for s in subs)
+        upload = max(s.mp[0] * s.mp[1] * s.mp[2] * s.cell.n_bands * s.cell.n_pts * 16 for s in subs)
+        need = 3 * orb_bytes * 1.08 + 2 * upload
+        free, total = torch.cuda.mem_get_info()
+        if need > 0.92 * free:
+            print(json.dumps({"workload": args.workload, "skipped": f"needs about {need / 1e9:.0f} GB of device "
+                              f"memory, {free / 1e9:.0f} GB free"}))
+            return
     else:
         subs = W.uneven_batch_run(n_a=18, n_b=2, max_steps=cap).subsims
     cells, sids, n_orb, n_pb = {}, [], 0, 0
@@ -797,10 +823,13 @@ def run_side_workload(args):
         if s.cell.name not in cells:
             cells[s.cell.name] = P.add_cell_spec(s.cell)
         sids.append(P.add_subsim(cells[s.cell.name], shifted_kpoints(s.cell.a, s.mp, s.shift), s.dt, cap))
+    one_k = {}
     for s, sid in zip(subs, sids):
         c = s.cell
         nk = s.mp[0] * s.mp[1] * s.mp[2]
-        psi = torch.from_numpy(W.plane_wave_orbitals(c.a, c.n, W.plane_wave_set(c.n_bands), nk)).cuda()
+        if c.name not in one_k:   # the plane-wave start is the same for every k: one set per cell
+            one_k[c.name] = torch.from_numpy(W.plane_wave_orbitals(c.a, c.n, W.plane_wave_set(c.n_bands), 1)).cuda()
+        psi = one_k[c.name].expand((nk,) + tuple(one_k[c.name].shape[1:])).contiguous()
         P.load_ground_state(sid, psi)
         del psi
         if isinstance(s.field, W.Pulse):
@@ -829,7 +858,10 @@ def run_side_workload(args):
     lps = (P.launches() - l0) / args.steps
     ms = e0.elapsed_time(e1) / args.steps
     fam = {k: v / args.steps for k, v in P.timings().items()}
+    fam_sum = sum(fam.values())
     out = {"workload": args.workload, "description": SIDE_WORKLOADS[args.workload],
+           "n_subsims": len(subs), "orbitals": n_orb,
+           "launch_gap_share": (ms - fam_sum) / ms,
            "precision": args.precision, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": ms, "orbital_steps_per_s": n_orb / (ms / 1e3),
            "point_band_steps_per_s": n_pb / (ms / 1e3), "family_ms_per_step": fam,
@@ -837,7 +869,7 @@ def run_side_workload(args):
            "variants_timed": tuned, "launches_per_step": lps}
     if args.workload == "hhg" and args.precision == "fp32":
         v = P.variant(cells[subs[0].cell.name])
-        if v[0] == 0 and v[1] == 3:
+        if v[0] in (0, 3) and v[1] == 4:
             peaks = {}
             try:
                 peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))

@@ -282,6 +282,23 @@ int tsbz_selftest_bounded_wait(int device, int polls, int deliver, int* status_o
  * device allocation.  Returns TSBZ_OK, TSBZ_EINVAL, TSBZ_ENOMEM or TSBZ_ECUDA. */
 int tsbz_probe_alu_peak(int device, int kind, int iters, double* flops_per_s, double* ms_out);
 
+/* Self-test of the fifth-generation tensor-core building blocks that the
+ * projector contractions use (instrumentation; the paper has no
+ * counterpart): one CTA on `device` forms D = A B^T with M = 128, N = 32,
+ * K = 16 as three TF32 products (A_lo B_hi + A_hi B_lo + A_hi B_hi, FP32
+ * accumulation) by tcgen05.mma with A in tensor memory and B in shared memory
+ * (canonical K-major layout, no swizzle), and copies D back.
+ *  - a: host, row-major [128][16]; b: host, row-major [32][16] (B^T); d: host,
+ *    row-major [128][32], written.  All owned by the caller.
+ *  - swap_lbo_sbo: 0 = descriptor with the K-direction core-matrix stride as
+ *    its leading-dimension offset (the layout the library uses), 1 = the two
+ *    offsets exchanged (both stay inside the operand's buffer).
+ *  - The MMA completion wait is bounded; a timeout returns TSBZ_ETIMEOUT with
+ *    the tensor memory released.  *status_out (nullable): status word.
+ *  - Synchronous; small device allocations.  Returns TSBZ_OK, TSBZ_EINVAL,
+ *    TSBZ_ECUDA or TSBZ_ETIMEOUT. */
+int tsbz_selftest_umma(int device, int swap_lbo_sbo, const float* a, const float* b, float* d, int* status_out);
+
 const char* tsbz_last_error(tsbz_ctx* ctx);
 void tsbz_destroy(tsbz_ctx* ctx);
 

@@ -95,6 +95,8 @@ _SIGS = {
     "tsbz_set_variant": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "tsbz_selftest_bounded_wait": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, _I], ctypes.c_int),
     "tsbz_probe_alu_peak": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D], ctypes.c_int),
+    "tsbz_selftest_umma": ([ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
+                            ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), _I], ctypes.c_int),
     "tsbz_last_error": ([ctypes.c_void_p], ctypes.c_char_p),
     "tsbz_destroy": ([ctypes.c_void_p], None),
     "tsbz_shifted_kpoints": ([_D, _I, _D, _D, ctypes.c_size_t], ctypes.c_int),
@@ -178,6 +180,20 @@ def probe_alu_peak(device: int, kind: str, iters: int = 20000):
     if rc:
         raise TsbzError(rc, "tsbz_probe_alu_peak")
     return f.value, ms.value
+
+
+def selftest_umma(device: int, a: np.ndarray, b: np.ndarray, swap_lbo_sbo: bool = False):
+    """D = A B^T (128 x 32, K = 16) through the library's tcgen05 building
+    blocks (tsbz_selftest_umma).  Returns (status code, status word, D)."""
+    fp = ctypes.POINTER(ctypes.c_float)
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    b = np.ascontiguousarray(b, dtype=np.float32)
+    assert a.shape == (128, 16) and b.shape == (32, 16)
+    d = np.zeros((128, 32), dtype=np.float32)
+    st = ctypes.c_int()
+    rc = load().tsbz_selftest_umma(int(device), 1 if swap_lbo_sbo else 0, a.ctypes.data_as(fp), b.ctypes.data_as(fp),
+                                   d.ctypes.data_as(fp), ctypes.byref(st))
+    return rc, st.value, d
 
 
 def density_noalloc(psi, occ, rho=None, stream=None):

@@ -21,6 +21,7 @@
 #include <stdint.h>
 
 #include "tsbz_sep.cuh"
+#include "tsbz_umma.cuh"
 
 #define FS_N 16
 #define FS_NP 256          // columns (threads)
@@ -78,6 +79,8 @@ struct FsSmem {
   int zmem[4][2];                    // the (at most two) atoms of group g
   int zcnt[4];
   unsigned long long mbar;
+  unsigned long long mbar_mma;   // completion of the tcgen05 contractions (one phase per commit)
+  uint32_t tslot;                // tensor-memory base address from tcgen05.alloc
 };
 
 // z group tables of the cell into shared memory (grouped kernels; read after
@@ -249,55 +252,13 @@ __device__ __forceinline__ void fs_ket(FsSmem& sm, const CellDev& c, float2* vou
   }
 }
 
-// ----------------------------------------------------------------------------
-// Projection pass: monomial sums up to degree D of the atoms a0 .. a0 + NAP - 1,
-// from the split A fragments of u (ah/al) and the tables zt / colt of the
-// pass.  The z contraction covers the z weights q' = q0 .. q0 + NQ - 1 with
-// q' = (D + 1) g + k (g the z group, k the power of d_z); the x and y
-// contractions run per atom on the z sums of its group.  Leaves
-// mres[(a - a0) * NM + mono] (NM = 4 for D = 1, 10 for D = 2).
-// ----------------------------------------------------------------------------
+// x and y contractions of a projection pass, from the z sums
+// sbuf[q'][iy][ix ^ iy] of the pass's z weights q' = q0 .. q0 + NQ - 1 (read
+// after a barrier): leaves mres[(a - a0) * NM + mono] and ends with a barrier.
 template <int D, int NQ, int NAP, int NZU>
-__device__ __forceinline__ void fs_project_pass(FsSmem& sm, const CellDev& c, int q0, int a0,
-                                                const uint32_t (&ah)[2][4][4], const uint32_t (&al)[2][4][4],
-                                                uint2* bz, float2* sbuf) {
-  // bz: B_z (32 x (2 NQ + 4) uint2); sbuf: the z sums [q'][iy][ix ^ iy] (NQ x 256 float2)
-  constexpr int NPR = 2 * NQ;          // real n of the pass
-  constexpr int BZP = NPR + 4;         // B_z row pitch (uint2)
+__device__ __forceinline__ void fs_xy_contract(FsSmem& sm, const CellDev& c, int q0, int a0, const float2* sbuf) {
   constexpr int NM = D == 1 ? 4 : 10;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, g = lane >> 2, t4 = lane & 3;
-  // B_z[k][n], k = 2 z + c (component of u), n = 2 q' + c' (component of S)
-  for (int i = tid; i < 32 * NPR; i += blockDim.x) {
-    const int k = i / NPR, n = i - k * NPR;
-    const int z = k >> 1, cu = k & 1, qq = q0 + (n >> 1), cs = n & 1;
-    const int gz = qq / (D + 1), kz = qq - gz * (D + 1);
-    const float4 f = fz_table<NZU>(sm, c, gz, z);
-    const float s = kz == 0 ? 1.f : (kz == 1 ? f.z : f.z * f.z);
-    const float zr = s * f.x, zi = s * f.y;
-    const float v = cs == 0 ? (cu == 0 ? zr : -zi) : (cu == 0 ? zi : zr);
-    bz[k * BZP + n] = fs_split2(v);
-  }
-  __syncthreads();
-  // z contraction on tensor cores: S[col][q'] for the warp's columns
-#pragma unroll
-  for (int nt = 0; nt < NPR / 8; ++nt) {
-    float d[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-#pragma unroll
-    for (int ks = 0; ks < 4; ++ks) {
-      const uint2 b0 = bz[(8 * ks + t4) * BZP + 8 * nt + g];
-      const uint2 b1 = bz[(8 * ks + t4 + 4) * BZP + 8 * nt + g];
-      fs_mma3(d[0], ah[0][ks], al[0][ks], b0, b1);
-      fs_mma3(d[1], ah[1][ks], al[1][ks], b0, b1);
-    }
-    const int ql = 4 * nt + t4;
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-      const int iyc = 2 * warp + mt;
-      sbuf[ql * FS_NP + iyc * FS_N + (g ^ iyc)] = make_float2(d[mt][0], d[mt][1]);
-      sbuf[ql * FS_NP + iyc * FS_N + ((g + 8) ^ iyc)] = make_float2(d[mt][2], d[mt][3]);
-    }
-  }
-  __syncthreads();
+  const int tid = threadIdx.x;
   // x contraction per row (q', iy): R_i = sum_ix F_x d_x^i S, i <= D - k; then the
   // y contraction M_a(i, j, k) = sum_iy F_y d_y^j R_i over the 16 lanes of the
   // half-warp that holds the rows iy = 0..15 of one q' (fixed-order shuffles).
@@ -385,6 +346,59 @@ __device__ __forceinline__ void fs_project_pass(FsSmem& sm, const CellDev& c, in
   __syncthreads();
 }
 
+
+// ----------------------------------------------------------------------------
+// Projection pass: monomial sums up to degree D of the atoms a0 .. a0 + NAP - 1,
+// from the split A fragments of u (ah/al) and the tables zt / colt of the
+// pass.  The z contraction covers the z weights q' = q0 .. q0 + NQ - 1 with
+// q' = (D + 1) g + k (g the z group, k the power of d_z); the x and y
+// contractions run per atom on the z sums of its group.  Leaves
+// mres[(a - a0) * NM + mono] (NM = 4 for D = 1, 10 for D = 2).
+// ----------------------------------------------------------------------------
+template <int D, int NQ, int NAP, int NZU>
+__device__ __forceinline__ void fs_project_pass(FsSmem& sm, const CellDev& c, int q0, int a0,
+                                                const uint32_t (&ah)[2][4][4], const uint32_t (&al)[2][4][4],
+                                                uint2* bz, float2* sbuf) {
+  // bz: B_z (32 x (2 NQ + 4) uint2); sbuf: the z sums [q'][iy][ix ^ iy] (NQ x 256 float2)
+  constexpr int NPR = 2 * NQ;          // real n of the pass
+  constexpr int BZP = NPR + 4;         // B_z row pitch (uint2)
+  constexpr int NM = D == 1 ? 4 : 10;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, g = lane >> 2, t4 = lane & 3;
+  // B_z[k][n], k = 2 z + c (component of u), n = 2 q' + c' (component of S)
+  for (int i = tid; i < 32 * NPR; i += blockDim.x) {
+    const int k = i / NPR, n = i - k * NPR;
+    const int z = k >> 1, cu = k & 1, qq = q0 + (n >> 1), cs = n & 1;
+    const int gz = qq / (D + 1), kz = qq - gz * (D + 1);
+    const float4 f = fz_table<NZU>(sm, c, gz, z);
+    const float s = kz == 0 ? 1.f : (kz == 1 ? f.z : f.z * f.z);
+    const float zr = s * f.x, zi = s * f.y;
+    const float v = cs == 0 ? (cu == 0 ? zr : -zi) : (cu == 0 ? zi : zr);
+    bz[k * BZP + n] = fs_split2(v);
+  }
+  __syncthreads();
+  // z contraction on tensor cores: S[col][q'] for the warp's columns
+#pragma unroll
+  for (int nt = 0; nt < NPR / 8; ++nt) {
+    float d[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) {
+      const uint2 b0 = bz[(8 * ks + t4) * BZP + 8 * nt + g];
+      const uint2 b1 = bz[(8 * ks + t4 + 4) * BZP + 8 * nt + g];
+      fs_mma3(d[0], ah[0][ks], al[0][ks], b0, b1);
+      fs_mma3(d[1], ah[1][ks], al[1][ks], b0, b1);
+    }
+    const int ql = 4 * nt + t4;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+      const int iyc = 2 * warp + mt;
+      sbuf[ql * FS_NP + iyc * FS_N + (g ^ iyc)] = make_float2(d[mt][0], d[mt][1]);
+      sbuf[ql * FS_NP + iyc * FS_N + ((g + 8) ^ iyc)] = make_float2(d[mt][2], d[mt][3]);
+    }
+  }
+  __syncthreads();
+  fs_xy_contract<D, NQ, NAP, NZU>(sm, c, q0, a0, sbuf);
+}
+
 // A fragments (split) of u = ubuf[z][col] for the warp's columns, k = 2 z + c
 __device__ __forceinline__ void fs_load_u(const float2* src, uint32_t (&ah)[2][4][4], uint32_t (&al)[2][4][4]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t4 = lane & 3;
@@ -402,6 +416,258 @@ __device__ __forceinline__ void fs_load_u(const float2* src, uint32_t (&ah)[2][4
       fs_split(ub[2 * (z1 * FS_PU + cA + 8) + c1], ah[mt][ks][3], al[mt][ks][3]);
     }
   }
+}
+
+// ----------------------------------------------------------------------------
+// The same z contractions on the fifth-generation tensor cores (tcgen05, NZU =
+// 4): each thread writes the split row of its column (A operand, TF32 hi and
+// lo) into tensor memory with tcgen05.st, the B operand (z factors, hi and
+// lo) sits in shared memory in the canonical K-major layout, one thread
+// issues the MMAs (M = 128 per half of the 256 columns, K = 8 per
+// instruction, three products per K step), their completion arrives on an
+// mbarrier (bounded wait), and each thread reads its row of the FP32
+// accumulator back with tcgen05.ld.  Same three-product TF32 scheme as the
+// mma.sync form; the accumulation order inside the tensor core differs, so
+// the two forms agree to FP32 rounding, not bit for bit.
+// Tensor-memory columns of a CTA (FU_COLS): ket A (hi, lo per half) and bra
+// accumulator in [0, 64), ket accumulator in [64, 128), bra A in [128, 256).
+// ----------------------------------------------------------------------------
+#define FU_COLS 256u
+#define FU_KET_A 0
+#define FU_KET_D 64
+#define FU_BRA_D 0
+#define FU_BRA_A 128
+
+struct FuState {
+  uint32_t tbase;   // tensor-memory base of the CTA
+  uint32_t bar;     // shared address of FsSmem::mbar_mma
+  uint32_t phase;   // parity of the next completion
+};
+
+// byte offset of element (row n, k) of a K-major operand with 128-byte core
+// matrices: K-direction stride lbo = 128, 8-row groups sbo apart
+__device__ __forceinline__ int fu_boff(int n, int k, int sbo) {
+  return (n >> 3) * sbo + (k >> 2) * 128 + (n & 7) * 16 + (k & 3) * 4;
+}
+
+// Wait for the last commit (bounded); true on every thread when it completed.
+__device__ __forceinline__ bool fu_wait(FuState& u) {
+  const bool ok = bk_mbar_wait(u.bar, u.phase, BK_WAIT_POLLS);
+  u.phase ^= 1u;
+  return __syncthreads_and(ok) != 0;
+}
+
+// Failure path after fu_wait returned false: record the timeout, give the
+// MMAs in flight one more bounded wait, release the tensor memory.
+__device__ __forceinline__ void fu_bail(const FuState& u, int* status) {
+  if (threadIdx.x == 0) {
+    atomicOr(status, BK_STATUS_TIMEOUT);
+    bk_mbar_wait(u.bar, u.phase ^ 1u, BK_WAIT_POLLS);
+  }
+  __syncthreads();
+  if ((threadIdx.x >> 5) == 0) um_dealloc(u.tbase, FU_COLS);
+}
+
+// Allocation at the start of a kernel (after the CTA knows it has work) and
+// release at its end; both are CTA-wide (barriers inside).
+__device__ __forceinline__ FuState fu_open(FsSmem& sm) {
+  if ((threadIdx.x >> 5) == 0) um_alloc(bk_smem(&sm.tslot), FU_COLS);
+  if (threadIdx.x == 0) bk_mbar_init(bk_smem(&sm.mbar_mma), 1);
+  um_fence_before();
+  __syncthreads();
+  um_fence_after();
+  FuState u;
+  u.tbase = sm.tslot;
+  u.bar = bk_smem(&sm.mbar_mma);
+  u.phase = 0;
+  return u;
+}
+
+__device__ __forceinline__ void fu_close(const FuState& u) {
+  um_fence_before();
+  __syncthreads();
+  if ((threadIdx.x >> 5) == 0) {
+    um_fence_after();
+    um_dealloc(u.tbase, FU_COLS);
+  }
+}
+
+// ket on tcgen05: vout[z][col] = conj(V_NL t)(col, z) (see fs_ket).  The B
+// matrix of z factors (K = 16: Re rows of q, then Im rows; N = 32: n = 2 z + c)
+// is built when build_b, in sm.bk (hi at 0, lo at 2 KiB).
+template <int NZU>
+__device__ __forceinline__ bool fu_ket(FsSmem& sm, const CellDev& c, float2* vout, bool build_b, FuState& u) {
+  static_assert(NZU == 4, "the tcgen05 ket covers 4 z groups (K = 16)");
+  constexpr int Q = 2 * NZU;
+  const int tid = threadIdx.x, warp = tid >> 5, col = tid, ix = col & (FS_N - 1), iy = col / FS_N;
+  const int h = warp >> 2, qd = warp & 3;
+  unsigned char* bkb = reinterpret_cast<unsigned char*>(sm.bk);
+  for (int i = tid; i < SEP_NA * FS_N; i += blockDim.x) {
+    const int a = i / FS_N, jx = i - a * FS_N;
+    const float4 fx = sm.colt[(2 * a) * FS_N + jx];
+    const float2 F = make_float2(fx.x, fx.y);
+    const float2 ws = sm.wt[4 * a], wx = sm.wt[4 * a + 1], wy = sm.wt[4 * a + 2], wz = sm.wt[4 * a + 3];
+    const float2 q0 = make_float2(ws.x + fx.z * wx.x, -(ws.y + fx.z * wx.y));
+    sm.gt[(a * 3 + 0) * FS_N + jx] = sep_cmul(F, q0);
+    sm.gt[(a * 3 + 1) * FS_N + jx] = sep_cmul(F, make_float2(wy.x, -wy.y));
+    sm.gt[(a * 3 + 2) * FS_N + jx] = sep_cmul(F, make_float2(wz.x, -wz.y));
+  }
+  for (int i = tid; build_b && i < 2 * Q * 2 * FS_N; i += blockDim.x) {
+    const int k = i / (2 * FS_N), n = i - k * 2 * FS_N;
+    const bool rrow = k < Q;
+    const int q = rrow ? k : k - Q, z = n >> 1, cc = n & 1;
+    const float4 f = fz_table<NZU>(sm, c, q >> 1, z);
+    const float sc = (q & 1) ? f.z : 1.f;
+    const float zr = sc * f.x, zi = sc * f.y;
+    const float v = rrow ? (cc ? zi : zr) : (cc ? zr : -zi);
+    uint32_t hi, lo;
+    fs_split(v, hi, lo);
+    *reinterpret_cast<uint32_t*>(bkb + fu_boff(n, k, 512)) = hi;
+    *reinterpret_cast<uint32_t*>(bkb + 2048 + fu_boff(n, k, 512)) = lo;
+  }
+  __syncthreads();
+  // A row of this column: k < Q Re, k >= Q Im of A_q = sum over the group's
+  // atoms of F_y (G00 + d_y G10) (q even) or F_y G01 (q odd)
+  uint32_t ah[16], al[16];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int gq = q >> 1;
+    float2 v = make_float2(0.f, 0.f);
+    const int cnt = sm.zcnt[gq];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      if (j < cnt) {
+        const int a = sm.zmem[gq][j];
+        const float4 fy = sm.colt[(2 * a + 1) * FS_N + iy];
+        const float2 F = make_float2(fy.x, fy.y);
+        float2 w;
+        if (q & 1) {
+          w = sep_cmul(F, sm.gt[(a * 3 + 2) * FS_N + ix]);
+        } else {
+          const float2 g0 = sm.gt[(a * 3 + 0) * FS_N + ix], g1 = sm.gt[(a * 3 + 1) * FS_N + ix];
+          w = sep_cmul(F, make_float2(g0.x + fy.z * g1.x, g0.y + fy.z * g1.y));
+        }
+        v.x += w.x;
+        v.y += w.y;
+      }
+    }
+    fs_split(v.x, ah[q], al[q]);
+    fs_split(v.y, ah[Q + q], al[Q + q]);
+  }
+  um_st16(um_addr(u.tbase, qd, FU_KET_A + 32 * h), ah);
+  um_st16(um_addr(u.tbase, qd, FU_KET_A + 32 * h + 16), al);
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  um_fence_before();
+  __syncthreads();
+  if (tid == 0) {
+    um_fence_after();
+    constexpr uint32_t idesc = um_idesc_tf32(128, 32);
+    const uint32_t b0 = bk_smem(bkb), b1 = b0 + 2048;
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+      const uint32_t d = u.tbase + FU_KET_D + 32 * hh;
+#pragma unroll
+      for (int ks = 0; ks < 2; ++ks) {
+        const uint32_t a_hi = u.tbase + FU_KET_A + 32 * hh + 8 * ks, a_lo = a_hi + 16;
+        const uint64_t bh = um_sdesc(b0 + 256 * ks, 128, 512), bl = um_sdesc(b1 + 256 * ks, 128, 512);
+        um_mma_tf32_ts(d, a_lo, bh, idesc, ks > 0);
+        um_mma_tf32_ts(d, a_hi, bl, idesc, true);
+        um_mma_tf32_ts(d, a_hi, bh, idesc, true);
+      }
+    }
+    um_commit(u.bar);
+  }
+  if (!fu_wait(u)) return false;
+  um_fence_after();
+  float d[32];
+  um_ld32(um_addr(u.tbase, qd, FU_KET_D + 32 * h), d);
+#pragma unroll
+  for (int z = 0; z < 16; ++z) vout[z * FS_PU + col] = make_float2(d[2 * z], d[2 * z + 1]);
+  return true;
+}
+
+// The A operand of the projection passes: this thread's column of u = src[z][col]
+// (k = 2 z + c, K = 32), split into TF32 hi and lo, into tensor memory.
+__device__ __forceinline__ void fu_stage_u(const float2* src, const FuState& u) {
+  const int col = threadIdx.x, warp = col >> 5, h = warp >> 2, qd = warp & 3;
+#pragma unroll
+  for (int kk = 0; kk < 2; ++kk) {
+    uint32_t hi[16], lo[16];
+#pragma unroll
+    for (int zz = 0; zz < 8; ++zz) {
+      const float2 v = src[(8 * kk + zz) * FS_PU + col];
+      fs_split(v.x, hi[2 * zz], lo[2 * zz]);
+      fs_split(v.y, hi[2 * zz + 1], lo[2 * zz + 1]);
+    }
+    um_st16(um_addr(u.tbase, qd, FU_BRA_A + 64 * h + 16 * kk), hi);
+    um_st16(um_addr(u.tbase, qd, FU_BRA_A + 64 * h + 32 + 16 * kk), lo);
+  }
+}
+
+// Projection pass on tcgen05 (see fs_project_pass); the A operand was staged by
+// fu_stage_u.  bz: 8 KiB of free shared memory for B_z (hi, lo).
+template <int D, int NQ, int NAP, int NZU>
+__device__ __forceinline__ bool fu_project_pass(FsSmem& sm, const CellDev& c, int q0, int a0, FuState& u,
+                                                unsigned char* bz, float2* sbuf) {
+  constexpr int NPR = 2 * NQ;                   // real n of the pass
+  constexpr int NPAD = (NPR + 15) / 16 * 16;    // N of the MMA (M = 128 needs a multiple of 16)
+  static_assert(NPAD <= 32, "one pass holds at most 16 complex z weights");
+  const int tid = threadIdx.x, warp = tid >> 5, col = tid, ix = col & (FS_N - 1), iy = col / FS_N;
+  const int h = warp >> 2, qd = warp & 3;
+  // B_z^T[n][k], n = 2 q' + c' (component of S), k = 2 z + c (component of u)
+  for (int i = tid; i < 32 * NPAD; i += blockDim.x) {
+    const int n = i / 32, k = i - n * 32;
+    float v = 0.f;
+    if (n < NPR) {
+      const int z = k >> 1, cu = k & 1, qq = q0 + (n >> 1), cs = n & 1;
+      const int gz = qq / (D + 1), kz = qq - gz * (D + 1);
+      const float4 f = fz_table<NZU>(sm, c, gz, z);
+      const float sc = kz == 0 ? 1.f : (kz == 1 ? f.z : f.z * f.z);
+      const float zr = sc * f.x, zi = sc * f.y;
+      v = cs == 0 ? (cu == 0 ? zr : -zi) : (cu == 0 ? zi : zr);
+    }
+    uint32_t hi, lo;
+    fs_split(v, hi, lo);
+    *reinterpret_cast<uint32_t*>(bz + fu_boff(n, k, 1024)) = hi;
+    *reinterpret_cast<uint32_t*>(bz + 4096 + fu_boff(n, k, 1024)) = lo;
+  }
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  um_fence_before();
+  __syncthreads();
+  if (tid == 0) {
+    um_fence_after();
+    constexpr uint32_t idesc = um_idesc_tf32(128, NPAD);
+    const uint32_t b0 = bk_smem(bz), b1 = b0 + 4096;
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+      const uint32_t d = u.tbase + FU_BRA_D + 32 * hh;
+#pragma unroll
+      for (int ks = 0; ks < 4; ++ks) {
+        const uint32_t a_hi = u.tbase + FU_BRA_A + 64 * hh + 8 * ks, a_lo = a_hi + 32;
+        const uint64_t bh = um_sdesc(b0 + 256 * ks, 128, 1024), bl = um_sdesc(b1 + 256 * ks, 128, 1024);
+        um_mma_tf32_ts(d, a_lo, bh, idesc, ks > 0);
+        um_mma_tf32_ts(d, a_hi, bl, idesc, true);
+        um_mma_tf32_ts(d, a_hi, bh, idesc, true);
+      }
+    }
+    um_commit(u.bar);
+  }
+  if (!fu_wait(u)) return false;
+  um_fence_after();
+  if constexpr (NPAD > 16) {
+    float d[32];
+    um_ld32(um_addr(u.tbase, qd, FU_BRA_D + 32 * h), d);
+#pragma unroll
+    for (int ql = 0; ql < NQ; ++ql) sbuf[ql * FS_NP + iy * FS_N + (ix ^ iy)] = make_float2(d[2 * ql], d[2 * ql + 1]);
+  } else {
+    float d[16];
+    um_ld16(um_addr(u.tbase, qd, FU_BRA_D + 32 * h), d);
+#pragma unroll
+    for (int ql = 0; ql < NQ; ++ql) sbuf[ql * FS_NP + iy * FS_N + (ix ^ iy)] = make_float2(d[2 * ql], d[2 * ql + 1]);
+  }
+  __syncthreads();
+  fs_xy_contract<D, NQ, NAP, NZU>(sm, c, q0, a0, sbuf);
+  return true;
 }
 
 // ----------------------------------------------------------------------------
@@ -524,12 +790,12 @@ __device__ __forceinline__ float2 fs_proj_value(const FsSmem& sm, const CellDev&
 // t_{n+1}).  With a constant field both use the same q, and the first-order
 // sums of the current's pass are those of the next step's (same z sums, rows
 // and order).  bz / sbuf: scratch (B_z, z sums), both buffers free.
-template <int NZU>
-__device__ __forceinline__ void fs_stage4_projections(FsSmem& sm, const LaunchSet& L, const CellDev& c, int u,
+template <int NZU, bool UM>
+__device__ __forceinline__ bool fs_stage4_projections(FsSmem& sm, const LaunchSet& L, const CellDev& c, int u,
                                                       const UnitDev& U, int b, float2* __restrict__ Pu,
                                                       float2* __restrict__ Pa, int same_next,
                                                       const uint32_t (&ah)[2][4][4], const uint32_t (&al)[2][4][4],
-                                                      uint2* bz, float2* sbuf) {
+                                                      FuState& fu, uint2* bz, float2* sbuf) {
   const int tid = threadIdx.x;
   const float2* phn = (const float2*)L.ph_next + (long long)u * L.ph_stride;
   const float2* pho = (const float2*)L.ph_obs + (long long)u * L.ph_stride;
@@ -537,7 +803,12 @@ __device__ __forceinline__ void fs_stage4_projections(FsSmem& sm, const LaunchSe
     fs_load_z(sm.zt, c, phn);
     sep_load_cols<FS_N>(sm.colt, c, phn);
     __syncthreads();
-    fs_project_pass<1, 2 * NZU, SEP_NA, NZU>(sm, c, 0, 0, ah, al, bz, sbuf);
+    if constexpr (UM) {
+      if (!fu_project_pass<1, 2 * NZU, SEP_NA, NZU>(sm, c, 0, 0, fu, reinterpret_cast<unsigned char*>(bz), sbuf))
+        return false;
+    } else {
+      fs_project_pass<1, 2 * NZU, SEP_NA, NZU>(sm, c, 0, 0, ah, al, bz, sbuf);
+    }
     if (tid < c.n_proj) Pu[tid] = fs_proj_value(sm, c, tid);
   }
   fs_load_z(sm.zt, c, pho);
@@ -549,7 +820,13 @@ __device__ __forceinline__ void fs_stage4_projections(FsSmem& sm, const LaunchSe
   constexpr int NPASS = NZU == SEP_NA ? 2 : 1, NAP = SEP_NA / NPASS;
 #pragma unroll 1
   for (int half = 0; half < NPASS; ++half) {
-    fs_project_pass<2, 3 * NZU / NPASS, NAP, NZU>(sm, c, half * (3 * NZU / NPASS), half * NAP, ah, al, bz, sbuf);
+    if constexpr (UM) {
+      if (!fu_project_pass<2, 3 * NZU / NPASS, NAP, NZU>(sm, c, half * (3 * NZU / NPASS), half * NAP, fu,
+                                                         reinterpret_cast<unsigned char*>(bz), sbuf))
+        return false;
+    } else {
+      fs_project_pass<2, 3 * NZU / NPASS, NAP, NZU>(sm, c, half * (3 * NZU / NPASS), half * NAP, ah, al, bz, sbuf);
+    }
     // rows (a, c_x, c_y, c_z) of projector type t: monomials w_t and w_t + e_alpha
     const int o = tid;
     if (o < 4 * 4 * NAP) {
@@ -568,13 +845,15 @@ __device__ __forceinline__ void fs_stage4_projections(FsSmem& sm, const LaunchSe
     }
     __syncthreads();
   }
+  return true;
 }
 
 // ----------------------------------------------------------------------------
 // Taylor stage m on a 16^3 grid, one CTA per (unit, band), one thread per
 // (x, y) column; same arithmetic contract as k_stage_bulk: t_m, the psi
 // accumulation, the projections of t_m (m < 4) or, at m = 4, those of
-// psi(t_{n+1}) for the next step (P) and for the current (Pa).
+// psi(t_{n+1}) for the next step (P) and for the current (Pa).  The z
+// contractions run on mma.sync.
 // ----------------------------------------------------------------------------
 template <int NZU>
 __global__ void __launch_bounds__(FS_NP, 2) k_stage_fused(LaunchSet L, const float2* __restrict__ tin,
@@ -640,7 +919,8 @@ __global__ void __launch_bounds__(FS_NP, 2) k_stage_fused(LaunchSet L, const flo
     if (tid < c.n_proj) Pu[tid] = fs_proj_value(sm, c, tid);
     return;
   }
-  fs_stage4_projections<NZU>(sm, L, c, u, U, b, Pu, Pa, same_next, ah, al, bz, sm.yb);
+  FuState fu{};
+  fs_stage4_projections<NZU, false>(sm, L, c, u, U, b, Pu, Pa, same_next, ah, al, fu, bz, sm.yb);
 }
 
 // ----------------------------------------------------------------------------
@@ -651,9 +931,10 @@ __global__ void __launch_bounds__(FS_NP, 2) k_stage_fused(LaunchSet L, const flo
 // in registers, and each stage's projections go straight to the next stage's
 // ket.  Memory traffic per step: psi read and written once, P and Pa.  Same
 // arithmetic per stage as k_stage_fused; psi is summed as
-// (((t_0 + t_1) + t_2) + t_3) + t_4.
+// (((t_0 + t_1) + t_2) + t_3) + t_4.  UM: the z contractions on tcgen05, else
+// on mma.sync.
 // ----------------------------------------------------------------------------
-template <int NZU>
+template <int NZU, bool UM>
 __global__ void __launch_bounds__(FS_NP, 2) k_step_fused(LaunchSet L, float2* __restrict__ psi,
                                                          float2* __restrict__ P, float2* __restrict__ Pa,
                                                          int same_next) {
@@ -673,6 +954,10 @@ __global__ void __launch_bounds__(FS_NP, 2) k_step_fused(LaunchSet L, float2* __
   float2* Pu = P + U.p_off + (long long)b * c.n_proj;
   const long long base = U.psi_off + (long long)b * FS_NPTS;
   const uint32_t bar = bk_smem(&sm.mbar);
+  FuState fu{};
+  if constexpr (UM) {
+    if (proj) fu = fu_open(sm);
+  }
   if (tid == 0) bk_mbar_init(bar, 1);
   fz_load<NZU>(sm, c);
   __syncthreads();
@@ -693,8 +978,13 @@ __global__ void __launch_bounds__(FS_NP, 2) k_step_fused(LaunchSet L, float2* __
   bool waited = false;
 #pragma unroll 1
   for (int m = 1; m <= 4; ++m) {
+    bool mma_ok = true;
     if (proj) {
-      fs_ket<NZU>(sm, c, vio, m == 1);   // the z-table B matrix once per step
+      if constexpr (UM) {
+        mma_ok = fu_ket<NZU>(sm, c, vio, m == 1, fu);   // the z-table B matrix once per step
+      } else {
+        fs_ket<NZU>(sm, c, vio, m == 1);
+      }
     } else {
 #pragma unroll
       for (int z = 0; z < N; ++z) vio[z * FS_PU + col] = make_float2(0.f, 0.f);
@@ -706,11 +996,22 @@ __global__ void __launch_bounds__(FS_NP, 2) k_step_fused(LaunchSet L, float2* __
           atomicOr(S.status, BK_STATUS_TIMEOUT);
           bk_mbar_wait(bar, 0, BK_WAIT_POLLS);
         }
+        if constexpr (UM) {
+          if (proj) {
+            if (mma_ok) fu_close(fu); else fu_bail(fu, S.status);
+          }
+        }
         return;
       }
       waited = true;
     } else {
       __syncthreads();
+    }
+    if constexpr (UM) {
+      if (!mma_ok) {
+        fu_bail(fu, S.status);
+        return;
+      }
     }
     fs_march<true>(sm, c, tin, vio, m, (float)(S.dt * L.dt_scale) / (float)m, q0, q1, q2, dg0, acc, nullptr, psi, base);
     __syncthreads();
@@ -720,11 +1021,23 @@ __global__ void __launch_bounds__(FS_NP, 2) k_step_fused(LaunchSet L, float2* __
       vio = t;
       continue;
     }
-    fs_load_u(vio, ah, al);
+    if constexpr (UM) {
+      fu_stage_u(vio, fu);
+    } else {
+      fs_load_u(vio, ah, al);
+    }
     if (m < 4) {
       // projections of t_m for the next stage; scratch in the buffer of t_{m-1}
-      fs_project_pass<1, 2 * NZU, SEP_NA, NZU>(sm, c, 0, 0, ah, al,
-                                               reinterpret_cast<uint2*>(tin + 2 * NZU * FS_NP), tin);
+      if constexpr (UM) {
+        if (!fu_project_pass<1, 2 * NZU, SEP_NA, NZU>(
+                sm, c, 0, 0, fu, reinterpret_cast<unsigned char*>(tin + 2 * NZU * FS_NP), tin)) {
+          fu_bail(fu, S.status);
+          return;
+        }
+      } else {
+        fs_project_pass<1, 2 * NZU, SEP_NA, NZU>(sm, c, 0, 0, ah, al,
+                                                 reinterpret_cast<uint2*>(tin + 2 * NZU * FS_NP), tin);
+      }
       if (tid < SEP_NP) {
         float2 w = make_float2(0.f, 0.f);
         if (tid < c.n_proj) {
@@ -740,20 +1053,28 @@ __global__ void __launch_bounds__(FS_NP, 2) k_step_fused(LaunchSet L, float2* __
       vio = t;
     } else {
       __syncthreads();   // both buffers free for the projection scratch
-      fs_stage4_projections<NZU>(sm, L, c, u, U, b, Pu, Pa, same_next, ah, al, reinterpret_cast<uint2*>(tin),
-                                 vio);
+      if (!fs_stage4_projections<NZU, UM>(sm, L, c, u, U, b, Pu, Pa, same_next, ah, al, fu,
+                                          reinterpret_cast<uint2*>(tin), vio)) {
+        fu_bail(fu, S.status);
+        return;
+      }
     }
+  }
+  if constexpr (UM) {
+    if (proj) fu_close(fu);
   }
 }
 
 // ----------------------------------------------------------------------------
 // Projections P[u][b][j] of float orbitals on a 16^3 grid (q_half tables),
 // one CTA per (unit, band): the same tensor-core pass as the fused stage, so
-// the projections of a restored state equal those the stage leaves, bit for bit.
+// the projections of a restored state equal those the stage leaves, bit for
+// bit (UM selects the tcgen05 or the mma.sync form, as the stage kernels do).
 // ----------------------------------------------------------------------------
-template <int NZU>
+template <int NZU, bool UM>
 __global__ void __launch_bounds__(FS_NP, 2) k_bra_fused(LaunchSet L, const float2* __restrict__ src,
                                                         float2* __restrict__ P) {
+  static_assert(!UM || NZU == 4, "the tcgen05 contractions cover grouped cells");
   extern __shared__ __align__(128) unsigned char fs_raw[];
   FsSmem& sm = *reinterpret_cast<FsSmem*>(fs_raw);
   const CellDev& c = L.cell;
@@ -762,6 +1083,8 @@ __global__ void __launch_bounds__(FS_NP, 2) k_bra_fused(LaunchSet L, const float
   if (!unit_active(L, u)) return;
   const UnitDev U = L.units[u];
   const int tid = threadIdx.x;
+  FuState fu{};
+  if constexpr (UM) fu = fu_open(sm);
   const float2* ph = (const float2*)L.ph_half + (long long)u * L.ph_stride;
   const float2* sb = src + U.psi_off + (long long)b * FS_NPTS + tid;
   fz_load<NZU>(sm, c);
@@ -770,11 +1093,20 @@ __global__ void __launch_bounds__(FS_NP, 2) k_bra_fused(LaunchSet L, const float
   fs_load_z(sm.zt, c, ph);
   sep_load_cols<FS_N>(sm.colt, c, ph);
   __syncthreads();
-  uint32_t ah[2][4][4], al[2][4][4];
-  fs_load_u(sm.yb, ah, al);
-  __syncthreads();
-  fs_project_pass<1, 2 * NZU, SEP_NA, NZU>(sm, c, 0, 0, ah, al, reinterpret_cast<uint2*>(sm.xb), sm.yb);
+  if constexpr (UM) {
+    fu_stage_u(sm.yb, fu);
+    if (!fu_project_pass<1, 2 * NZU, SEP_NA, NZU>(sm, c, 0, 0, fu, reinterpret_cast<unsigned char*>(sm.xb), sm.yb)) {
+      fu_bail(fu, L.subs[U.sub].status);
+      return;
+    }
+  } else {
+    uint32_t ah[2][4][4], al[2][4][4];
+    fs_load_u(sm.yb, ah, al);
+    __syncthreads();
+    fs_project_pass<1, 2 * NZU, SEP_NA, NZU>(sm, c, 0, 0, ah, al, reinterpret_cast<uint2*>(sm.xb), sm.yb);
+  }
   if (tid < c.n_proj) P[U.p_off + (long long)b * c.n_proj + tid] = fs_proj_value(sm, c, tid);
+  if constexpr (UM) fu_close(fu);
 }
 
 // ----------------------------------------------------------------------------

@@ -23,21 +23,27 @@ template <typename K> static void fs_attr(K* kernel, size_t bytes) {
 static inline bool fs_cube16(const CellDev& c) { return c.n1 == 16 && c.n2 == 16 && c.n3 == 16; }
 
 // Kernel variants of the single-precision path (LaunchSet::variant):
-//   16^3 cells with z groups: 0 whole step in one launch, 1 fused stage per
-//     launch, 2 z-march stage with CUDA-core projections;
+//   16^3 cells with z groups: 0 whole step in one launch with the z
+//     contractions on tcgen05, 1 fused stage per launch (mma.sync), 2 z-march
+//     stage with CUDA-core projections, 3 whole step with the z contractions
+//     on mma.sync;
 //   other 16^3 cells and 8^3 cells: 0 fused / bulk-staged stage, 1 z-march stage;
 //   other shapes: the z-march stage only.
 // Returns 0 (whole step), 1 (fused or bulk-staged stage) or 2 (z-march stage).
 static int stage_kind(const LaunchSet& L) {
   const CellDev& c = L.cell;
   if (L.ph_next == nullptr) return 2;
-  if (fs_cube16(c) && fs_grouped(c)) return L.variant;
+  if (fs_cube16(c) && fs_grouped(c)) return L.variant == 3 ? 0 : L.variant;
   if (fs_cube16(c) || (c.n1 == 8 && c.n2 == 8 && c.n3 == 8)) return L.variant == 0 ? 1 : 2;
   return 2;
 }
 
+// The grouped 16^3 whole-step kernel (and the projection pass that matches it)
+// runs its z contractions on tcgen05 in variant 0.
+static inline bool fs_umma(const LaunchSet& L) { return L.variant == 0; }
+
 int sep_variants(const CellDev& c) {
-  if (fs_cube16(c) && fs_grouped(c)) return 3;
+  if (fs_cube16(c) && fs_grouped(c)) return 4;
   if (fs_cube16(c) || (c.n1 == 8 && c.n2 == 8 && c.n3 == 8)) return 2;
   return 1;
 }
@@ -57,15 +63,20 @@ void launch_bra_sep(const LaunchSet& L, const void* src, void* out, int with_d, 
     // the projections the 16^3 fused stage leaves are formed by the same pass
     static bool attr = false;
     if (!attr) {
-      fs_attr(k_bra_fused<4>, sizeof(FsSmem));
-      fs_attr(k_bra_fused<SEP_NA>, sizeof(FsSmem));
+      fs_attr(k_bra_fused<4, true>, sizeof(FsSmem));
+      fs_attr(k_bra_fused<4, false>, sizeof(FsSmem));
+      fs_attr(k_bra_fused<SEP_NA, false>, sizeof(FsSmem));
       attr = true;
     }
-    if (fs_grouped(c))
-      k_bra_fused<4><<<grid, FS_NP, sizeof(FsSmem), (cudaStream_t)stream>>>(L, (const float2*)src, (float2*)out);
-    else
-      k_bra_fused<SEP_NA><<<grid, FS_NP, sizeof(FsSmem), (cudaStream_t)stream>>>(L, (const float2*)src,
+    if (fs_grouped(c) && fs_umma(L))
+      k_bra_fused<4, true><<<grid, FS_NP, sizeof(FsSmem), (cudaStream_t)stream>>>(L, (const float2*)src,
+                                                                                (float2*)out);
+    else if (fs_grouped(c))
+      k_bra_fused<4, false><<<grid, FS_NP, sizeof(FsSmem), (cudaStream_t)stream>>>(L, (const float2*)src,
                                                                                  (float2*)out);
+    else
+      k_bra_fused<SEP_NA, false><<<grid, FS_NP, sizeof(FsSmem), (cudaStream_t)stream>>>(L, (const float2*)src,
+                                                                                        (float2*)out);
     return;
   }
   const unsigned thr = sep_threads(L.cell);
@@ -142,12 +153,17 @@ bool launch_step_fused(const LaunchSet& L, void* psi, void* P, void* Pa, int sam
   if (L.n_units == 0 || stage_kind(L) != 0) return false;
   static bool attr = false;
   if (!attr) {
-    fs_attr(k_step_fused<4>, sizeof(FsSmem));
+    fs_attr(k_step_fused<4, true>, sizeof(FsSmem));
+    fs_attr(k_step_fused<4, false>, sizeof(FsSmem));
     attr = true;
   }
   const unsigned grid = (unsigned)L.n_units * (unsigned)L.cell.n_bands;
-  k_step_fused<4><<<grid, FS_NP, sizeof(FsSmem), (cudaStream_t)stream>>>(L, (float2*)psi, (float2*)P, (float2*)Pa,
-                                                                          same_next);
+  if (fs_umma(L))
+    k_step_fused<4, true><<<grid, FS_NP, sizeof(FsSmem), (cudaStream_t)stream>>>(L, (float2*)psi, (float2*)P,
+                                                                                (float2*)Pa, same_next);
+  else
+    k_step_fused<4, false><<<grid, FS_NP, sizeof(FsSmem), (cudaStream_t)stream>>>(L, (float2*)psi, (float2*)P,
+                                                                                 (float2*)Pa, same_next);
   return true;
 }
 

@@ -166,8 +166,9 @@ _Z_THREE = [[0.0, 0.0, 0.25], [0.5, 0.25, 0.25], [0.25, 0.75, 0.25]]
 
 VARIANT_CASES = [
     # (precision, cell factory, mp, number of variants)
-    ("fp32", W.cell_a, (2, 1, 1), 3),                 # whole step / fused tensor-core stage / CUDA-core z-march
-    ("fp32", lambda: _cube16(_Z_ONE), (2, 1, 1), 3),  # z groups of one atom
+    # whole step (tcgen05) / fused stage (tcgen05) / CUDA-core z-march / whole step (mma.sync)
+    ("fp32", W.cell_a, (2, 1, 1), 4),
+    ("fp32", lambda: _cube16(_Z_ONE), (2, 1, 1), 4),  # z groups of one atom
     ("fp32", lambda: _cube16(_Z_SIX), (2, 1, 1), 2),  # per-atom fused stage / z-march
     ("fp32", lambda: _cube16(_Z_THREE), (1, 2, 1), 2),
     ("fp32", _tiny, (2, 2, 1), 2),                    # bulk-staged 8^3 stage / z-march

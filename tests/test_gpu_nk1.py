@@ -29,9 +29,9 @@ def _gpu_two_step(name):
     cell = NK.cell()
     P = Propagator("fp64")
     cid = P.add_cell_spec(cell)
-    for mp, shift in NK.RUNS[name]:
-        nk = mp[0] * mp[1] * mp[2]
-        sid = P.add_subsim(cid, shifted_kpoints(cell.a, mp, shift), NK.DT, NK.N_STEPS)
+    sids = [(P.add_subsim(cid, shifted_kpoints(cell.a, mp, shift), NK.DT, NK.N_STEPS), mp[0] * mp[1] * mp[2])
+            for mp, shift in NK.RUNS[name]]
+    for sid, nk in sids:
         P.load_ground_state(sid, W.plane_wave_orbitals(cell.a, cell.n, W.plane_wave_set(cell.n_bands), nk))
     iters, err = P.ground_state(max_iter=200, tol=1e-10)
     assert err <= 1e-10, (name, iters, err)
