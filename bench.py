@@ -332,8 +332,16 @@ FP32_LANES_PER_SM = 128
 # + dram__bytes_write.sum) on the reduced workload (8 of the 64 subgrids, 8192
 # orbitals), scaled by the orbital count to the full workload.  Valid only for
 # the source it was taken on: the SHA-1 of the kernel header is checked at run time.
-STEP_TRAFFIC = {"file": "tsbz_fused.cuh", "sha1": "1fab0b2ebf57dd6737ebb69eb6d2b3cb815b0ab1",
-                "bytes_per_launch_full": 8 * 496.75776e6, "profile": "profiles/k_step_fused_fp32_twostep8.md"}
+STEP_TRAFFIC = {"file": "tsbz_fused.cuh", "sha1": "2c28815383469a3ea7eb683dd5862252dda270ce",
+                "bytes_per_launch_full": 8 * 492.910848e6, "profile": "profiles/k_step_fused_tcgen05_twostep8.md"}
+# DRAM bytes of the per-stage stencil kernel k_stage_zb<false> from an ncu capture of the
+# reduced dense tensor-core workload (8 of the 64 subgrids): stages 1 and 2 moved 774.8 and
+# 1295.1 MB against 805.3 and 1342.2 MB of algorithmic bytes (0.964 of them); the full
+# launch is taken as that fraction of its algorithmic bytes.  Valid for the source it
+# was taken on.
+STENCIL_TRAFFIC = {"file": "tsbz_tc.cuh", "sha1": "2bd77934cbda428416643c624a258d0564747242",
+                   "fraction_of_algorithmic": (774.778112 + 1295.140096) / (805.306368 + 1342.17728),
+                   "profile": "profiles/k_stage_zb_fp32tc_twostep8.md"}
 
 
 def _file_sha1(path: str) -> str | None:
@@ -467,12 +475,16 @@ def stencil_roofline(device, n_subsims, hbm, peaks_src, steps=3):
     stage_ms = per_variant[best]
     byts = stage_bytes_per_launch(8, run.n_orbitals, cell.n_pts, reads_v=True)
     gbs = byts / (stage_ms / 1e3) / 1e9
+    traffic = None
+    path = os.path.join(ROOT, "paper_2112_00920_gb300", "csrc", STENCIL_TRAFFIC["file"])
+    if best == 0 and n_subsims == 64 and _file_sha1(path) == STENCIL_TRAFFIC["sha1"]:
+        traffic = STENCIL_TRAFFIC["fraction_of_algorithmic"] * byts
     names = ["k_stage_zb<false> (band of t_{m-1} bulk-copied to shared memory, V and psi read per plane)",
              "k_stage_zb<true> (bands of t_{m-1}, V and psi bulk-copied to shared memory)",
              "k_stage_zf (halo plane per z, two CTA barriers per plane)"]
     return {"kernel": names[best] + ": one Taylor stage = FD stencil + local potential + non-local term V "
                                     "(an input array) + Taylor accumulation",
-            "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "traffic": None,
+            "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "traffic": traffic,
             "algorithmic_bytes_per_launch": byts, "ms_per_launch": stage_ms, "peak_source": peaks_src,
             "variant": best, "ms_per_launch_by_variant": dict(zip(names[:n_var], per_variant)),
             "note": "fp32_tc mode on the benchmark workload; 17 arrays of 2 GiB per 4 launches (t_{m-1} and V "
