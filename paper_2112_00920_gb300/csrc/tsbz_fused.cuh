@@ -67,9 +67,10 @@ struct FsSmem {
   // (ket) overwritten by t_m; the projection passes use them as scratch
   float2 xb[FS_N * FS_PU];
   float2 yb[FS_N * FS_PU];
-  uint2 bk[32 * FS_BKP];             // ket B matrix (hi, lo)
+  uint2 bk[32 * FS_BKP];             // ket B matrix (hi, lo); tcgen05 form: and the stage 1-3 bra B_z
   float4 zt[SEP_NA * FS_N];          // (Re F_z, Im F_z, d_z, 0) per atom and plane
   float4 colt[SEP_NA * 2 * FS_N];    // x and y factors (Re F, Im F, d, 0)
+  float4 xpk[SEP_NA * FS_N * 3];     // x factors times d^w, w = 0..2, as (Re, Re, Im, Im) pairs
   float2 gt[SEP_NA * 3 * FS_N];      // ket column tables G00, G10, G01 per atom and ix
   float2 wt[SEP_NP];                 // pn E P of the band
   float2 mres[SEP_NA * 10];          // monomial sums of one projection pass
@@ -112,6 +113,33 @@ __device__ __forceinline__ void fs_load_z(float4* zt, const CellDev& c, const fl
       v = make_float4(g * p.x, g * p.y, c.d1f[idx], 0.f);
     }
     zt[i] = v;
+  }
+}
+
+// Factor tables of one phase table: colt (x and y rows, as the column loader
+// of the other kernels) and, for the x contraction of the projection passes,
+// d_x^w F_x for w = 0..2 in the (Re, Re, Im, Im) form of the packed products.
+__device__ __forceinline__ void fs_load_cols(FsSmem& sm, const CellDev& c, const float2* ph) {
+  const int nm = c.nmax;
+  for (int i = threadIdx.x; i < SEP_NA * 2 * FS_N; i += blockDim.x) {
+    const int a = i / (2 * FS_N), r = i - a * 2 * FS_N, ax = r / FS_N, ii = r - ax * FS_N;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (a < c.n_atoms && ii < (ax == 0 ? c.n1 : c.n2)) {
+      const int idx = (a * 3 + ax) * nm + ii;
+      const float g = c.g1f[idx];
+      const float2 p = ph[idx];
+      v = make_float4(g * p.x, g * p.y, c.d1f[idx], 0.f);
+    }
+    sm.colt[i] = v;
+    if (ax == 0) {
+      float fr = v.x, fi = v.y;
+#pragma unroll
+      for (int w = 0; w < 3; ++w) {
+        sm.xpk[(a * FS_N + ii) * 3 + w] = make_float4(fr, fr, fi, fi);
+        fr = __fmul_rn(v.z, fr);
+        fi = __fmul_rn(v.z, fi);
+      }
+    }
   }
 }
 
@@ -269,28 +297,33 @@ __device__ __forceinline__ void fs_xy_contract(FsSmem& sm, const CellDev& c, int
     const int ql = live ? (r >> 4) : 0, iyr = r & 15;
     const int al_ = ql / (D + 1), kz = ql - al_ * (D + 1), a = a0 + al_;
     const int sq = (D + 1) * fz_grp<NZU>(sm, a) + kz - q0;   // z sums of the atom's group
-    // explicit round-to-nearest operations (no contraction), so that the sums a
-    // D = 1 pass and a D = 2 pass have in common come out bit for bit the same
-    float2 R0 = make_float2(0.f, 0.f), R1 = R0, R2 = R0;
+    // packed FP32x2 products: for w = 0..D - k, A_w accumulates d^w Re F_x (s_re, s_im)
+    // and B_w d^w Im F_x (s_re, s_im); R_w = sum d^w F_x s = (A_w.x - B_w.y, A_w.y + B_w.x).
+    // Every row runs every w of the pass (no divergence); the D = 1 and D = 2 passes
+    // share the operations of w = 0, 1, so their common sums agree bit for bit.
+    const float2 zero2 = make_float2(0.f, 0.f);
+    float2 A0 = zero2, B0 = zero2, A1 = zero2, B1 = zero2, A2 = zero2, B2 = zero2;
     if (live) {
+      const float4* xw = sm.xpk + a * FS_N * 3;
+      const float2* sr = sbuf + sq * FS_NP + iyr * FS_N;
 #pragma unroll 4
       for (int ixr = 0; ixr < FS_N; ++ixr) {
-        const float2 s = sbuf[sq * FS_NP + iyr * FS_N + (ixr ^ iyr)];
-        const float4 fx = sm.colt[(2 * a) * FS_N + ixr];
-        const float2 p = fs_cmul_rn(make_float2(fx.x, fx.y), s);
-        R0.x = __fadd_rn(R0.x, p.x);
-        R0.y = __fadd_rn(R0.y, p.y);
-        if (D - kz >= 1) {
-          const float2 pd = make_float2(__fmul_rn(fx.z, p.x), __fmul_rn(fx.z, p.y));
-          R1.x = __fadd_rn(R1.x, pd.x);
-          R1.y = __fadd_rn(R1.y, pd.y);
-          if (D == 2 && kz == 0) {
-            R2.x = __fmaf_rn(fx.z, pd.x, R2.x);
-            R2.y = __fmaf_rn(fx.z, pd.y, R2.y);
-          }
+        const float2 sv = sr[ixr ^ iyr];
+        const float4 p0 = xw[ixr * 3 + 0], p1 = xw[ixr * 3 + 1];
+        A0 = __ffma2_rn(make_float2(p0.x, p0.y), sv, A0);
+        B0 = __ffma2_rn(make_float2(p0.z, p0.w), sv, B0);
+        A1 = __ffma2_rn(make_float2(p1.x, p1.y), sv, A1);
+        B1 = __ffma2_rn(make_float2(p1.z, p1.w), sv, B1);
+        if (D == 2) {
+          const float4 p2 = xw[ixr * 3 + 2];
+          A2 = __ffma2_rn(make_float2(p2.x, p2.y), sv, A2);
+          B2 = __ffma2_rn(make_float2(p2.z, p2.w), sv, B2);
         }
       }
     }
+    const float2 R0 = make_float2(__fsub_rn(A0.x, B0.y), __fadd_rn(A0.y, B0.x));
+    const float2 R1 = make_float2(__fsub_rn(A1.x, B1.y), __fadd_rn(A1.y, B1.x));
+    const float2 R2 = make_float2(__fsub_rn(A2.x, B2.y), __fadd_rn(A2.y, B2.x));
     // y weights of this row: F_y d_y^j
     const float4 fy = sm.colt[(2 * a + 1) * FS_N + iyr];
     const float2 Fy = make_float2(fy.x, fy.y), Fyd = make_float2(__fmul_rn(fy.z, fy.x), __fmul_rn(fy.z, fy.y));
@@ -437,6 +470,7 @@ __device__ __forceinline__ void fs_load_u(const float2* src, uint32_t (&ah)[2][4
 #define FU_KET_D 64
 #define FU_BRA_D 0
 #define FU_BRA_A 128
+#define FU_BZ_OFF 4096   // byte offset in FsSmem::bk of the stage 1-3 bra B_z (4 KiB after the ket B)
 
 struct FuState {
   uint32_t tbase;   // tensor-memory base of the CTA
@@ -527,12 +561,14 @@ __device__ __forceinline__ bool fu_ket(FsSmem& sm, const CellDev& c, float2* vou
   }
   __syncthreads();
   // A row of this column: k < Q Re, k >= Q Im of A_q = sum over the group's
-  // atoms of F_y (G00 + d_y G10) (q even) or F_y G01 (q odd)
+  // atoms of F_y (G00 + d_y G10) (q even) or F_y G01 (q odd); each atom's
+  // tables are read once for both q of its group
   uint32_t ah[16], al[16];
+  float2 av[Q];
 #pragma unroll
-  for (int q = 0; q < Q; ++q) {
-    const int gq = q >> 1;
-    float2 v = make_float2(0.f, 0.f);
+  for (int q = 0; q < Q; ++q) av[q] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int gq = 0; gq < NZU; ++gq) {
     const int cnt = sm.zcnt[gq];
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
@@ -540,19 +576,21 @@ __device__ __forceinline__ bool fu_ket(FsSmem& sm, const CellDev& c, float2* vou
         const int a = sm.zmem[gq][j];
         const float4 fy = sm.colt[(2 * a + 1) * FS_N + iy];
         const float2 F = make_float2(fy.x, fy.y);
-        float2 w;
-        if (q & 1) {
-          w = sep_cmul(F, sm.gt[(a * 3 + 2) * FS_N + ix]);
-        } else {
-          const float2 g0 = sm.gt[(a * 3 + 0) * FS_N + ix], g1 = sm.gt[(a * 3 + 1) * FS_N + ix];
-          w = sep_cmul(F, make_float2(g0.x + fy.z * g1.x, g0.y + fy.z * g1.y));
-        }
-        v.x += w.x;
-        v.y += w.y;
+        const float2 g0 = sm.gt[(a * 3 + 0) * FS_N + ix], g1 = sm.gt[(a * 3 + 1) * FS_N + ix];
+        const float2 g2 = sm.gt[(a * 3 + 2) * FS_N + ix];
+        const float2 we = sep_cmul(F, make_float2(g0.x + fy.z * g1.x, g0.y + fy.z * g1.y));
+        const float2 wo = sep_cmul(F, g2);
+        av[2 * gq].x += we.x;
+        av[2 * gq].y += we.y;
+        av[2 * gq + 1].x += wo.x;
+        av[2 * gq + 1].y += wo.y;
       }
     }
-    fs_split(v.x, ah[q], al[q]);
-    fs_split(v.y, ah[Q + q], al[Q + q]);
+  }
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    fs_split(av[q].x, ah[q], al[q]);
+    fs_split(av[q].y, ah[Q + q], al[Q + q]);
   }
   um_st16(um_addr(u.tbase, qd, FU_KET_A + 32 * h), ah);
   um_st16(um_addr(u.tbase, qd, FU_KET_A + 32 * h + 16), al);
@@ -605,17 +643,19 @@ __device__ __forceinline__ void fu_stage_u(const float2* src, const FuState& u) 
 }
 
 // Projection pass on tcgen05 (see fs_project_pass); the A operand was staged by
-// fu_stage_u.  bz: 8 KiB of free shared memory for B_z (hi, lo).
+// fu_stage_u.  bz: NPAD/8 KiB of shared memory for B_z (hi, then lo); when
+// build_b is false it already holds the B_z of the same z tables and pass.
 template <int D, int NQ, int NAP, int NZU>
 __device__ __forceinline__ bool fu_project_pass(FsSmem& sm, const CellDev& c, int q0, int a0, FuState& u,
-                                                unsigned char* bz, float2* sbuf) {
+                                                unsigned char* bz, float2* sbuf, bool build_b = true) {
   constexpr int NPR = 2 * NQ;                   // real n of the pass
   constexpr int NPAD = (NPR + 15) / 16 * 16;    // N of the MMA (M = 128 needs a multiple of 16)
+  constexpr int LO = NPAD / 8 * 1024;           // byte offset of the lo part
   static_assert(NPAD <= 32, "one pass holds at most 16 complex z weights");
   const int tid = threadIdx.x, warp = tid >> 5, col = tid, ix = col & (FS_N - 1), iy = col / FS_N;
   const int h = warp >> 2, qd = warp & 3;
   // B_z^T[n][k], n = 2 q' + c' (component of S), k = 2 z + c (component of u)
-  for (int i = tid; i < 32 * NPAD; i += blockDim.x) {
+  for (int i = tid; build_b && i < 32 * NPAD; i += blockDim.x) {
     const int n = i / 32, k = i - n * 32;
     float v = 0.f;
     if (n < NPR) {
@@ -629,7 +669,7 @@ __device__ __forceinline__ bool fu_project_pass(FsSmem& sm, const CellDev& c, in
     uint32_t hi, lo;
     fs_split(v, hi, lo);
     *reinterpret_cast<uint32_t*>(bz + fu_boff(n, k, 1024)) = hi;
-    *reinterpret_cast<uint32_t*>(bz + 4096 + fu_boff(n, k, 1024)) = lo;
+    *reinterpret_cast<uint32_t*>(bz + LO + fu_boff(n, k, 1024)) = lo;
   }
   asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
   um_fence_before();
@@ -637,7 +677,7 @@ __device__ __forceinline__ bool fu_project_pass(FsSmem& sm, const CellDev& c, in
   if (tid == 0) {
     um_fence_after();
     constexpr uint32_t idesc = um_idesc_tf32(128, NPAD);
-    const uint32_t b0 = bk_smem(bz), b1 = b0 + 4096;
+    const uint32_t b0 = bk_smem(bz), b1 = b0 + LO;
 #pragma unroll
     for (int hh = 0; hh < 2; ++hh) {
       const uint32_t d = u.tbase + FU_BRA_D + 32 * hh;
@@ -683,7 +723,7 @@ __device__ __forceinline__ void fs_copy_band(float2* dst, const float2* src, uin
 // Factor tables of the unit (q of the step) and W = E P of the band.
 __device__ __forceinline__ void fs_unit_tables(FsSmem& sm, const CellDev& c, const float2* ph, const float2* Pu) {
   fs_load_z(sm.zt, c, ph);
-  sep_load_cols<FS_N>(sm.colt, c, ph);
+  fs_load_cols(sm, c, ph);
   for (int j = threadIdx.x; j < SEP_NP; j += blockDim.x) {
     float2 w = make_float2(0.f, 0.f);
     if (j < c.n_proj) {
@@ -801,7 +841,7 @@ __device__ __forceinline__ bool fs_stage4_projections(FsSmem& sm, const LaunchSe
   const float2* pho = (const float2*)L.ph_obs + (long long)u * L.ph_stride;
   if (!same_next) {
     fs_load_z(sm.zt, c, phn);
-    sep_load_cols<FS_N>(sm.colt, c, phn);
+    fs_load_cols(sm, c, phn);
     __syncthreads();
     if constexpr (UM) {
       if (!fu_project_pass<1, 2 * NZU, SEP_NA, NZU>(sm, c, 0, 0, fu, reinterpret_cast<unsigned char*>(bz), sbuf))
@@ -812,7 +852,7 @@ __device__ __forceinline__ bool fs_stage4_projections(FsSmem& sm, const LaunchSe
     if (tid < c.n_proj) Pu[tid] = fs_proj_value(sm, c, tid);
   }
   fs_load_z(sm.zt, c, pho);
-  sep_load_cols<FS_N>(sm.colt, c, pho);
+  fs_load_cols(sm, c, pho);
   __syncthreads();
   float2* Pab = Pa + U.pa_off + 4LL * b * c.n_proj;
   // the second-order sums of every atom in one pass when the z groups halve
@@ -1029,8 +1069,10 @@ __global__ void __launch_bounds__(FS_NP, 2) k_step_fused(LaunchSet L, float2* __
     if (m < 4) {
       // projections of t_m for the next stage; scratch in the buffer of t_{m-1}
       if constexpr (UM) {
-        if (!fu_project_pass<1, 2 * NZU, SEP_NA, NZU>(
-                sm, c, 0, 0, fu, reinterpret_cast<unsigned char*>(tin + 2 * NZU * FS_NP), tin)) {
+        // the B_z of stages 1-3 (same z tables) is built once per step, beside the ket B
+        if (!fu_project_pass<1, 2 * NZU, SEP_NA, NZU>(sm, c, 0, 0, fu,
+                                                      reinterpret_cast<unsigned char*>(sm.bk) + FU_BZ_OFF, tin,
+                                                      m == 1)) {
           fu_bail(fu, S.status);
           return;
         }
@@ -1091,7 +1133,7 @@ __global__ void __launch_bounds__(FS_NP, 2) k_bra_fused(LaunchSet L, const float
 #pragma unroll
   for (int z = 0; z < FS_N; ++z) sm.yb[z * FS_PU + tid] = sb[z * FS_NP];
   fs_load_z(sm.zt, c, ph);
-  sep_load_cols<FS_N>(sm.colt, c, ph);
+  fs_load_cols(sm, c, ph);
   __syncthreads();
   if constexpr (UM) {
     fu_stage_u(sm.yb, fu);

@@ -85,19 +85,21 @@ def _mixed_groups(nb_b=8):
     ca, cb = W.cell_a(), W.cell_b(n_bands=nb_b)
     a_subs = [random_subsim(ca, (2, 1, 1), (0.125, 0.375, 0.625), 0.08, 4, W.Kick(k0=0.005), seed=41),
               random_subsim(ca, (1, 1, 3), (0.7, 0.2, 0.9), 0.08, 2, W.Kick(k0=0.0003), seed=42)]
-    b_subs = [random_subsim(cb, (2, 1, 1), (0.3, 0.6, 0.1), 0.08, 3, W.Kick(k0=0.002), seed=43)]
+    b_subs = [random_subsim(cb, (2, 1, 1), (0.3, 0.6, 0.1), 0.08, 3, W.Kick(k0=0.002), seed=43),
+              random_subsim(cb, (1, 1, 2), (0.8, 0.4, 0.55), 0.08, 4, W.Kick(k0=0.0001), seed=45)]
     return [(ca, a_subs), (cb, b_subs)]
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_mixed_cells_uneven(precision):
-    """Cell A (16^3, 16 bands) and cell B (32^3, 64 atoms; 8 of its bands) with
-    subgrids of 2, 3 and 2 k-points, kicks 5e-3 / 3e-4 / 2e-3 and budgets 4, 2, 3
-    in one context; every sub-simulation matches its own oracle run."""
+    """Two sub-simulations of cell A (16^3, 16 bands) and two of cell B (32^3, 64
+    atoms; 8 of its bands) with subgrids of 2, 3, 2 and 2 k-points, kicks 5e-3 /
+    3e-4 / 2e-3 / 1e-4 and budgets 4, 2, 3, 4 in one context; every sub-simulation
+    matches its own oracle run."""
     groups = _mixed_groups()
     P, ids = _context(precision, groups)
     P.propagate(4)
-    assert [P.step(i[1]) for i in ids] == [4, 2, 3]
+    assert [P.step(i[1]) for i in ids] == [4, 2, 3, 4]
     jt, rt = BARS[precision]
     for n, (_, sid, c, s) in enumerate(ids):
         errs = compare(_gpu_result(P, sid), _oracle(("mixed", n), c, s), jt, rt)
