@@ -763,7 +763,7 @@ def main():
                "autotune": {"variant": tuned_variant, "n_variants": tuned_n, "variants_timed": n_tried,
                             "ms_per_step": tuned_ms,
                             "variants": "0 whole step in one launch (z contractions on tcgen05), 1 fused stage "
-                                        "per launch (tcgen05), 2 z-march stage with CUDA-core projections, 3 whole "
+                                        "per launch (mma.sync), 2 z-march stage with CUDA-core projections, 3 whole "
                                         "step with the z contractions on mma.sync" if tuned_n == 4 else None},
                "clocks": clk.summary(),
                "fp64_gpu": fp64,
