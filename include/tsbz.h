@@ -220,7 +220,9 @@ int tsbz_set_graphs(tsbz_ctx* ctx, int on);
  * replaced by an orthonormal basis of the converged occupied space (the
  * density, the current and every propagated observable depend on that space
  * only); rho, v_Hxc and J(0-) are then recomputed from them.  TSBZ_FP64
- * contexts, at most 32 bands per cell, before the first step.  *iters_out and
+ * contexts, at most 256 bands per cell (TSBZ_EINVAL beyond), before the first
+ * step.  Device scratch: five n_units n_b^2 complex matrices of the largest
+ * cell, from the context's allocator.  *iters_out and
  * *err_out (nullable): iterations done and the last density error.  Returns
  * TSBZ_ESTATE when max_iter iterations did not converge. */
 int tsbz_ground_state(tsbz_ctx* ctx, int max_iter, double tol, int degree, double mix, int* iters_out,

@@ -1459,24 +1459,28 @@ int tsbz_ground_state(tsbz_ctx* ctx, int max_iter, double tol, int degree, doubl
     if (hs.steps != 0) return set_err(ctx, TSBZ_ESTATE, "the ground state is solved before the first step");
   }
   int max_units = 0;
+  size_t max_mat = 0;   // complex entries of one cell's n_units n_b^2 matrices
   for (auto& hc : ctx->cells) {
     if (hc.dev.n_bands > scf_max_bands())
-      return set_err(ctx, TSBZ_EINVAL, "the ground-state solver takes at most 32 bands per cell");
+      return set_err(ctx, TSBZ_EINVAL, "the ground-state solver takes at most 256 bands per cell");
     max_units = std::max(max_units, (int)hc.unit_ids.size());
+    max_mat = std::max(max_mat, hc.unit_ids.size() * (size_t)hc.dev.n_bands * hc.dev.n_bands);
   }
   int rc = ensure_ready(ctx);
   if (rc) return rc;
   const size_t ns = ctx->subs.size();
   // scratch: Gram matrices, coefficients, bounds
-  void *dS = nullptr, *dH = nullptr, *dC = nullptr;
+  void *dS = nullptr, *dH = nullptr, *dC = nullptr, *dW1 = nullptr, *dW2 = nullptr;
   double *dlam = nullptr, *dfa = nullptr, *dfb = nullptr, *dfc = nullptr;
   int* dbad = nullptr;
-  const size_t mat = (size_t)max_units * 32 * 32 * sizeof(double2);
+  const size_t mat = std::max<size_t>(max_mat, 1) * sizeof(double2);
   auto cleanup = [&]() {
-    for (void* p : {dS, dH, dC, (void*)dlam, (void*)dfa, (void*)dfb, (void*)dfc, (void*)dbad}) dfree(ctx, p);
+    for (void* p : {dS, dH, dC, dW1, dW2, (void*)dlam, (void*)dfa, (void*)dfb, (void*)dfc, (void*)dbad})
+      dfree(ctx, p);
     ctx->d_filt = nullptr;
   };
   if ((rc = dalloc(ctx, mat, &dS)) || (rc = dalloc(ctx, mat, &dH)) || (rc = dalloc(ctx, mat, &dC)) ||
+      (rc = dalloc(ctx, mat, &dW1)) || (rc = dalloc(ctx, mat, &dW2)) ||
       (rc = dalloc_t(ctx, (size_t)max_units, &dlam)) || (rc = dalloc_t(ctx, 3 * (size_t)ctx->n_units, &dfa)) ||
       (rc = dalloc_t(ctx, 3 * (size_t)ctx->n_units, &dfb)) || (rc = dalloc_t(ctx, 3 * (size_t)ctx->n_units, &dfc)) ||
       (rc = dalloc_t(ctx, 1, &dbad))) {
@@ -1495,22 +1499,41 @@ int tsbz_ground_state(tsbz_ctx* ctx, int max_iter, double tol, int degree, doubl
     launch_stage<double>(L, in, out, prev, ctx->P, 0, ctx->stream);
     ctx->launches += 2;
   };
-  // Rayleigh-Ritz bound and orthonormalisation of the block in `y` (h y into `hy`)
+  // Orthonormalisation of the block in `y` by shifted CholeskyQR3, then the
+  // largest Ritz value from h applied to the orthonormal block.  The three
+  // rotations alternate y -> hy -> y -> hy, h Q goes into `y`, and the result
+  // is copied back into `y` once every cell is done.  The first pass shifts
+  // the Gram matrix by 11 (m n + n (n + 1)) u tr(S) (m points, n bands,
+  // u = 2^-53).
   std::vector<double> lam_u(ctx->n_units, 0.0);
   auto orthonormalise = [&](void* y, void* hy) -> int {
     for (auto& hc : ctx->cells) {
       if (hc.unit_ids.empty()) continue;
-      apply(hc, dfc, y, hy, nullptr);
       LaunchSet L = make_set(ctx, hc);
-      launch_scf_gram(L, y, hy, dS, dH, ctx->stream);
-      launch_scf_ortho(L.n_units, hc.dev.n_bands, dS, dH, dC, dlam, dbad, ctx->stream);
-      launch_scf_rotate(L, y, dC, ctx->stream);
-      ctx->launches += 3;
+      const int nb = hc.dev.n_bands;
+      const double m = (double)hc.dev.npts, n = (double)nb;
+      const double shift_coef = 11.0 * (m * n + n * (n + 1.0)) * std::ldexp(1.0, -53);
+      void* src = y;
+      void* dst = hy;
+      for (int pass = 0; pass < 3; ++pass) {
+        launch_scf_gram(L, src, nullptr, dS, nullptr, ctx->stream);
+        launch_scf_ortho(L.n_units, nb, pass == 0 ? shift_coef : 0.0, 0, dS, dH, dC, dW1, dW2, dlam, dbad,
+                         ctx->stream);
+        launch_scf_rotate(L, src, dC, dst, ctx->stream);
+        std::swap(src, dst);
+      }
+      // the orthonormal block is in `src` (= hy); h Q into `dst` (= y)
+      apply(hc, dfc, src, dst, nullptr);
+      L = make_set(ctx, hc);
+      launch_scf_gram(L, src, dst, dS, dH, ctx->stream);
+      launch_scf_ortho(L.n_units, nb, 0.0, 1, dS, dH, dC, dW1, dW2, dlam, dbad, ctx->stream);
+      ctx->launches += 11;
       std::vector<double> lam(L.n_units);
       CK(cudaMemcpyAsync(lam.data(), dlam, sizeof(double) * lam.size(), cudaMemcpyDeviceToHost, ctx->stream));
       CK(cudaStreamSynchronize(ctx->stream));
       for (size_t i = 0; i < lam.size(); ++i) lam_u[hc.unit_ids[i]] = lam[i];
     }
+    CK(cudaMemcpyAsync(y, hy, ctx->psi_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
     return TSBZ_OK;
   };
   // upper bound of the spectrum of h_k (A = 0) per unit: FD kinetic with the

@@ -175,9 +175,13 @@ void launch_stage_v(const LaunchSet& L, const void* tin, void* tout, void* psi, 
 // Ground-state solver (tsbz_scf.cu).
 int scf_max_bands();
 void launch_scf_gram(const LaunchSet& L, const void* Y, const void* HY, void* S, void* H, void* stream);
-void launch_scf_ortho(int n_units, int nb, const void* S, const void* H, void* C, double* lam, int* bad,
-                      void* stream);
-void launch_scf_rotate(const LaunchSet& L, void* Y, const void* C, void* stream);
+// HY null: S only.  S, H, C, W1, W2: n_units n_b^2 complex each;
+// C = L^{-H} with S + shift_coef tr(S) I = L L^H; with want_lam, H is
+// replaced by L^{-1} H L^{-H} and lam receives its largest eigenvalue
+void launch_scf_ortho(int n_units, int nb, double shift_coef, int want_lam, const void* S, void* H, void* C,
+                      void* W1, void* W2, double* lam, int* bad, void* stream);
+// Yout = Y C per unit (out of place)
+void launch_scf_rotate(const LaunchSet& L, const void* Y, const void* C, void* Yout, void* stream);
 
 bool sep_supported(const CellDev& c);
 int sep_variants(const CellDev& c);   // kernel variants of the single-precision path on this cell

@@ -61,3 +61,121 @@ def test_ground_state_matches_oracle_scf():
         assert np.max(np.abs(X.conj().T @ X - np.eye(cell.n_bands))) <= 1e-10
         sv = np.linalg.svd(Q.conj().T @ X, compute_uv=False)
         assert np.min(sv) >= 1 - 1e-6
+
+
+# Cells with more than one 32-band tile of the Gram and factorisation kernels,
+# Gamma only: the two-atom cell with 33 = 32 + 1 bands (self-consistent gap
+# 0.088 Ha above the last occupied state) and the free-electron cell with the
+# 57 = 32 + 25 plane waves of the closed shells |n|^2 <= 5 (gap 0.40 Ha to the
+# |n|^2 = 6 shell).
+WIDE = (dict(n=(8, 8, 8), a=(6.0, 6.0, 6.0), n_bands=33, atoms="pair"),
+        dict(n=(12, 12, 12), a=(7.0, 7.0, 7.0), n_bands=57, atoms="none"))
+
+
+def _shell_leak(u, n, n_b):
+    """Largest norm share of a band outside the plane waves with |n|^2 <= 5."""
+    f = np.fft.fftn(u.reshape((n_b,) + n[::-1]), axes=(-3, -2, -1))
+    ii = [np.fft.fftfreq(m, 1.0 / m) for m in n[::-1]]
+    z, y, x = np.meshgrid(*ii, indexing="ij")
+    outside = (x * x + y * y + z * z) > 5
+    p = np.abs(f) ** 2
+    return float(np.max(np.sum(p[:, outside], axis=1) / np.sum(p, axis=(-3, -2, -1))))
+
+
+def test_ground_state_beyond_32_bands():
+    """Two cells of 33 and 57 bands solved together: density against the
+    oracle's SCF, orthonormal orbitals spanning the oracle's occupied space,
+    the free-electron closed form (uniform density N_e / Omega, the closed
+    plane-wave shells), and the kicked propagation from each ground state."""
+    from paper_2112_00920_gb300 import Propagator, shifted_kpoints
+    dt, n = 0.08, 5
+    P = Propagator("fp64")
+    runs = []
+    for i, spec in enumerate(WIDE):
+        cell = W.cell_tiny(**spec)
+        k = kpoints.kpoints_cartesian(cell.a, (1, 1, 1), (0.0, 0.0, 0.0))
+        gs = scf.ground_state(cell, k, seed=3, tol=1e-9)
+        cid = P.add_cell_spec(cell)
+        sid = P.add_subsim(cid, shifted_kpoints(cell.a, (1, 1, 1), (0.0, 0.0, 0.0)), dt, n)
+        runs.append((cell, k, gs, sid))
+    for i, (cell, k, gs, sid) in enumerate(runs):
+        g = Grid(cell)
+        P.load_ground_state(sid, W.random_orbitals(1, cell.n_bands, cell.n, g.dv, seed=31 + i))
+    iters, err = P.ground_state(max_iter=150, tol=1e-9)
+    print("GPU SCF iterations", iters, "error", err)
+    assert err <= 1e-9
+    for cell, k, gs, sid in runs:
+        g = Grid(cell)
+        rho = P.density(sid)
+        rel = np.max(np.abs(rho - gs["rho"])) / np.max(gs["rho"])
+        u_gpu, _ = P.get_state(sid)
+        X = u_gpu[0].reshape(cell.n_bands, -1).T * np.sqrt(g.dv)
+        Q = gs["u"][0].reshape(cell.n_bands, -1).T * np.sqrt(g.dv)
+        orth = np.max(np.abs(X.conj().T @ X - np.eye(cell.n_bands)))
+        smin = np.min(np.linalg.svd(Q.conj().T @ X, compute_uv=False))
+        print(f"{cell.n_bands} bands: density vs oracle {rel:.2e}, orthonormality {orth:.2e}, "
+              f"smallest principal cosine {smin:.12f}")
+        assert rel <= 1e-7
+        assert orth <= 1e-10
+        assert smin >= 1 - 1e-6
+        if not cell.use_projectors:
+            rho0 = cell.occ * cell.n_bands / g.omega
+            uni = float(np.max(np.abs(rho - rho0)) / rho0)
+            leak = _shell_leak(u_gpu[0], cell.n, cell.n_bands)
+            print(f"free electrons: density vs N_e / Omega {uni:.2e}, weight outside the shells {leak:.2e}")
+            assert uni <= 1e-8
+            assert leak <= 1e-10
+        P.set_kick(sid, 0.005, (1.0, 0.0, 0.0))
+    P.propagate(n)
+    for cell, k, gs, sid in runs:
+        J, _ = P.current(sid)
+        a = dynamics.field_samples(W.Kick(k0=0.005), dt, n)
+        o = dynamics.propagate(cell, k, gs["u"], dt, n, a, keep_state=False)
+        ej = analysis.err_j(J, o["J"])
+        print(f"{cell.n_bands} bands: err_J of the two ground states' propagations {ej:.2e}")
+        assert ej <= 1e-7
+    P.close()
+
+
+def test_ground_state_cell_b_128_bands():
+    """The 64-atom, 128-band cell B at Gamma (32^3 grid, four band tiles):
+    the converged block is orthonormal, its density is the library's rho,
+    and it spans an invariant subspace of h[rho] built by the oracle from
+    that density (the Kohn-Sham condition; the eigenvalues are not needed:
+    the residual h Y - Y (Y^H h Y dV) vanishes for the exact occupied space)."""
+    from paper_2112_00920_gb300 import Propagator, shifted_kpoints
+    from oracle.cell import local_potential, phased_projectors, projector_tables
+    from oracle.hamiltonian import apply_h
+    from oracle.hxc import v_hxc
+    import time
+    cell = W.cell_b()
+    g = Grid(cell)
+    P = Propagator("fp64")
+    cid = P.add_cell_spec(cell)
+    sid = P.add_subsim(cid, shifted_kpoints(cell.a, (1, 1, 1), (0.0, 0.0, 0.0)), 0.08, 1)
+    P.load_ground_state(sid, W.random_orbitals(1, cell.n_bands, cell.n, g.dv, seed=41))
+    t0 = time.perf_counter()
+    iters, err = P.ground_state(max_iter=150, tol=1e-8)
+    secs = time.perf_counter() - t0
+    print(f"cell B GPU SCF: {iters} iterations, error {err:.2e}, {secs:.1f} s")
+    assert err <= 1e-8
+    u, _ = P.get_state(sid)
+    rho = P.density(sid)
+    P.close()
+    nb = cell.n_bands
+    X = u[0].reshape(nb, -1)
+    orth = np.max(np.abs(g.dv * (X.conj() @ X.T) - np.eye(nb)))
+    drho = np.max(np.abs(scf.density_from(cell, u) - rho)) / np.max(rho)
+    beta, disp, e_kb = projector_tables(cell)
+    q = np.zeros(3)
+    v_eff = local_potential(cell) + v_hxc(g, rho)
+    hu = apply_h(g, u[0], q, v_eff, phased_projectors(cell, beta, disp, q), e_kb).reshape(nb, -1)
+    hs = g.dv * (X.conj() @ hu.T)
+    r = hu - hs.T @ X
+    res = float(np.max(np.sqrt(g.dv * np.sum(np.abs(r) ** 2, axis=1))))
+    herm = float(np.max(np.abs(hs - hs.conj().T)))
+    print(f"orthonormality {orth:.2e}, density {drho:.2e}, block residual {res:.2e}, "
+          f"Hermiticity of Y^H h Y {herm:.2e}")
+    assert orth <= 1e-10
+    assert drho <= 1e-12
+    assert res <= 1e-6
