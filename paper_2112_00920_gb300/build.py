@@ -19,7 +19,7 @@ LIB = os.path.join(BUILD, "libtsbz.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["tsbz_api.cu", "tsbz_kernels_f64.cu", "tsbz_kernels_f32.cu", "tsbz_tc.cu", "tsbz_sep.cu", "tsbz_noalloc.cu",
-              "tsbz_scf.cu", "tsbz_probe.cu", "tsbz_umma.cu"]
+              "tsbz_scf.cu", "tsbz_probe.cu", "tsbz_umma.cu", "tsbz_slab.cu"]
 CPP_SOURCES = ["tsbz_host.cpp"]
 
 

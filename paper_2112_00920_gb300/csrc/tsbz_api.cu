@@ -535,13 +535,20 @@ template <typename T> int run_stages(tsbz_ctx* ctx, bool fresh_p, int same_next_
       }
       continue;
     }
+    // single precision on 32-point rows: variant 0 is the slab z-march stage, the
+    // point-parallel stage takes the variants after it
+    const bool slab = ctx->precision == TSBZ_FP32 && slab_supported(hc.dev);
+    LaunchSet Lp = L;
+    if (slab && L.variant > 0) Lp.variant = L.variant == 3 ? 0 : L.variant;
     for (int m = 1; m <= 4; ++m) {
       ev_start(ctx, FAM_BRA);
-      launch_bra<T>(L, srcs[m - 1], ctx->P, 0, 0, ctx->stream);
+      if (!(slab && launch_bra_slab(L, srcs[m - 1], ctx->P, ctx->stream)))
+        launch_bra<T>(L, srcs[m - 1], ctx->P, 0, 0, ctx->stream);
       ev_stop(ctx);
       if (hc.dev.use_proj) ++ctx->launches;
       ev_start(ctx, FAM_STAGE);
-      launch_stage<T>(L, srcs[m - 1], dsts[m - 1], ctx->psi, ctx->P, m, ctx->stream);
+      if (!(slab && launch_stage_slab(L, srcs[m - 1], dsts[m - 1], ctx->psi, ctx->P, m, ctx->stream)))
+        launch_stage<T>(Lp, srcs[m - 1], dsts[m - 1], ctx->psi, ctx->P, m, ctx->stream);
       ev_stop(ctx);
       ++ctx->launches;
     }
@@ -735,6 +742,9 @@ int sync_and_check(tsbz_ctx* ctx) {
 //   point-parallel path (FP64, and FP32 on shapes without a z-march kernel):
 //     bands per staged projection chunk 8 (0), 4 (1), 16 (2, when its shared
 //     memory fits);
+//   FP32 on grids with 32-point rows (slab_supported): 0 slab z-march stage,
+//     then the point-parallel stage with 4 (1), 16 (2, when it fits) or 8 (3)
+//     bands per chunk;
 //   FP32_TC on 16^3 grids: stage with the band of t bulk-staged in shared
 //     memory and V, psi read per plane (0) or bulk-staged too (1), z-march
 //     stage with a halo plane per z (2);
@@ -744,6 +754,7 @@ int n_variants(const tsbz_ctx* ctx, const HostCell& hc) {
   if (ctx->precision == TSBZ_FP32_TC) return (c.n1 == 16 && c.n2 == 16 && c.n3 == 16) ? 3 : 1;
   if (ctx->precision == TSBZ_FP32 && sep_supported(c)) return sep_variants(c);
   const size_t big = (size_t)16 * (c.n_proj > 0 ? c.n_proj : 1) * ctx->elem_size();
+  if (ctx->precision == TSBZ_FP32 && slab_supported(c)) return big <= 160 * 1024 ? 4 : 2;
   return big <= 160 * 1024 ? 3 : 2;
 }
 
@@ -1028,18 +1039,42 @@ int tsbz_init_cell(tsbz_ctx* ctx, const tsbz_cell_desc* d, int* cell_id) {
     c.pbox_ok = ok ? 1 : 0;
   }
   // z groups: atoms with bit-identical z rows of the float factor tables
+  const int nm_z = c.nmax;
+  auto same_z = [&](int a, int b) {
+    for (int i = 0; i < nm_z; ++i) {
+      const size_t ia = (size_t)(a * 3 + 2) * nm_z + i, ib = (size_t)(b * 3 + 2) * nm_z + i;
+      if (g1f[ia] != g1f[ib] || d1f[ia] != d1f[ib]) return false;
+    }
+    return true;
+  };
+  c.zs_n = 0;
+  for (int i = 0; i <= 8; ++i) c.zs_off[i] = 0;
+  for (int i = 0; i < 64; ++i) c.zs_mem[i] = 0;
+  if (c.use_proj && d->n_atoms <= 64) {
+    std::vector<int> rep, grp(d->n_atoms, -1);
+    for (int a = 0; a < d->n_atoms; ++a) {
+      for (size_t h = 0; h < rep.size() && grp[a] < 0; ++h)
+        if (same_z(a, rep[h])) grp[a] = (int)h;
+      if (grp[a] < 0) {
+        grp[a] = (int)rep.size();
+        rep.push_back(a);
+      }
+    }
+    if (rep.size() <= 8) {
+      c.zs_n = (int)rep.size();
+      int k = 0;
+      for (int g = 0; g < c.zs_n; ++g) {
+        c.zs_off[g] = k;
+        for (int a = 0; a < d->n_atoms; ++a)
+          if (grp[a] == g) c.zs_mem[k++] = a;
+      }
+      for (int g = c.zs_n; g <= 8; ++g) c.zs_off[g] = k;
+    }
+  }
   c.n_zg = 0;
   for (int i = 0; i < 8; ++i) c.zg_of[i] = c.zg_rep[i] = c.zg_mem[i] = 0;
   for (int i = 0; i <= 8; ++i) c.zg_off[i] = 0;
   if (c.use_proj && d->n_atoms <= 8) {
-    const int nm = c.nmax;
-    auto same_z = [&](int a, int b) {
-      for (int i = 0; i < nm; ++i) {
-        const size_t ia = (size_t)(a * 3 + 2) * nm + i, ib = (size_t)(b * 3 + 2) * nm + i;
-        if (g1f[ia] != g1f[ib] || d1f[ia] != d1f[ib]) return false;
-      }
-      return true;
-    };
     for (int a = 0; a < 8; ++a) c.zg_of[a] = 0;
     for (int a = 0; a < d->n_atoms; ++a) {
       int g = -1;

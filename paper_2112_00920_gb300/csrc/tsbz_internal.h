@@ -60,6 +60,11 @@ struct CellDev {
   int zg_rep[8];      // first atom of group g
   int zg_off[9];      // members of group g: zg_mem[zg_off[g] .. zg_off[g + 1])
   int zg_mem[8];
+  // the same grouping for cells of up to 64 atoms in at most 8 groups (the slab
+  // stage of 32-point rows; zs_n = 0 when the cell has more groups or atoms)
+  int zs_n;
+  int zs_off[9];      // members of group g: zs_mem[zs_off[g] .. zs_off[g + 1])
+  int zs_mem[64];
 };
 
 // Whether the finalize spreads one unit over a whole CTA (units with many
@@ -182,6 +187,14 @@ void launch_scf_ortho(int n_units, int nb, double shift_coef, int want_lam, cons
                       void* W1, void* W2, double* lam, int* bad, void* stream);
 // Yout = Y C per unit (out of place)
 void launch_scf_rotate(const LaunchSet& L, const void* Y, const void* C, void* Yout, void* stream);
+
+// Slab z-march stage for float orbitals on grids with 32-point rows (tsbz_slab.cu):
+// variant 0 of such cells; false (nothing launched) otherwise.
+bool slab_supported(const CellDev& c);
+bool launch_stage_slab(const LaunchSet& L, const void* tin, void* tout, void* psi, const void* P, int m,
+                       void* stream);
+// Projections P of float orbitals on the same cells (variant 0, q_half tables).
+bool launch_bra_slab(const LaunchSet& L, const void* src, void* P, void* stream);
 
 bool sep_supported(const CellDev& c);
 int sep_variants(const CellDev& c);   // kernel variants of the single-precision path on this cell

@@ -1,7 +1,8 @@
 """GPU: uneven batches in one context, and the autotuner.
 
 Sub-simulations of different cells (the 16^3 cell A on the fused stage
-kernels, the 32^3, 64-atom cell B on the point-parallel kernels), different
+kernels, the 32^3, 64-atom cell B on the slab z-march stage in single
+precision and the point-parallel kernels in FP64), different
 subgrid sizes and different step budgets advance together through the C ABI;
 each is compared with the oracle run on its own.  The autotuner's trial steps
 must leave the state bit for bit as it was, and every kernel variant it can
@@ -135,7 +136,7 @@ def test_autotune_restores_state_and_keeps_parity(precision):
     P.propagate(1)
     before = [(P.get_state(sid), P.density(sid), P.norms(sid), P.current(sid)) for _, sid, _, _ in ids]
     n = P.autotune(budget_ms=60000)
-    assert n >= 6   # cell A: 3 variants; cell B: 3
+    assert n >= 6   # cell A: 3 or more variants; cell B: 3 (FP64) or 4 (FP32)
     for (_, sid, _, _), (st, rho, nr, cur) in zip(ids, before):
         st2 = P.get_state(sid)
         assert st2[1] == st[1] == 1
@@ -175,6 +176,11 @@ VARIANT_CASES = [
     ("fp32", lambda: _cube16(_Z_THREE), (1, 2, 1), 2),
     ("fp32", _tiny, (2, 2, 1), 2),                    # bulk-staged 8^3 stage / z-march
     ("fp32", lambda: W.cell_tiny(atoms="offgrid", n=(10, 12, 14), a=(7.0, 8.0, 9.0), n_bands=3), (3, 1, 1), 3),
+    # 32-point rows: slab z-march stage / point-parallel with 4, 16, 8 bands per chunk
+    ("fp32", lambda: W.cell_b(n_bands=4), (1, 1, 2), 4),   # 64 atoms in 8 z groups
+    # (grid spacings near cell B's 0.64 bohr: dt = 0.08 stays inside the Taylor-4 stability bound)
+    ("fp32", lambda: W.cell_tiny(atoms="offgrid", n=(32, 16, 24), a=(20.0, 10.0, 15.0), n_bands=3), (2, 1, 1), 4),
+    ("fp32", lambda: W.cell_tiny(atoms="none", n=(32, 16, 16), a=(20.0, 10.0, 10.5), n_bands=3), (1, 2, 1), 4),
     ("fp64", _tiny, (2, 2, 1), 3),                    # point-parallel: 8, 4, 16 bands per chunk
     ("fp32_tc", W.cell_a, (2, 1, 1), 3),              # bulk-staged stencil stage (t; t, V, psi) / halo-plane z-march
     ("fp32_tc", lambda: W.cell_tiny(atoms="offgrid", n=(10, 12, 16), a=(7.0, 8.0, 9.0), n_bands=3), (3, 1, 1), 1),
