@@ -49,6 +49,9 @@ struct SlSmem {
   float2 pr[SL_R][SL_T];      // psi on the slab's rows (stages m >= 2)
   float vr[SL_R][SL_T];       // v_eff on the slab's rows
   float4 fz[SL_G][SL_MAXZ];   // (Re f_g, Im f_g, d_g, 0) per (group, plane)
+  float4 xt[64][SL_N1];       // (Re g_x ph_x, Im g_x ph_x, d_x, g_x) per (atom, x)
+  float4 yt[64][SL_SY];       // the same in y on the slab's rows
+  float2 wt[64][4];           // W_aj = pnorm_j E_j P_aj
   unsigned long long bar[SL_R];
 };
 
@@ -149,36 +152,29 @@ __global__ void __launch_bounds__(SL_T, 2) k_stage_slab(LaunchSet L, const float
     }
     sm.fz[g][z] = e;
   }
-  // C_g0, C_g1 of this column from the projections of t_{m-1}
-  float2 C0[G > 0 ? G : 1], C1[G > 0 ? G : 1];
-#pragma unroll
-  for (int g = 0; g < (G > 0 ? G : 1); ++g) C0[g] = C1[g] = make_float2(0.f, 0.f);
-  if (c.use_proj) {
+  // per-atom factor rows in x (all columns) and y (the slab's rows), and W, for
+  // the non-local coefficients below (coalesced loads, then shared memory)
+  const int na = c.use_proj ? c.n_atoms : 0;
+  if (na) {
     const float2* Pb = P + U.p_off + (long long)b * c.n_proj;
-#pragma unroll
-    for (int g = 0; g < G; ++g) {
-      if (g >= c.zs_n) break;
-      for (int j = c.zs_off[g]; j < c.zs_off[g + 1]; ++j) {
-        const int a = c.zs_mem[j];
-        const long long ox = (long long)(a * 3) * nm + ix, oy = (long long)(a * 3 + 1) * nm + iy;
-        const float gy = c.g1f[oy];   // the same for the whole warp (one grid row)
-        if (gy == 0.f) continue;      // the row is outside the atom's projector box
-        const float gxy = c.g1f[ox] * gy;
-        if (gxy == 0.f) continue;     // the column is outside it in x
-        const float dx = c.d1f[ox], dy = c.d1f[oy];
-        const float2 pxy = sl_cmul(ph[ox], ph[oy]);
-        const float2 f = make_float2(gxy * pxy.x, -gxy * pxy.y);   // g_x g_y conj(ph_x ph_y)
-        const float* wk = c.wkbf + 4 * a;
-        const float2 p0 = Pb[4 * a], p1 = Pb[4 * a + 1], p2 = Pb[4 * a + 2], p3 = Pb[4 * a + 3];
-        const float2 w = make_float2(wk[0] * p0.x + dx * (wk[1] * p1.x) + dy * (wk[2] * p2.x),
-                                     wk[0] * p0.y + dx * (wk[1] * p1.y) + dy * (wk[2] * p2.y));
-        const float2 w3 = make_float2(wk[3] * p3.x, wk[3] * p3.y);
-        const float2 a0 = sl_cmul(f, w), a1 = sl_cmul(f, w3);
-        C0[g].x += a0.x;
-        C0[g].y += a0.y;
-        C1[g].x += a1.x;
-        C1[g].y += a1.y;
-      }
+    for (int i = tid; i < na * SL_N1; i += SL_T) {
+      const int a = i / SL_N1, x = i - a * SL_N1;
+      const long long o = (long long)(a * 3) * nm + x;
+      const float g = c.g1f[o];
+      const float2 q = ph[o];
+      sm.xt[a][x] = make_float4(g * q.x, g * q.y, c.d1f[o], g);
+    }
+    for (int i = tid; i < na * SL_SY; i += SL_T) {
+      const int a = i / SL_SY, r = i - a * SL_SY;
+      const long long o = (long long)(a * 3 + 1) * nm + slab * SL_SY + r;
+      const float g = c.g1f[o];
+      const float2 q = ph[o];
+      sm.yt[a][r] = make_float4(g * q.x, g * q.y, c.d1f[o], g);
+    }
+    for (int i = tid; i < 4 * na; i += SL_T) {
+      const float2 p = Pb[i];
+      const float w = c.wkbf[i];
+      sm.wt[i >> 2][i & 3] = make_float2(w * p.x, w * p.y);
     }
   }
   const float* qt = reinterpret_cast<const float*>(L.qt_half) + 4 * u;
@@ -196,7 +192,34 @@ __global__ void __launch_bounds__(SL_T, 2) k_stage_slab(LaunchSet L, const float
     xo[mm - 1] = (ry + ND) * SL_N1 + ((ix + mm) & (SL_N1 - 1));
     xo[ND + mm - 1] = (ry + ND) * SL_N1 + ((ix - mm) & (SL_N1 - 1));
   }
-  __syncthreads();   // the barriers are initialised and the f table written before anyone reads them
+  __syncthreads();   // the barriers are initialised and the tables written before anyone reads them
+  // C_g0, C_g1 of this column from the projections of t_{m-1}
+  float2 C0[G > 0 ? G : 1], C1[G > 0 ? G : 1];
+#pragma unroll
+  for (int g = 0; g < (G > 0 ? G : 1); ++g) C0[g] = C1[g] = make_float2(0.f, 0.f);
+  if (na) {
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      if (g >= c.zs_n) break;
+      for (int j = c.zs_off[g]; j < c.zs_off[g + 1]; ++j) {
+        const int a = c.zs_mem[j];
+        const float4 ey = sm.yt[a][ry];   // the same for the whole warp (one grid row)
+        if (ey.w == 0.f) continue;         // the row is outside the atom's projector box
+        const float4 ex = sm.xt[a][ix];
+        if (ex.w == 0.f) continue;         // the column is outside it in x
+        // g_x g_y conj(ph_x ph_y) = conj(e_x e_y), e = g ph
+        const float2 exy = sl_cmul(make_float2(ex.x, ex.y), make_float2(ey.x, ey.y));
+        const float2 f = make_float2(exy.x, -exy.y);
+        const float2 w0 = sm.wt[a][0], w1 = sm.wt[a][1], w2 = sm.wt[a][2], w3 = sm.wt[a][3];
+        const float2 w = make_float2(w0.x + ex.z * w1.x + ey.z * w2.x, w0.y + ex.z * w1.y + ey.z * w2.y);
+        const float2 a0 = sl_cmul(f, w), a1 = sl_cmul(f, w3);
+        C0[g].x += a0.x;
+        C0[g].y += a0.y;
+        C1[g].x += a1.x;
+        C1[g].y += a1.y;
+      }
+    }
+  }
   // the queue t(z - 4 .. z + 4) of this column: planes -4 .. 3 first (slots 0 .. 7, the first fill)
   float2 qv[2 * ND + 1];
   bool ok = true;
