@@ -431,7 +431,7 @@ template <typename T> int run_observe(tsbz_ctx* ctx, int fin_mode) {
         launch_bra_tc(L, ctx->psi, ctx->Pa, 1, ctx->stream);
       else if (sep)
         launch_bra_sep(L, ctx->psi, ctx->Pa, 1, 1, ctx->stream);
-      else
+      else if (!(ctx->precision == TSBZ_FP32 && launch_bra_slab(L, ctx->psi, ctx->Pa, 1, 1, ctx->stream)))
         launch_bra<T>(L, ctx->psi, ctx->Pa, 1, 1, ctx->stream);
       ev_stop(ctx);
       if (hc.dev.use_proj) ++ctx->launches;
@@ -542,7 +542,7 @@ template <typename T> int run_stages(tsbz_ctx* ctx, bool fresh_p, int same_next_
     if (slab && L.variant > 0) Lp.variant = L.variant == 3 ? 0 : L.variant;
     for (int m = 1; m <= 4; ++m) {
       ev_start(ctx, FAM_BRA);
-      if (!(slab && launch_bra_slab(L, srcs[m - 1], ctx->P, ctx->stream)))
+      if (!(slab && launch_bra_slab(L, srcs[m - 1], ctx->P, 0, 0, ctx->stream)))
         launch_bra<T>(L, srcs[m - 1], ctx->P, 0, 0, ctx->stream);
       ev_stop(ctx);
       if (hc.dev.use_proj) ++ctx->launches;

@@ -317,21 +317,34 @@ __global__ void __launch_bounds__(SL_T, 2) k_stage_slab(LaunchSet L, const float
 // its first CTA adds the slabs' partial projections from distributed shared
 // memory in slab order.
 // ----------------------------------------------------------------------------
-struct SbSmem {
+// KD z moments per column: 2 for P (monomials 1, d_x, d_y, d_z), 3 for the
+// current's Pa (the monomials of degree <= 2: each projector monomial times
+// 1, d_x, d_y, d_z).  NX x sums per (atom, row): the (z power k, x power i)
+// with i + k < KD.
+template <int KD> struct SbSmem {
+  static constexpr int NX = KD == 2 ? 3 : 6;
+  static constexpr int NOUT = KD == 2 ? 4 : 16;   // outputs per atom
   float4 fb[SL_G][SL_MAXZ];      // (Re g_z ph_z, Im g_z ph_z, d_z, 0) per (group, plane)
-  float2 S[2 * SL_G][SL_T];      // z sums of the columns
-  float2 R[64][SL_SY][3];        // x sums per (atom, slab row)
-  float2 Pp[4 * 64];             // this slab's partial projections
+  float2 S[KD * SL_G][SL_T];     // z sums of the columns
+  float2 R[64][SL_SY][NX];       // x sums per (atom, slab row)
+  float2 Pp[NOUT * 64];          // this slab's partial projections
   int grp[64];                   // z group of each atom
 };
 
-template <int G>
+// x-sum index of (z power k, x power i)
+template <int KD> __device__ __forceinline__ int sb_xterm(int k, int i) {
+  if (KD == 2) return k == 0 ? i : 2;
+  return k == 0 ? i : (k == 1 ? 3 + i : 5);
+}
+
+template <int G, int KD>
 __global__ void __launch_bounds__(SL_T) k_bra_slab(LaunchSet L, const float2* __restrict__ src,
-                                                   float2* __restrict__ P) {
+                                                   float2* __restrict__ out, int use_obs) {
   namespace cg = cooperative_groups;
+  using Sm = SbSmem<KD>;
   constexpr int D = 8;   // planes of t loaded ahead
   extern __shared__ __align__(16) unsigned char sbraw[];
-  SbSmem& sm = *reinterpret_cast<SbSmem*>(sbraw);
+  Sm& sm = *reinterpret_cast<Sm*>(sbraw);
   const CellDev& c = L.cell;
   const int n2 = c.n2, n3 = c.n3, nm = c.nmax, n12 = SL_N1 * n2, na = c.n_atoms;
   const int n_slabs = n2 / SL_SY;
@@ -340,7 +353,7 @@ __global__ void __launch_bounds__(SL_T) k_bra_slab(LaunchSet L, const float2* __
   if (!unit_active(L, u)) return;   // the same for every CTA of the cluster (one unit)
   const UnitDev U = L.units[u];
   const int tid = threadIdx.x, ix = tid & (SL_N1 - 1), ry = tid / SL_N1, iy = slab * SL_SY + ry;
-  const float2* ph = (const float2*)L.ph_half + (long long)u * L.ph_stride;
+  const float2* ph = (const float2*)(use_obs ? L.ph_obs : L.ph_half) + (long long)u * L.ph_stride;
   for (int i = tid; i < SL_G * n3; i += SL_T) {
     const int g = i / n3, z = i - g * n3;
     float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -356,11 +369,13 @@ __global__ void __launch_bounds__(SL_T) k_bra_slab(LaunchSet L, const float2* __
   for (int g = 0; g < c.zs_n; ++g)
     for (int j = c.zs_off[g] + tid; j < c.zs_off[g + 1]; j += SL_T) sm.grp[c.zs_mem[j]] = g;
   __syncthreads();
-  // z sums of this column
+  // z sums of this column: S_gk = sum_z g_z ph_z d_z^k t
   const float2* col = src + U.psi_off + (long long)b * c.npts + (long long)iy * SL_N1 + ix;
-  float2 S0[G], S1[G];
+  float2 Sk[KD][G];
 #pragma unroll
-  for (int g = 0; g < G; ++g) S0[g] = S1[g] = make_float2(0.f, 0.f);
+  for (int k = 0; k < KD; ++k)
+#pragma unroll
+    for (int g = 0; g < G; ++g) Sk[k][g] = make_float2(0.f, 0.f);
   float2 tq[D];
 #pragma unroll
   for (int k = 0; k < D; ++k) tq[k] = col[(long long)k * n12];
@@ -375,81 +390,91 @@ __global__ void __launch_bounds__(SL_T) k_bra_slab(LaunchSet L, const float2* __
       for (int g = 0; g < G; ++g) {
         const float4 f = sm.fb[g][z];
         if (f.x == 0.f && f.y == 0.f) continue;   // plane z is outside the group's box (uniform)
-        const float2 ft = make_float2(f.x * t.x - f.y * t.y, f.x * t.y + f.y * t.x);
-        S0[g].x += ft.x;
-        S0[g].y += ft.y;
-        S1[g].x += f.z * ft.x;
-        S1[g].y += f.z * ft.y;
+        float2 ft = make_float2(f.x * t.x - f.y * t.y, f.x * t.y + f.y * t.x);
+#pragma unroll
+        for (int k = 0; k < KD; ++k) {
+          Sk[k][g].x += ft.x;
+          Sk[k][g].y += ft.y;
+          ft = make_float2(f.z * ft.x, f.z * ft.y);
+        }
       }
     }
   }
 #pragma unroll
-  for (int g = 0; g < G; ++g) {
-    sm.S[g][tid] = S0[g];
-    sm.S[G + g][tid] = S1[g];
-  }
+  for (int k = 0; k < KD; ++k)
+#pragma unroll
+    for (int g = 0; g < G; ++g) sm.S[k * G + g][tid] = Sk[k][g];
   __syncthreads();
-  // x sums per (atom, slab row) over the atom's box columns [sx, sx + lx) (periodic)
+  // x sums per (atom, slab row) over the atom's box columns [sx, sx + lx) (periodic):
+  // R_(k,i) = sum_x g_x ph_x d_x^i S_gk
   for (int j = tid; j < na * SL_SY; j += SL_T) {
     const int a = j / SL_SY, r = j - a * SL_SY;
     const int g = sm.grp[a];
     const int* bx = c.pbox + a * 6;
     const int sx = bx[0], lx = bx[1], sy = bx[2], ly = bx[3];
-    float2 r00 = make_float2(0.f, 0.f), r01 = r00, r10 = r00;
+    float2 rr[Sm::NX];
+#pragma unroll
+    for (int e = 0; e < Sm::NX; ++e) rr[e] = make_float2(0.f, 0.f);
     if (((slab * SL_SY + r - sy) % n2 + n2) % n2 < ly) {   // the row is in the atom's box
       for (int i = 0; i < lx; ++i) {
         const int x = (sx + i) & (SL_N1 - 1);
         const long long ox = (long long)(a * 3) * nm + x;
         const float gx = c.g1f[ox];
         const float2 px = ph[ox];
-        const float2 w = make_float2(gx * px.x, gx * px.y);
         const float dx = c.d1f[ox];
-        const float2 s0 = sm.S[g][r * SL_N1 + x], s1 = sm.S[G + g][r * SL_N1 + x];
-        const float2 ws0 = make_float2(w.x * s0.x - w.y * s0.y, w.x * s0.y + w.y * s0.x);
-        r00.x += ws0.x;
-        r00.y += ws0.y;
-        r01.x += dx * ws0.x;
-        r01.y += dx * ws0.y;
-        r10.x += w.x * s1.x - w.y * s1.y;
-        r10.y += w.x * s1.y + w.y * s1.x;
+#pragma unroll
+        for (int k = 0; k < KD; ++k) {
+          const float2 sv = sm.S[k * G + g][r * SL_N1 + x];
+          float2 w = make_float2(gx * (px.x * sv.x - px.y * sv.y), gx * (px.x * sv.y + px.y * sv.x));
+#pragma unroll
+          for (int ip = 0; ip + k < KD; ++ip) {
+            const int e = sb_xterm<KD>(k, ip);
+            rr[e].x += w.x;
+            rr[e].y += w.y;
+            w = make_float2(dx * w.x, dx * w.y);
+          }
+        }
       }
     }
-    sm.R[a][r][0] = r00;
-    sm.R[a][r][1] = r01;
-    sm.R[a][r][2] = r10;
+#pragma unroll
+    for (int e = 0; e < Sm::NX; ++e) sm.R[a][r][e] = rr[e];
   }
   __syncthreads();
-  // y sums: this slab's part of P_aj
-  for (int j = tid; j < 4 * na; j += SL_T) {
-    const int a = j >> 2, mono = j & 3;
+  // y sums: this slab's part of every output (P_aj, or Pa_aj,alpha)
+  for (int j = tid; j < Sm::NOUT * na; j += SL_T) {
+    const int a = j / Sm::NOUT, o = j - a * Sm::NOUT;
+    const int tt = KD == 2 ? o : o >> 2, al = KD == 2 ? 0 : o & 3;
+    // exponents of the monomial: the projector's (tt) plus the weight's (al)
+    const int ei = (tt == 1) + (al == 1), ej = (tt == 2) + (al == 2), ek = (tt == 3) + (al == 3);
+    const int e = sb_xterm<KD>(ek, ei);
     float2 acc = make_float2(0.f, 0.f);
     for (int r = 0; r < SL_SY; ++r) {
       const long long oy = (long long)(a * 3 + 1) * nm + slab * SL_SY + r;
       const float gy = c.g1f[oy];
       if (gy == 0.f) continue;
       const float2 py = ph[oy];
-      float2 w = make_float2(gy * py.x, gy * py.y);
-      if (mono == 2) w = make_float2(w.x * c.d1f[oy], w.y * c.d1f[oy]);
-      const float2 v = sm.R[a][r][mono == 1 ? 1 : (mono == 3 ? 2 : 0)];
-      acc.x += w.x * v.x - w.y * v.y;
-      acc.y += w.x * v.y + w.y * v.x;
+      float wy = gy;
+      for (int q = 0; q < ej; ++q) wy *= c.d1f[oy];
+      const float2 v = sm.R[a][r][e];
+      acc.x += wy * (py.x * v.x - py.y * v.y);
+      acc.y += wy * (py.x * v.y + py.y * v.x);
     }
-    const float sc = (float)c.dv * c.pnormf[j];
+    const float sc = (float)c.dv * c.pnormf[4 * a + tt];
     sm.Pp[j] = make_float2(sc * acc.x, sc * acc.y);
   }
   // the slabs' parts, added in slab order by the cluster's first CTA
   cg::cluster_group cl = cg::this_cluster();
   cl.sync();
   if (cl.block_rank() == 0) {
-    float2* Pb = P + U.p_off + (long long)b * c.n_proj;
-    for (int j = tid; j < 4 * na; j += SL_T) {
+    float2* ob = KD == 2 ? out + U.p_off + (long long)b * c.n_proj : out + U.pa_off + (long long)b * c.n_proj * 4;
+    for (int j = tid; j < Sm::NOUT * na; j += SL_T) {
       float2 v = make_float2(0.f, 0.f);
       for (int r = 0; r < n_slabs; ++r) {
         const float2 w = cl.map_shared_rank(sm.Pp, r)[j];
         v.x += w.x;
         v.y += w.y;
       }
-      Pb[j] = v;
+      ob[j] = v;
     }
   }
   cl.sync();   // the other CTAs keep their shared memory until it has been read
@@ -484,7 +509,7 @@ bool launch_stage_slab(const LaunchSet& L, const void* tin, void* tout, void* ps
   return true;
 }
 
-bool launch_bra_slab(const LaunchSet& L, const void* src, void* P, void* stream) {
+bool launch_bra_slab(const LaunchSet& L, const void* src, void* out, int with_d, int use_obs, void* stream) {
   const CellDev& c = L.cell;
   if (L.variant != 0 || !slab_supported(c) || !c.use_proj) return false;
   if (L.n_units == 0) return true;
@@ -492,7 +517,6 @@ bool launch_bra_slab(const LaunchSet& L, const void* src, void* P, void* stream)
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(c.n_bands * n_slabs, L.n_units);
   cfg.blockDim = dim3(SL_T);
-  cfg.dynamicSmemBytes = sizeof(SbSmem);
   cfg.stream = (cudaStream_t)stream;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
@@ -501,14 +525,24 @@ bool launch_bra_slab(const LaunchSet& L, const void* src, void* P, void* stream)
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  auto go = [&](auto kern) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SbSmem));
-    cudaLaunchKernelEx(&cfg, kern, L, (const float2*)src, (float2*)P);
+  auto go = [&](auto kern, size_t smem) {
+    cfg.dynamicSmemBytes = smem;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaLaunchKernelEx(&cfg, kern, L, (const float2*)src, (float2*)out, use_obs);
   };
   const int g = c.zs_n;
-  if (g == 1) go(k_bra_slab<1>);
-  else if (g == 2) go(k_bra_slab<2>);
-  else if (g <= 4) go(k_bra_slab<4>);
-  else go(k_bra_slab<8>);
+  if (with_d) {
+    const size_t sm3 = sizeof(SbSmem<3>);
+    if (g == 1) go(k_bra_slab<1, 3>, sm3);
+    else if (g == 2) go(k_bra_slab<2, 3>, sm3);
+    else if (g <= 4) go(k_bra_slab<4, 3>, sm3);
+    else go(k_bra_slab<8, 3>, sm3);
+  } else {
+    const size_t sm2 = sizeof(SbSmem<2>);
+    if (g == 1) go(k_bra_slab<1, 2>, sm2);
+    else if (g == 2) go(k_bra_slab<2, 2>, sm2);
+    else if (g <= 4) go(k_bra_slab<4, 2>, sm2);
+    else go(k_bra_slab<8, 2>, sm2);
+  }
   return true;
 }
