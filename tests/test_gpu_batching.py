@@ -209,3 +209,23 @@ def test_every_variant_parity(case):
             P.set_variant(ids[0][0], nv)
         finally:
             P.close()
+
+
+def test_mixed_graph_replay_bitwise():
+    """The mixed cell-A / cell-B batch in single precision (whole-step kernel on
+    cell A, slab stage and cluster projections on cell B) gives the same orbitals
+    and currents bit for bit whether its steps are launched directly or replayed
+    from the captured graph, and twice in a row: every reduction runs in a fixed
+    order."""
+    out = []
+    for graphs in (False, True, True):
+        P, ids = _context("fp32", _mixed_groups(), graphs=graphs)
+        P.propagate(2)
+        P.propagate(2)
+        out.append([(P.current(sid)[0], P.get_state(sid)[0], P.density(sid)) for _, sid, _, _ in ids])
+        P.close()
+    for run in out[1:]:
+        for (ja, sa, ra), (jb, sb, rb) in zip(out[0], run):
+            np.testing.assert_array_equal(ja, jb)
+            np.testing.assert_array_equal(sa, sb)
+            np.testing.assert_array_equal(ra, rb)
