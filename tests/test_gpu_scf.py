@@ -179,3 +179,38 @@ def test_ground_state_cell_b_128_bands():
     assert orth <= 1e-10
     assert drho <= 1e-12
     assert res <= 1e-6
+
+
+def test_ground_state_rejects_unsupported_contexts():
+    """The solver runs in FP64 contexts on cells of at most 256 bands and before
+    the first step: an FP32 context, a 257-band cell and a second call after a
+    step are refused with TSBZ_EINVAL / TSBZ_ESTATE and leave the context usable."""
+    from paper_2112_00920_gb300 import Propagator, TsbzError, shifted_kpoints
+    cell = W.cell_tiny(n=(8, 8, 8), a=(6.0, 6.0, 6.0), n_bands=4, atoms="pair")
+    g = Grid(cell)
+    kp = shifted_kpoints(cell.a, (1, 1, 1), (0.0, 0.0, 0.0))
+    start = W.random_orbitals(1, cell.n_bands, cell.n, g.dv, seed=5)
+    P = Propagator("fp32")
+    sid = P.add_subsim(P.add_cell_spec(cell), kp, 0.08, 2)
+    P.load_ground_state(sid, start)
+    with pytest.raises(TsbzError) as e:
+        P.ground_state(max_iter=5, tol=1e-8)
+    assert e.value.code == -1   # TSBZ_EINVAL
+    P.propagate(1)              # the context still steps
+    P.close()
+    wide = W.cell_tiny(n=(8, 8, 8), a=(6.0, 6.0, 6.0), n_bands=257, atoms="none")
+    P = Propagator("fp64")
+    sid = P.add_subsim(P.add_cell_spec(wide), kp, 0.08, 2)
+    P.load_ground_state(sid, W.random_orbitals(1, 257, wide.n, Grid(wide).dv, seed=6))
+    with pytest.raises(TsbzError) as e:
+        P.ground_state(max_iter=5, tol=1e-8)
+    assert e.value.code == -1
+    P.close()
+    P = Propagator("fp64")
+    sid = P.add_subsim(P.add_cell_spec(cell), kp, 0.08, 2)
+    P.load_ground_state(sid, start)
+    P.propagate(1)
+    with pytest.raises(TsbzError) as e:
+        P.ground_state(max_iter=5, tol=1e-8)
+    assert e.value.code == -6   # TSBZ_ESTATE: the ground state comes before the first step
+    P.close()
