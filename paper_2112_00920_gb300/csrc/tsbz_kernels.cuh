@@ -1045,9 +1045,12 @@ __global__ void k_hxc_final(const SubDev* subs, const int* sub_ids, int n_subs, 
 // ----------------------------------------------------------------------------
 #define HXC_FFT_MAXN 16
 #define HXC_FFT_MAXPTS 4096
+#define HXC_LINES_MIN_SUBS 8   // sub-simulations of a cell from which the per-axis line kernels take over
 
 // In-place radix-2 transform of the line x (length N, a power of two):
 // x[k] <- sum_n x[n] exp(sign 2 pi i n k / N); tw[m] = exp(2 pi i m / N).
+// The twiddles exp(0) = 1 and exp(sign i pi / 2) = sign i are applied exactly,
+// without a multiplication (22 of the 32 butterflies of a 16-point line).
 template <int N>
 __device__ __forceinline__ void hxc_fft_line(double2 (&x)[N], const double2* __restrict__ tw, int sign) {
 #pragma unroll
@@ -1068,10 +1071,18 @@ __device__ __forceinline__ void hxc_fft_line(double2 (&x)[N], const double2* __r
     for (int i = 0; i < N; i += len) {
 #pragma unroll
       for (int k = 0; k < half; ++k) {
-        const double2 w = tw[k * step];
-        const double wi = sign * w.y;
+        const int m = k * step;
         const double2 v = x[i + k + half];
-        const double2 vw = make_double2(v.x * w.x - v.y * wi, v.x * wi + v.y * w.x);
+        double2 vw;
+        if (m == 0) {
+          vw = v;
+        } else if (4 * m == N) {
+          vw = sign > 0 ? make_double2(-v.y, v.x) : make_double2(v.y, -v.x);
+        } else {
+          const double2 w = tw[m];
+          const double wi = sign * w.y;
+          vw = make_double2(v.x * w.x - v.y * wi, v.x * wi + v.y * w.x);
+        }
         const double2 u = x[i + k];
         x[i + k] = make_double2(u.x + vw.x, u.y + vw.y);
         x[i + k + half] = make_double2(u.x - vw.x, u.y - vw.y);
@@ -1143,6 +1154,38 @@ static __global__ void __launch_bounds__(256) k_hxc_fft(const SubDev* subs, cons
 }
 
 __host__ __device__ inline bool hxc_fft_ok(int n) { return n == 2 || n == 4 || n == 8 || n == 16; }
+
+// One FFT line per thread along one axis, over the grids of every sub-simulation
+// of the list at once (work holds n_subs grids of npts complex values), in
+// place: the same line transform as k_hxc_fft, spread over all SMs.
+template <int N>
+static __global__ void __launch_bounds__(64) k_fft_lines(double2* __restrict__ work, long long total_lines, int npts,
+                                                         int stride, const double2* __restrict__ tw, int sign) {
+  const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= total_lines) return;
+  const int per = npts / N;
+  const long long s = l / per;
+  const int ll = (int)(l - s * per), in = ll % stride, outer = ll / stride;
+  double2* w = work + s * npts + (long long)outer * stride * N + in;
+  double2 x[N];
+#pragma unroll
+  for (int n = 0; n < N; ++n) x[n] = w[(long long)n * stride];
+  hxc_fft_line<N>(x, tw, sign);
+#pragma unroll
+  for (int n = 0; n < N; ++n) w[(long long)n * stride] = x[n];
+}
+
+static void launch_fft_lines(double2* work, int n_subs, int npts, int n, int stride, const double2* tw, int sign,
+                             cudaStream_t st) {
+  const long long lines = (long long)n_subs * (npts / n);
+  const unsigned blocks = (unsigned)((lines + 63) / 64);
+  switch (n) {
+    case 2: k_fft_lines<2><<<blocks, 64, 0, st>>>(work, lines, npts, stride, tw, sign); break;
+    case 4: k_fft_lines<4><<<blocks, 64, 0, st>>>(work, lines, npts, stride, tw, sign); break;
+    case 8: k_fft_lines<8><<<blocks, 64, 0, st>>>(work, lines, npts, stride, tw, sign); break;
+    default: k_fft_lines<16><<<blocks, 64, 0, st>>>(work, lines, npts, stride, tw, sign); break;
+  }
+}
 
 // v_eff of every sub-simulation of the list: copied to veff_save (swap = 0) or
 // exchanged with it (swap = 1).
@@ -1268,7 +1311,22 @@ int launch_hxc_t(const SubDev* subs_dev, const int* sub_ids_dev, int n_subs, con
   if (n_subs == 0) return 0;
   cudaStream_t st = (cudaStream_t)stream;
   const long long total = (long long)n_subs * c.npts;
-  if (hxc_fft_ok(c.n1) && hxc_fft_ok(c.n2) && hxc_fft_ok(c.n3) && c.npts <= HXC_FFT_MAXPTS) {
+  const bool pow2 = hxc_fft_ok(c.n1) && hxc_fft_ok(c.n2) && hxc_fft_ok(c.n3);
+  if (pow2 && n_subs >= HXC_LINES_MIN_SUBS) {
+    // many sub-simulations: per-axis line kernels over all of them (the FP64
+    // work of one grid per CTA would occupy only n_subs SMs)
+    const int thr = 256;
+    const unsigned blocks = (unsigned)((total + thr - 1) / thr);
+    const int nn[3] = {c.n1, c.n2, c.n3};
+    const int strides[3] = {1, c.n1, c.n1 * c.n2};
+    k_hxc_load<<<blocks, thr, 0, st>>>(subs_dev, sub_ids_dev, n_subs, c.npts, wa);
+    for (int ax = 0; ax < 3; ++ax) launch_fft_lines(wa, n_subs, c.npts, nn[ax], strides[ax], tw[ax], -1, st);
+    k_poisson<<<blocks, thr, 0, st>>>(wa, total, c);
+    for (int ax = 2; ax >= 0; --ax) launch_fft_lines(wa, n_subs, c.npts, nn[ax], strides[ax], tw[ax], +1, st);
+    k_hxc_final<T><<<blocks, thr, 0, st>>>(subs_dev, sub_ids_dev, n_subs, c, wa);
+    return 9;
+  }
+  if (pow2 && c.npts <= HXC_FFT_MAXPTS) {
     const size_t sm = (size_t)c.npts * sizeof(double2);
     if (sm > 48 * 1024) cudaFuncSetAttribute(k_hxc_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_hxc_fft<<<n_subs, 256, sm, st>>>(subs_dev, sub_ids_dev, c, tw[0], tw[1], tw[2], wa);
