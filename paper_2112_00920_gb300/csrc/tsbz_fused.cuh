@@ -1152,6 +1152,74 @@ __global__ void __launch_bounds__(FS_NP, 2) k_bra_fused(LaunchSet L, const float
 }
 
 // ----------------------------------------------------------------------------
+// Projections of the current, Pa[u][b][j][alpha] = <beta~_j|u>, <d_alpha beta~_j|u>
+// on the q_obs tables, one CTA per (unit, band): the second-order pass of the
+// whole-step kernel's stage 4 (monomials of degree <= 2), for the evaluations
+// of J outside a step (J(0-), J(0+), a restored state).
+// ----------------------------------------------------------------------------
+template <int NZU, bool UM>
+__global__ void __launch_bounds__(FS_NP, 2) k_pa_fused(LaunchSet L, const float2* __restrict__ src,
+                                                       float2* __restrict__ Pa) {
+  static_assert(!UM || NZU == 4, "the tcgen05 contractions cover grouped cells");
+  extern __shared__ __align__(128) unsigned char fs_raw[];
+  FsSmem& sm = *reinterpret_cast<FsSmem*>(fs_raw);
+  const CellDev& c = L.cell;
+  const int b = blockIdx.x % c.n_bands;
+  const int u = L.unit_ids[blockIdx.x / c.n_bands];
+  if (!unit_active(L, u)) return;
+  const UnitDev U = L.units[u];
+  const int tid = threadIdx.x;
+  FuState fu{};
+  if constexpr (UM) fu = fu_open(sm);
+  const float2* ph = (const float2*)L.ph_obs + (long long)u * L.ph_stride;
+  const float2* sb = src + U.psi_off + (long long)b * FS_NPTS + tid;
+  fz_load<NZU>(sm, c);
+#pragma unroll
+  for (int z = 0; z < FS_N; ++z) sm.yb[z * FS_PU + tid] = sb[z * FS_NP];
+  fs_load_z(sm.zt, c, ph);
+  fs_load_cols(sm, c, ph);
+  __syncthreads();
+  uint32_t ah[2][4][4], al[2][4][4];
+  if constexpr (UM) {
+    fu_stage_u(sm.yb, fu);
+  } else {
+    fs_load_u(sm.yb, ah, al);
+    __syncthreads();   // yb becomes the z-sum scratch
+  }
+  float2* Pab = Pa + U.pa_off + 4LL * b * c.n_proj;
+  constexpr int NPASS = NZU == SEP_NA ? 2 : 1, NAP = SEP_NA / NPASS;
+#pragma unroll 1
+  for (int half = 0; half < NPASS; ++half) {
+    if constexpr (UM) {
+      if (!fu_project_pass<2, 3 * NZU / NPASS, NAP, NZU>(sm, c, half * (3 * NZU / NPASS), half * NAP, fu,
+                                                         reinterpret_cast<unsigned char*>(sm.xb), sm.yb)) {
+        fu_bail(fu, L.subs[U.sub].status);
+        return;
+      }
+    } else {
+      fs_project_pass<2, 3 * NZU / NPASS, NAP, NZU>(sm, c, half * (3 * NZU / NPASS), half * NAP, ah, al,
+                                                    reinterpret_cast<uint2*>(sm.xb), sm.yb);
+    }
+    // rows (a, c_x, c_y, c_z) of projector type t: monomials w_t and w_t + e_alpha
+    const int o = tid;
+    if (o < 4 * 4 * NAP) {
+      const int al_ = o >> 4, t = (o >> 2) & 3, sa = o & 3;
+      const int a = half * NAP + al_;
+      const int j = 4 * a + t;
+      if (j < c.n_proj) {
+        int e[3] = {t == 1 ? 1 : 0, t == 2 ? 1 : 0, t == 3 ? 1 : 0};
+        if (sa > 0) e[sa - 1] += 1;
+        const float2 M = sm.mres[al_ * 10 + fs_mono(e[0], e[1], e[2])];
+        const double sc = c.dv * (double)c.pnormf[j];
+        Pab[4 * j + sa] = make_float2((float)(sc * M.x), (float)(sc * M.y));
+      }
+    }
+    __syncthreads();
+  }
+  if constexpr (UM) fu_close(fu);
+}
+
+// ----------------------------------------------------------------------------
 // Observation pass on 16^3 grids: one CTA per unit, bands in turn through a
 // ring of FO_SLOTS band buffers filled by bulk copies.  A slot's "full"
 // mbarrier completes when its band has landed, its "empty" mbarrier when all

@@ -79,6 +79,25 @@ void launch_bra_sep(const LaunchSet& L, const void* src, void* out, int with_d, 
                                                                                         (float2*)out);
     return;
   }
+  if (stage_kind(L) <= 1 && with_d && use_obs && fs_cube16(c)) {
+    // the current's projections by the second-order pass of the fused stage 4
+    static bool attr_pa = false;
+    if (!attr_pa) {
+      fs_attr(k_pa_fused<4, true>, sizeof(FsSmem));
+      fs_attr(k_pa_fused<4, false>, sizeof(FsSmem));
+      fs_attr(k_pa_fused<SEP_NA, false>, sizeof(FsSmem));
+      attr_pa = true;
+    }
+    if (fs_grouped(c) && fs_umma(L))
+      k_pa_fused<4, true><<<grid, FS_NP, sizeof(FsSmem), (cudaStream_t)stream>>>(L, (const float2*)src, (float2*)out);
+    else if (fs_grouped(c))
+      k_pa_fused<4, false><<<grid, FS_NP, sizeof(FsSmem), (cudaStream_t)stream>>>(L, (const float2*)src,
+                                                                                (float2*)out);
+    else
+      k_pa_fused<SEP_NA, false><<<grid, FS_NP, sizeof(FsSmem), (cudaStream_t)stream>>>(L, (const float2*)src,
+                                                                                       (float2*)out);
+    return;
+  }
   const unsigned thr = sep_threads(L.cell);
   cudaStream_t st = (cudaStream_t)stream;
   const float2* s = (const float2*)src;
