@@ -238,10 +238,10 @@ int layout(tsbz_ctx* ctx) {
     hc.hxc_subs.clear();
     ph_stride = std::max<long long>(ph_stride, (long long)hc.dev.n_atoms * 3 * hc.dev.nmax);
   }
-  // finalize tiles: 16 per sub-simulation; with units that take a whole CTA
+  // finalize tiles: TSBZ_FIN_TILES per sub-simulation; with units that take a whole CTA
   // each, as many as the largest such sub-simulation has k-points (at most
   // TSBZ_FIN_MAX_TILES)
-  int fin_units = 16;
+  int fin_units = TSBZ_FIN_TILES;
   for (size_t s = 0; s < ctx->subs.size(); ++s)
     if (fin_wide(ctx->cells[ctx->subs[s].cell].dev)) fin_units = std::max(fin_units, ctx->subs[s].n_k);
   ctx->fin_tiles = std::min(TSBZ_FIN_MAX_TILES, fin_units);

@@ -19,6 +19,9 @@
 #define TSBZ_PT 128        // points per CTA in the point-parallel kernels
 #define TSBZ_BG 32         // max bands per band group in the point-parallel kernels
 #define TSBZ_FIN_MAX_TILES 128   // most CTAs per sub-simulation of the finalize
+#ifndef TSBZ_FIN_TILES
+#define TSBZ_FIN_TILES 16        // CTAs per sub-simulation of the finalize (small units)
+#endif
 
 struct CellDev {
   int n1, n2, n3, npts, nmax;
