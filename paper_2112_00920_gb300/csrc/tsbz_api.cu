@@ -439,7 +439,9 @@ template <typename T> int run_observe(tsbz_ctx* ctx, int fin_mode) {
     ev_start(ctx, FAM_OBS);
     if (!(sep && launch_observe_fused(L, ctx->psi, ctx->rho_part, ctx->jk_part, ctx->nrm_part, ctx->stream)) &&
         !(ctx->precision != TSBZ_FP64 &&
-          launch_observe_zf(L, ctx->psi, ctx->rho_part, ctx->jk_part, ctx->nrm_part, ctx->stream)))
+          launch_observe_zf(L, ctx->psi, ctx->rho_part, ctx->jk_part, ctx->nrm_part, ctx->stream)) &&
+        !(ctx->precision == TSBZ_FP32 &&
+          launch_observe_slab(L, ctx->psi, ctx->rho_part, ctx->jk_part, ctx->nrm_part, ctx->stream)))
       launch_observe<T>(L, ctx->psi, ctx->rho_part, ctx->jk_part, ctx->nrm_part, ctx->stream);
     ev_stop(ctx);
     ++ctx->launches;

@@ -196,6 +196,10 @@ void launch_scf_rotate(const LaunchSet& L, const void* Y, const void* C, void* Y
 bool slab_supported(const CellDev& c);
 bool launch_stage_slab(const LaunchSet& L, const void* tin, void* tout, void* psi, const void* P, int m,
                        void* stream);
+// Observation (density, local current, band norms) of float orbitals on the same
+// cells, every variant; false when the cell does not qualify.
+bool launch_observe_slab(const LaunchSet& L, const void* psi, double* rho_part, double* jk_part, double* nrm_part,
+                         void* stream);
 // Projections of float orbitals on the same cells (variant 0): P (with_d = 0) or
 // the current's Pa (with_d = 1), on the q_half (use_obs = 0) or q_obs tables.
 bool launch_bra_slab(const LaunchSet& L, const void* src, void* out, int with_d, int use_obs, void* stream);

@@ -480,6 +480,209 @@ __global__ void __launch_bounds__(SL_T) k_bra_slab(LaunchSet L, const float2* __
   cl.sync();   // the other CTAs keep their shared memory until it has been read
 }
 
+// ----------------------------------------------------------------------------
+// Observation on the slab layout: one CTA per (unit, band group of TSBZ_BG
+// bands, slab of 8 rows, block of SO_ZP planes), one thread per column of the
+// slab.  The bands of the group stream through a ring of plane slabs (the
+// slab's rows and the next 4 rows, periodic in y; the block's planes and the
+// next 4, periodic in z) filled by bulk copies in one continuous sequence
+// q = band * (SO_ZP + 4) + plane.  Per
+// point it adds occ |u|^2 to the group's density (two-sum in float), and for
+// the current's local part the forward correlations
+//   sum_r Im(conj(u(r)) u(r + m e_ax)),  m = 1 .. 4
+// (z neighbours from a register queue, x and y from the staged plane); per band
+// the norm.  The density sums over the group's bands in float per point, as the
+// point-parallel form does; the current sums over bands with two-sums.
+// Outputs: rho_part of the group on the block's points, jk_part and nrm_part of
+// point tile slab * (n3 / SO_ZP) + block (zeros in the tiles beyond them).
+// ----------------------------------------------------------------------------
+#define SO_RY (SL_SY + SL_ND)          // staged rows: the slab's and 4 forward
+#define SO_PL (SO_RY * SL_N1)
+#define SO_R 8                         // ring slots
+#define SO_ZP 8                        // planes per CTA
+
+struct SoSmem {
+  float2 ring[SO_R][SO_PL];
+  float nrm[SL_T / 32][TSBZ_BG];
+  double redj[SL_T / 32][3];
+  unsigned long long bar[SO_R];
+};
+
+// Thread 0: stage sequence element q (band q / (SO_ZP + 4), plane z0 + q % (SO_ZP + 4)).
+__device__ __forceinline__ void so_issue(SoSmem& sm, const float2* gbase, long long q, int slab, int z0, int n2,
+                                         int n3, int npts) {
+  constexpr int np = SO_ZP + SL_ND;
+  const int bl = (int)(q / np), p = z0 + (int)(q - (long long)bl * np);
+  const int s = (int)(q & (SO_R - 1));
+  const uint32_t bar = bk_smem(&sm.bar[s]);
+  constexpr uint32_t row = SL_N1 * (uint32_t)sizeof(float2);
+  bk_mbar_expect_tx(bar, SO_RY * row);
+  const float2* src = gbase + (long long)bl * npts + (long long)(p % n3) * SL_N1 * n2;
+  float2* dst = sm.ring[s];
+  const int r0 = slab * SL_SY;
+  if (r0 + SO_RY <= n2) {
+    bk_copy_g2s(bk_smem(dst), src + r0 * SL_N1, SO_RY * row, bar);
+  } else {
+    const int k = n2 - r0;   // rows r0 .. n2 - 1, then 0 .. SO_RY - k - 1
+    bk_copy_g2s(bk_smem(dst), src + r0 * SL_N1, k * row, bar);
+    bk_copy_g2s(bk_smem(dst + k * SL_N1), src, (SO_RY - k) * row, bar);
+  }
+}
+
+__device__ __forceinline__ uint32_t so_parity(long long q) { return (uint32_t)((q / SO_R) & 1); }
+
+__global__ void __launch_bounds__(SL_T, 2) k_observe_slab(LaunchSet L, const float2* __restrict__ psi,
+                                                          double* __restrict__ rho_part, double* __restrict__ jk_part,
+                                                          double* __restrict__ nrm_part) {
+  constexpr int ND = SL_ND, NZ = SO_ZP, np = SO_ZP + SL_ND;
+  extern __shared__ __align__(128) unsigned char soraw[];
+  SoSmem& sm = *reinterpret_cast<SoSmem*>(soraw);
+  const CellDev& c = L.cell;
+  const int n2 = c.n2, n3 = c.n3, n12 = SL_N1 * n2, npts = c.npts;
+  const int n_slabs = n2 / SL_SY, n_zb = n3 / SO_ZP, n_pt = n_slabs * n_zb;   // point tiles of the kernel
+  const int grp = blockIdx.x / n_pt, pt = blockIdx.x - grp * n_pt;
+  const int slab = pt / n_zb, zb = pt - slab * n_zb, z0 = zb * SO_ZP;
+  const int u = L.unit_ids[blockIdx.y];
+  if (!unit_active(L, u)) return;
+  const UnitDev U = L.units[u];
+  const SubDev S = L.subs[U.sub];
+  const int tid = threadIdx.x, ix = tid & (SL_N1 - 1), ry = tid / SL_N1, lane = tid & 31, warp = tid >> 5;
+  const int b0 = grp * TSBZ_BG, nbg = min(TSBZ_BG, c.n_bands - b0);
+  const float2* gbase = psi + U.psi_off + (long long)b0 * npts;
+  const long long qend = (long long)nbg * np;   // sequence elements of the group
+  if (tid == 0) {
+    for (int k = 0; k < SO_R; ++k) bk_mbar_init(bk_smem(&sm.bar[k]), 1);
+    for (long long q = 0; q < SO_R && q < qend; ++q) so_issue(sm, gbase, q, slab, z0, n2, n3, npts);
+  }
+  __syncthreads();
+  long long issued = qend < SO_R ? qend : SO_R;
+  float rho[NZ];   // the group's density per plane of this column (float, as the point-parallel form)
+#pragma unroll
+  for (int z = 0; z < NZ; ++z) rho[z] = 0.f;
+  float js[3] = {0.f, 0.f, 0.f}, je[3] = {0.f, 0.f, 0.f};
+  const int me = ry * SL_N1 + ix;
+  int xo[ND];
+#pragma unroll
+  for (int mm = 1; mm <= ND; ++mm) xo[mm - 1] = ry * SL_N1 + ((ix + mm) & (SL_N1 - 1));
+  bool ok = true;
+  // release the slot of sequence element q (every thread is done with it) and
+  // stage element q + SO_R there
+  auto release = [&](long long q) -> bool {
+    const bool fail = __syncthreads_or(!ok);
+    if (fail) return false;
+    if (q + SO_R < qend) {
+      if (tid == 0) so_issue(sm, gbase, q + SO_R, slab, z0, n2, n3, npts);
+      issued = q + SO_R + 1;
+    }
+    return true;
+  };
+  bool alive = true;
+  for (int bl = 0; bl < nbg && alive; ++bl) {
+    const long long q0 = (long long)bl * np;
+    float2 qv[2 * ND + 1];
+#pragma unroll
+    for (int k = 0; k < ND; ++k) {
+      ok = ok && bk_mbar_wait(bk_smem(&sm.bar[(q0 + k) & (SO_R - 1)]), so_parity(q0 + k), BK_WAIT_POLLS);
+      qv[k] = sm.ring[(q0 + k) & (SO_R - 1)][me];
+    }
+    float nbs = 0.f;
+    float cx[ND], cy[ND], cz[ND];
+#pragma unroll
+    for (int mm = 0; mm < ND; ++mm) cx[mm] = cy[mm] = cz[mm] = 0.f;
+    // the plane loop is unrolled, so that rho[z] is a register
+#pragma unroll
+    for (int z = 0; z < NZ; ++z) {
+      {
+        const long long qz = q0 + z, qn = qz + ND;
+        ok = ok && bk_mbar_wait(bk_smem(&sm.bar[qn & (SO_R - 1)]), so_parity(qn), BK_WAIT_POLLS);
+        qv[ND] = sm.ring[qn & (SO_R - 1)][me];
+        const float2* pl = sm.ring[qz & (SO_R - 1)];
+        const float2 ce = qv[0];
+#pragma unroll
+        for (int mm = 1; mm <= ND; ++mm) {
+          const float2 xu = pl[xo[mm - 1]], yu = pl[me + mm * SL_N1], zu = qv[mm];
+          // Im(conj(u) v) = u_r v_i - u_i v_r
+          cx[mm - 1] = __fmaf_rn(ce.x, xu.y, __fmaf_rn(-ce.y, xu.x, cx[mm - 1]));
+          cy[mm - 1] = __fmaf_rn(ce.x, yu.y, __fmaf_rn(-ce.y, yu.x, cy[mm - 1]));
+          cz[mm - 1] = __fmaf_rn(ce.x, zu.y, __fmaf_rn(-ce.y, zu.x, cz[mm - 1]));
+        }
+        const float n2v = ce.x * ce.x + ce.y * ce.y;
+        rho[z] += n2v;
+        nbs += n2v;
+#pragma unroll
+        for (int k = 0; k < 2 * ND; ++k) qv[k] = qv[k + 1];
+        if (!release(qz)) alive = false;
+      }
+      if (!alive) break;
+    }
+    if (!alive) break;
+    // the 4 planes after the block are done too
+    for (int k = 0; k < ND && alive; ++k) alive = release(q0 + NZ + k);
+    if (!alive) break;
+    float bx = 0.f, by = 0.f, bz = 0.f;
+#pragma unroll
+    for (int mm = 1; mm <= ND; ++mm) {
+      bx = __fmaf_rn(2.f * c.gradwf[0][mm], cx[mm - 1], bx);
+      by = __fmaf_rn(2.f * c.gradwf[1][mm], cy[mm - 1], by);
+      bz = __fmaf_rn(2.f * c.gradwf[2][mm], cz[mm - 1], bz);
+    }
+    const float bv[3] = {bx, by, bz};
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+      const float t = js[ax] + bv[ax], bb = t - js[ax];
+      je[ax] += (js[ax] - (t - bb)) + (bv[ax] - bb);
+      js[ax] = t;
+    }
+    for (int off = 16; off > 0; off >>= 1) nbs += __shfl_xor_sync(0xffffffffu, nbs, off);
+    if (lane == 0) sm.nrm[warp][bl] = nbs;
+  }
+  if (!alive || !ok) {
+    if (tid == 0) {
+      atomicOr(S.status, BK_STATUS_TIMEOUT);
+      // let every issued copy land before the CTA's shared memory is released
+      for (long long q = issued > SO_R ? issued - SO_R : 0; q < issued; ++q)
+        bk_mbar_wait(bk_smem(&sm.bar[q & (SO_R - 1)]), so_parity(q), BK_WAIT_POLLS);
+    }
+    return;
+  }
+  // density of the group on the block's points
+  const long long pbase = (long long)slab * SL_SY * SL_N1 + me;
+#pragma unroll
+  for (int z = 0; z < NZ; ++z)
+    rho_part[U.rho_off + (long long)grp * npts + (long long)(z0 + z) * n12 + pbase] = c.occ * (double)rho[z];
+  // the group's current over the slab's points, in warp order
+  double jd[3];
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    jd[ax] = (double)js[ax] + (double)je[ax];
+    for (int off = 16; off > 0; off >>= 1) jd[ax] += __shfl_xor_sync(0xffffffffu, jd[ax], off);
+  }
+  if (lane == 0)
+    for (int ax = 0; ax < 3; ++ax) sm.redj[warp][ax] = jd[ax];
+  __syncthreads();
+  if (tid < 3) {
+    double sum = 0.0;
+    for (int w = 0; w < SL_T / 32; ++w) sum += sm.redj[w][tid];
+    jk_part[U.jk_off + ((long long)pt * c.n_bgroups + grp) * 3 + tid] = sum;
+  }
+  for (int bl = tid; bl < nbg; bl += SL_T) {
+    double sum = 0.0;
+    for (int w = 0; w < SL_T / 32; ++w) sum += (double)sm.nrm[w][bl];
+    nrm_part[U.nrm_off + (long long)pt * c.n_bands + b0 + bl] = sum;
+  }
+  // tiles beyond the kernel's hold nothing of this group
+  if (pt == 0) {
+    for (int i = tid; i < (c.n_tiles - n_pt) * 3; i += SL_T) {
+      const int t = n_pt + i / 3, ax = i - (i / 3) * 3;
+      jk_part[U.jk_off + ((long long)t * c.n_bgroups + grp) * 3 + ax] = 0.0;
+    }
+    for (int i = tid; i < (c.n_tiles - n_pt) * nbg; i += SL_T) {
+      const int t = n_pt + i / nbg, bl = i - (i / nbg) * nbg;
+      nrm_part[U.nrm_off + (long long)t * c.n_bands + b0 + bl] = 0.0;
+    }
+  }
+}
+
 }  // namespace
 
 bool slab_supported(const CellDev& c) {
@@ -544,5 +747,18 @@ bool launch_bra_slab(const LaunchSet& L, const void* src, void* out, int with_d,
     else if (g <= 4) go(k_bra_slab<4, 2>, sm2);
     else go(k_bra_slab<8, 2>, sm2);
   }
+  return true;
+}
+
+bool launch_observe_slab(const LaunchSet& L, const void* psi, double* rho_part, double* jk_part, double* nrm_part,
+                         void* stream) {
+  const CellDev& c = L.cell;
+  const int n_pt = (c.n2 / SL_SY) * (c.n3 / SO_ZP);
+  if (!slab_supported(c) || c.n3 % SO_ZP != 0 || c.n_tiles < n_pt) return false;
+  if (L.n_units == 0) return true;
+  const size_t smem = sizeof(SoSmem);
+  cudaFuncSetAttribute(k_observe_slab, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const dim3 grid(c.n_bgroups * n_pt, L.n_units);
+  k_observe_slab<<<grid, SL_T, smem, (cudaStream_t)stream>>>(L, (const float2*)psi, rho_part, jk_part, nrm_part);
   return true;
 }
