@@ -531,7 +531,7 @@ __device__ __forceinline__ void so_issue(SoSmem& sm, const float2* gbase, long l
 
 __device__ __forceinline__ uint32_t so_parity(long long q) { return (uint32_t)((q / SO_R) & 1); }
 
-__global__ void __launch_bounds__(SL_T, 2) k_observe_slab(LaunchSet L, const float2* __restrict__ psi,
+__global__ void __launch_bounds__(SL_T, 3) k_observe_slab(LaunchSet L, const float2* __restrict__ psi,
                                                           double* __restrict__ rho_part, double* __restrict__ jk_part,
                                                           double* __restrict__ nrm_part) {
   constexpr int ND = SL_ND, NZ = SO_ZP, np = SO_ZP + SL_ND;
