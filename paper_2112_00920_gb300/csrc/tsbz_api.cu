@@ -720,13 +720,24 @@ int copy_state_in(tsbz_ctx* ctx, int s, const double* psi, size_t n_elems, int o
   if ((long long)n_elems != need)
     return set_err(ctx, TSBZ_EINVAL, "psi has " + std::to_string(n_elems) + " complex values, expected " +
                                          std::to_string(need));
-  CK(cudaMemcpyAsync(ctx->staging, psi, sizeof(double2) * need,
-                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+  // page-locked host memory mapped into the device's address space is read by
+  // the conversion kernel over the host link directly; anything else goes
+  // through the staging buffer by one copy
+  const double2* src = (const double2*)ctx->staging;
+  cudaPointerAttributes at{};
+  if (!on_device && cudaPointerGetAttributes(&at, psi) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+      at.devicePointer) {
+    src = (const double2*)at.devicePointer;
+  } else {
+    cudaGetLastError();   // a query on memory CUDA does not know may leave an error behind
+    CK(cudaMemcpyAsync(ctx->staging, psi, sizeof(double2) * need,
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+  }
   char* dst = (char*)ctx->psi + ctx->unit_psi_off[hs.unit0] * ctx->elem_size();
   if (ctx->precision == TSBZ_FP64)
-    launch_convert_in_t<double>(ctx->staging, dst, need, ctx->stream);
+    launch_convert_in_t<double>(src, dst, need, ctx->stream);
   else
-    launch_convert_in_t<float>(ctx->staging, dst, need, ctx->stream);
+    launch_convert_in_t<float>(src, dst, need, ctx->stream);
   ++ctx->launches;
   CK(cudaGetLastError());
   return TSBZ_OK;
@@ -1148,7 +1159,8 @@ int tsbz_load_ground_state(tsbz_ctx* ctx, int s, const double* psi, size_t n_ele
   hs.loaded = true;
   hs.need_init = true;
   hs.need_j0plus = true;
-  return sync_and_check(ctx);
+  // a caller's device buffer may be freed and reused as soon as this returns
+  return psi_on_device ? sync_and_check(ctx) : TSBZ_OK;
 }
 
 int tsbz_set_kick(tsbz_ctx* ctx, int s, double k0, const double dir[3]) {
