@@ -979,9 +979,9 @@ int tsbz_init_cell(tsbz_ctx* ctx, const tsbz_cell_desc* d, int* cell_id) {
   if (c.use_proj)
     for (int j = 0; j < c.n_proj; ++j) wkb[j] = hc.pnorm[j] * ekb[j];
   auto to_f = [](const std::vector<double>& v) { return std::vector<float>(v.begin(), v.end()); };
-  const std::vector<float> g1f = to_f(g1), d1f = to_f(d1), pnf = to_f(hc.pnorm), wkf = to_f(wkb);
+  const std::vector<float> g1f = to_f(g1), d1f = to_f(d1), pnf = to_f(hc.pnorm), wkf = to_f(wkb), ekf = to_f(ekb);
   double *vl, *gg, *dd, *pn, *ek, *wk;
-  float *ggf, *ddf, *pnff, *wkff;
+  float *ggf, *ddf, *pnff, *wkff, *ekff;
   int rc;
   if ((rc = dalloc_t(ctx, hc.vloc.size(), &vl))) return rc;
   if ((rc = dalloc_t(ctx, g1.size(), &gg))) return rc;
@@ -993,6 +993,7 @@ int tsbz_init_cell(tsbz_ctx* ctx, const tsbz_cell_desc* d, int* cell_id) {
   if ((rc = dalloc_t(ctx, d1f.size(), &ddf))) return rc;
   if ((rc = dalloc_t(ctx, pnf.size(), &pnff))) return rc;
   if ((rc = dalloc_t(ctx, wkf.size(), &wkff))) return rc;
+  if ((rc = dalloc_t(ctx, ekf.size(), &ekff))) return rc;
   CK(cudaMemcpy(vl, hc.vloc.data(), sizeof(double) * hc.vloc.size(), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(gg, g1.data(), sizeof(double) * g1.size(), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(dd, d1.data(), sizeof(double) * d1.size(), cudaMemcpyHostToDevice));
@@ -1003,6 +1004,7 @@ int tsbz_init_cell(tsbz_ctx* ctx, const tsbz_cell_desc* d, int* cell_id) {
   CK(cudaMemcpy(ddf, d1f.data(), sizeof(float) * d1f.size(), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(pnff, pnf.data(), sizeof(float) * pnf.size(), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(wkff, wkf.data(), sizeof(float) * wkf.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ekff, ekf.data(), sizeof(float) * ekf.size(), cudaMemcpyHostToDevice));
   c.vloc = vl;
   c.g1 = gg;
   c.d1 = dd;
@@ -1013,6 +1015,7 @@ int tsbz_init_cell(tsbz_ctx* ctx, const tsbz_cell_desc* d, int* cell_id) {
   c.d1f = ddf;
   c.pnormf = pnff;
   c.wkbf = wkff;
+  c.ekbf = ekff;
   // projector boxes from the double Gaussian tables: the smallest periodic index
   // range of each atom and axis that holds every nonzero factor
   c.pbox = nullptr;

@@ -49,6 +49,7 @@ struct CellDev {
   const float* d1f;
   const float* pnormf;
   const float* wkbf;
+  const float* ekbf;   // E_j
   // atoms whose z factor tables are identical (same z position, hence the same
   // Gaussian, displacement and phase rows for every q) form one z group; the
   // z contractions of the 16^3 fused stage run once per group (cells of at

@@ -881,16 +881,36 @@ __global__ void __launch_bounds__(256) k_finalize(const SubDev* __restrict__ sub
       for (int ax = 0; ax < 3; ++ax) jk[ax] += jk_part[U.jk_off + 3LL * i + ax];
     if (c.use_proj) {
       const int np = c.n_proj;
+      if constexpr (sizeof(T) == sizeof(float)) {
+        // single-precision projections: each thread forms and sums its own terms
+        // in FP32 (the terms carry the projections' own ~1e-6 relative error) and
+        // converts the sum once; the FP64 pipe of this GPU is ~1/64 of the FP32 one
+        float jf[3] = {0.f, 0.f, 0.f};
 #pragma unroll 4
-      for (int i = e_first; i < c.n_bands * np; i += e_step) {
-        const int j = i % np;
-        const V* pr = Pa + U.pa_off + 4LL * i;
-        const double ar = pr[0].x, ai = pr[0].y;
-        const double e2 = 2.0 * c.ekb[j];
-        for (int ax = 0; ax < 3; ++ax) {
-          // Im(conj(c) a) = c_r a_i - c_i a_r
-          const double cr = pr[1 + ax].x, ci = pr[1 + ax].y;
-          jn[ax] += e2 * (cr * ai - ci * ar);
+        for (int i = e_first; i < c.n_bands * np; i += e_step) {
+          const int j = i % np;
+          const V* pr = Pa + U.pa_off + 4LL * i;
+          const float ar = pr[0].x, ai = pr[0].y;
+          const float e2 = 2.0f * c.ekbf[j];
+          for (int ax = 0; ax < 3; ++ax) {
+            // Im(conj(c) a) = c_r a_i - c_i a_r
+            const float cr = pr[1 + ax].x, ci = pr[1 + ax].y;
+            jf[ax] = __fmaf_rn(e2, __fmaf_rn(cr, ai, -ci * ar), jf[ax]);
+          }
+        }
+        for (int ax = 0; ax < 3; ++ax) jn[ax] = (double)jf[ax];
+      } else {
+#pragma unroll 4
+        for (int i = e_first; i < c.n_bands * np; i += e_step) {
+          const int j = i % np;
+          const V* pr = Pa + U.pa_off + 4LL * i;
+          const double ar = pr[0].x, ai = pr[0].y;
+          const double e2 = 2.0 * c.ekb[j];
+          for (int ax = 0; ax < 3; ++ax) {
+            // Im(conj(c) a) = c_r a_i - c_i a_r
+            const double cr = pr[1 + ax].x, ci = pr[1 + ax].y;
+            jn[ax] += e2 * (cr * ai - ci * ar);
+          }
         }
       }
     }
