@@ -332,8 +332,9 @@ FP32_LANES_PER_SM = 128
 # + dram__bytes_write.sum) on the reduced workload (8 of the 64 subgrids, 8192
 # orbitals), scaled by the orbital count to the full workload.  Valid only for
 # the source it was taken on: the SHA-1 of the kernel header is checked at run time.
-STEP_TRAFFIC = {"file": "tsbz_fused.cuh", "sha1": "f4d12e87e3e5674d6e47074d7c32c5a3bef46fdd",
-                "bytes_per_launch_full": 8 * 492.968448e6, "profile": "profiles/k_step_fused_tcgen05_twostep8.md"}
+STEP_TRAFFIC = {"file": "tsbz_fused.cuh", "sha1": "93d95614680d5daa93a0a54a1c9dbb337bade2aa",
+                "bytes_per_launch_full": 8 * (273.970432e6 + 218.047744e6),
+                "profile": "profiles/k_step_fused_tcgen05_twostep8.md"}
 # DRAM bytes of the per-stage stencil kernel k_stage_zb<false> from an ncu capture of the
 # reduced dense tensor-core workload (8 of the 64 subgrids): stages 1 and 2 moved 774.8 and
 # 1295.1 MB against 805.3 and 1342.2 MB of algorithmic bytes (0.964 of them); the full
