@@ -44,8 +44,13 @@ extern "C" {
 #define TSBZ_ENONFINITE (-5) /* a non-finite current was produced          */
 #define TSBZ_ESTATE (-6)     /* call out of order (e.g. no ground state)   */
 
-/* Arithmetic of the propagation (a2-a5).  Density, current, Hartree and
- * the time integration of the observables are FP64 in every mode. */
+/* Arithmetic of the propagation (a2-a5).  In every mode the density and
+ * current are summed over k-points, bands and tiles in FP64 (or in float
+ * two-sum pairs, which carry the same sums exactly to FP64 rounding), and
+ * the Hartree and XC potentials and the time integration of the observables
+ * are FP64; in the single-precision modes the per-point and per-projector
+ * terms themselves are formed from the float orbitals and projections in
+ * float. */
 #define TSBZ_FP64 0          /* everything in double                          */
 #define TSBZ_FP32 1          /* stencil, Taylor and projectors in float; on
                                 cells of at most 8 atoms with 16^3 grids the
