@@ -46,7 +46,7 @@ extern "C" {
 
 /* Arithmetic of the propagation (a2-a5).  In every mode the density and
  * current are summed over k-points, bands and tiles in FP64 (or in float
- * two-sum pairs, which carry the same sums exactly to FP64 rounding), and
+ * two-sum pairs, which carry those sums to about 48 bits), and
  * the Hartree and XC potentials and the time integration of the observables
  * are FP64; in the single-precision modes the per-point and per-projector
  * terms themselves are formed from the float orbitals and projections in
