@@ -136,11 +136,14 @@ int tsbz_add_subsim(tsbz_ctx* ctx, int cell_id, int n_k, const double* k_cart, d
  * (psi_on_device = 0) or the device (1).  v_hxc_frozen ([n3][n2][n1] host
  * doubles) is required in TSBZ_HXC_FROZEN mode and ignored otherwise.
  * Computes rho(0), v_Hxc[rho(0)] and J(0-) (A = 0), and resets the step count.
- * The copy is asynchronous: it is enqueued on the context stream and may
- * still be in flight when the call returns.  A page-locked host buffer must
- * stay unchanged until a later call that waits for the device (tsbz_propagate,
- * tsbz_get_current, tsbz_get_density, tsbz_get_state, ...) has returned;
- * pageable host memory is read before the call returns. */
+ * A host upload is asynchronous: it is enqueued on the context stream and may
+ * still be in flight when the call returns.  Page-locked host memory mapped
+ * into the device's address space is read by the conversion kernel directly
+ * (no staging copy); it, and a page-locked v_hxc_frozen, must stay unchanged
+ * until a later call that waits for the device (tsbz_propagate,
+ * tsbz_get_current, tsbz_get_density, tsbz_get_state, ...) has returned.
+ * Pageable host memory is read before the call returns.  A device source is
+ * copied and waited for before the call returns, so its owner may free it. */
 int tsbz_load_ground_state(tsbz_ctx* ctx, int subsim_id, const double* psi, size_t n_elems, int psi_on_device,
                            const double* v_hxc_frozen);
 
