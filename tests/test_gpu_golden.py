@@ -83,10 +83,10 @@ def test_fp64_matches_oracle_600_steps(golden):
     assert er <= 1e-12 and en <= 1e-12
 
 
-# errors measured over the 600 steps on GB300 (fp32: err_J 2.6e-7, err_eps 2.6e-7;
+# errors measured over the 600 steps on GB300 (fp32: err_J 2.7e-7, err_eps 3.4e-7;
 # fp32_tc: err_J 2.5e-6, err_eps 3.1e-6): the bars sit 10x above them, well inside
 # the 1e-4 target for eps(omega)
-SINGLE_BARS = {"fp32": dict(err_j=2.6e-6, err_eps=2.6e-6), "fp32_tc": dict(err_j=2.5e-5, err_eps=3.1e-5)}
+SINGLE_BARS = {"fp32": dict(err_j=2.7e-6, err_eps=3.4e-6), "fp32_tc": dict(err_j=2.5e-5, err_eps=3.1e-5)}
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp32_tc"])
