@@ -37,6 +37,7 @@ struct HostCell {
   std::vector<int> hxc_subs;   // non-frozen sub-simulations of this cell
   int* d_hxc_subs = nullptr;
   bool pa_by_stage = false;    // the last stage 4 also wrote P (next step) and Pa
+  bool p_by_obs = false;       // the last observation's Pa pass also wrote P (next step)
   int variant = 0;             // kernel variant (tsbz_autotune / tsbz_set_variant)
   bool tables_step = false;    // the phase tables hold a time step's q (not J(0-/0+) tables)
   double tune_ms[TSBZ_MAX_VARIANTS] = {0, 0, 0, 0};   // ms per step measured per variant
@@ -425,17 +426,26 @@ template <typename T> int run_observe(tsbz_ctx* ctx, int fin_mode) {
     LaunchSet L = make_set(ctx, hc);
     const bool sep = ctx->precision == TSBZ_FP32 && sep_supported(hc.dev);
     // the projections for the current (not needed for the density-only ETRS predictor)
+    bool wrote_p = false;
     if (fin_mode != TSBZ_FIN_RHO && !(fin_mode == TSBZ_FIN_STEP && hc.pa_by_stage)) {
       ev_start(ctx, FAM_BRA);
+      // after a Taylor step under a constant field the slab pass also leaves in P
+      // the projections the next step starts from (same q, same operations)
+      const bool p_next = fin_mode == TSBZ_FIN_STEP && ctx->propagator == TSBZ_PROP_TAYLOR4 &&
+                          cell_field_const(ctx, hc);
       if (ctx->precision == TSBZ_FP32_TC)
         launch_bra_tc(L, ctx->psi, ctx->Pa, 1, ctx->stream);
       else if (sep)
         launch_bra_sep(L, ctx->psi, ctx->Pa, 1, 1, ctx->stream);
-      else if (!(ctx->precision == TSBZ_FP32 && launch_bra_slab(L, ctx->psi, ctx->Pa, 1, 1, ctx->stream)))
+      else if (ctx->precision == TSBZ_FP32 &&
+               launch_bra_slab(L, ctx->psi, ctx->Pa, 1, 1, ctx->stream, p_next ? ctx->P : nullptr))
+        wrote_p = p_next && hc.dev.use_proj;
+      else
         launch_bra<T>(L, ctx->psi, ctx->Pa, 1, 1, ctx->stream);
       ev_stop(ctx);
       if (hc.dev.use_proj) ++ctx->launches;
     }
+    hc.p_by_obs = wrote_p;
     ev_start(ctx, FAM_OBS);
     if (!(sep && launch_observe_fused(L, ctx->psi, ctx->rho_part, ctx->jk_part, ctx->nrm_part, ctx->stream)) &&
         !(ctx->precision != TSBZ_FP64 &&
@@ -543,11 +553,14 @@ template <typename T> int run_stages(tsbz_ctx* ctx, bool fresh_p, int same_next_
     LaunchSet Lp = L;
     if (slab && L.variant > 0) Lp.variant = L.variant == 3 ? 0 : L.variant;
     for (int m = 1; m <= 4; ++m) {
-      ev_start(ctx, FAM_BRA);
-      if (!(slab && launch_bra_slab(L, srcs[m - 1], ctx->P, 0, 0, ctx->stream)))
-        launch_bra<T>(L, srcs[m - 1], ctx->P, 0, 0, ctx->stream);
-      ev_stop(ctx);
-      if (hc.dev.use_proj) ++ctx->launches;
+      // stage 1 starts from P when the last observation left the projections of psi there
+      if (!(m == 1 && !fresh_p && ctx->p_next_valid && hc.p_by_obs)) {
+        ev_start(ctx, FAM_BRA);
+        if (!(slab && launch_bra_slab(L, srcs[m - 1], ctx->P, 0, 0, ctx->stream)))
+          launch_bra<T>(L, srcs[m - 1], ctx->P, 0, 0, ctx->stream);
+        ev_stop(ctx);
+        if (hc.dev.use_proj) ++ctx->launches;
+      }
       ev_start(ctx, FAM_STAGE);
       if (!(slab && launch_stage_slab(L, srcs[m - 1], dsts[m - 1], ctx->psi, ctx->P, m, ctx->stream)))
         launch_stage<T>(Lp, srcs[m - 1], dsts[m - 1], ctx->psi, ctx->P, m, ctx->stream);
@@ -781,7 +794,7 @@ struct Snapshot {
   std::vector<std::vector<double>> rho, vhxc, norms;
   std::vector<std::vector<unsigned char>> veff;
   bool p_next_valid = false;
-  std::vector<bool> pa_by_stage;
+  std::vector<bool> pa_by_stage, p_by_obs;
 };
 
 int snapshot_take(tsbz_ctx* ctx, Snapshot& sn) {
@@ -814,7 +827,10 @@ int snapshot_take(tsbz_ctx* ctx, Snapshot& sn) {
     CK(cudaMemcpyAsync(sn.veff[s].data(), hs.veff, sn.veff[s].size(), cudaMemcpyDeviceToHost, ctx->stream));
   }
   sn.p_next_valid = ctx->p_next_valid;
-  for (auto& hc : ctx->cells) sn.pa_by_stage.push_back(hc.pa_by_stage);
+  for (auto& hc : ctx->cells) {
+    sn.pa_by_stage.push_back(hc.pa_by_stage);
+    sn.p_by_obs.push_back(hc.p_by_obs);
+  }
   return sync_and_check(ctx);
 }
 
@@ -835,7 +851,10 @@ int snapshot_restore(tsbz_ctx* ctx, Snapshot& sn) {
     CK(cudaMemcpyAsync(hs.veff, sn.veff[s].data(), sn.veff[s].size(), cudaMemcpyHostToDevice, ctx->stream));
   }
   ctx->p_next_valid = sn.p_next_valid;
-  for (size_t i = 0; i < ctx->cells.size(); ++i) ctx->cells[i].pa_by_stage = sn.pa_by_stage[i];
+  for (size_t i = 0; i < ctx->cells.size(); ++i) {
+    ctx->cells[i].pa_by_stage = sn.pa_by_stage[i];
+    ctx->cells[i].p_by_obs = sn.p_by_obs[i];
+  }
   const int rc = sync_and_check(ctx);
   dfree(ctx, sn.psi);
   dfree(ctx, sn.P);

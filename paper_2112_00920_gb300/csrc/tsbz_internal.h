@@ -202,8 +202,10 @@ bool launch_stage_slab(const LaunchSet& L, const void* tin, void* tout, void* ps
 bool launch_observe_slab(const LaunchSet& L, const void* psi, double* rho_part, double* jk_part, double* nrm_part,
                          void* stream);
 // Projections of float orbitals on the same cells (variant 0): P (with_d = 0) or
-// the current's Pa (with_d = 1), on the q_half (use_obs = 0) or q_obs tables.
-bool launch_bra_slab(const LaunchSet& L, const void* src, void* out, int with_d, int use_obs, void* stream);
+// the current's Pa (with_d = 1), on the q_half (use_obs = 0) or q_obs tables;
+// pnext, if given with with_d, also receives Pa's first-weight entries as P.
+bool launch_bra_slab(const LaunchSet& L, const void* src, void* out, int with_d, int use_obs, void* stream,
+                     void* pnext = nullptr);
 
 bool sep_supported(const CellDev& c);
 int sep_variants(const CellDev& c);   // kernel variants of the single-precision path on this cell

@@ -331,15 +331,25 @@ template <int KD> struct SbSmem {
   int grp[64];                   // z group of each atom
 };
 
+// a b in explicitly rounded operations (no contraction left to the compiler)
+__device__ __forceinline__ float2 sb_cmul(float2 a, float2 b) {
+  return make_float2(__fmaf_rn(a.x, b.x, -__fmul_rn(a.y, b.y)), __fmaf_rn(a.x, b.y, __fmul_rn(a.y, b.x)));
+}
+
 // x-sum index of (z power k, x power i)
 template <int KD> __device__ __forceinline__ int sb_xterm(int k, int i) {
   if (KD == 2) return k == 0 ? i : 2;
   return k == 0 ? i : (k == 1 ? 3 + i : 5);
 }
 
+// pnext (three z moments only, may be null): also write the first-weight
+// entries Pa_aj,0 = P_aj into P, the projections the next step starts from when
+// the field is constant (q at t_{n+1} and at t_{n+1} + dt/2 are then the same,
+// and these entries are formed by the same operations as the two-moment pass).
 template <int G, int KD>
 __global__ void __launch_bounds__(SL_T) k_bra_slab(LaunchSet L, const float2* __restrict__ src,
-                                                   float2* __restrict__ out, int use_obs) {
+                                                   float2* __restrict__ out, float2* __restrict__ pnext,
+                                                   int use_obs) {
   namespace cg = cooperative_groups;
   using Sm = SbSmem<KD>;
   constexpr int D = 8;   // planes of t loaded ahead
@@ -390,12 +400,14 @@ __global__ void __launch_bounds__(SL_T) k_bra_slab(LaunchSet L, const float2* __
       for (int g = 0; g < G; ++g) {
         const float4 f = sm.fb[g][z];
         if (f.x == 0.f && f.y == 0.f) continue;   // plane z is outside the group's box (uniform)
-        float2 ft = make_float2(f.x * t.x - f.y * t.y, f.x * t.y + f.y * t.x);
+        // every rounding spelled out: the two- and three-moment passes form the
+        // moments they share by the same operations, bit for bit
+        float2 ft = sb_cmul(make_float2(f.x, f.y), t);
 #pragma unroll
         for (int k = 0; k < KD; ++k) {
-          Sk[k][g].x += ft.x;
-          Sk[k][g].y += ft.y;
-          ft = make_float2(f.z * ft.x, f.z * ft.y);
+          Sk[k][g].x = __fadd_rn(Sk[k][g].x, ft.x);
+          Sk[k][g].y = __fadd_rn(Sk[k][g].y, ft.y);
+          ft = make_float2(__fmul_rn(f.z, ft.x), __fmul_rn(f.z, ft.y));
         }
       }
     }
@@ -425,13 +437,14 @@ __global__ void __launch_bounds__(SL_T) k_bra_slab(LaunchSet L, const float2* __
 #pragma unroll
         for (int k = 0; k < KD; ++k) {
           const float2 sv = sm.S[k * G + g][r * SL_N1 + x];
-          float2 w = make_float2(gx * (px.x * sv.x - px.y * sv.y), gx * (px.x * sv.y + px.y * sv.x));
+          const float2 pv = sb_cmul(px, sv);
+          float2 w = make_float2(__fmul_rn(gx, pv.x), __fmul_rn(gx, pv.y));
 #pragma unroll
           for (int ip = 0; ip + k < KD; ++ip) {
             const int e = sb_xterm<KD>(k, ip);
-            rr[e].x += w.x;
-            rr[e].y += w.y;
-            w = make_float2(dx * w.x, dx * w.y);
+            rr[e].x = __fadd_rn(rr[e].x, w.x);
+            rr[e].y = __fadd_rn(rr[e].y, w.y);
+            w = make_float2(__fmul_rn(dx, w.x), __fmul_rn(dx, w.y));
           }
         }
       }
@@ -454,10 +467,11 @@ __global__ void __launch_bounds__(SL_T) k_bra_slab(LaunchSet L, const float2* __
       if (gy == 0.f) continue;
       const float2 py = ph[oy];
       float wy = gy;
-      for (int q = 0; q < ej; ++q) wy *= c.d1f[oy];
+      for (int q = 0; q < ej; ++q) wy = __fmul_rn(wy, c.d1f[oy]);
       const float2 v = sm.R[a][r][e];
-      acc.x += wy * (py.x * v.x - py.y * v.y);
-      acc.y += wy * (py.x * v.y + py.y * v.x);
+      const float2 pv = sb_cmul(py, v);
+      acc.x = __fadd_rn(acc.x, __fmul_rn(wy, pv.x));
+      acc.y = __fadd_rn(acc.y, __fmul_rn(wy, pv.y));
     }
     const float sc = (float)c.dv * c.pnormf[4 * a + tt];
     sm.Pp[j] = make_float2(sc * acc.x, sc * acc.y);
@@ -475,6 +489,7 @@ __global__ void __launch_bounds__(SL_T) k_bra_slab(LaunchSet L, const float2* __
         v.y += w.y;
       }
       ob[j] = v;
+      if (KD == 3 && pnext != nullptr && (j & 3) == 0) pnext[U.p_off + (long long)b * c.n_proj + (j >> 2)] = v;
     }
   }
   cl.sync();   // the other CTAs keep their shared memory until it has been read
@@ -712,7 +727,8 @@ bool launch_stage_slab(const LaunchSet& L, const void* tin, void* tout, void* ps
   return true;
 }
 
-bool launch_bra_slab(const LaunchSet& L, const void* src, void* out, int with_d, int use_obs, void* stream) {
+bool launch_bra_slab(const LaunchSet& L, const void* src, void* out, int with_d, int use_obs, void* stream,
+                     void* pnext) {
   const CellDev& c = L.cell;
   if (L.variant != 0 || !slab_supported(c) || !c.use_proj) return false;
   if (L.n_units == 0) return true;
@@ -731,7 +747,7 @@ bool launch_bra_slab(const LaunchSet& L, const void* src, void* out, int with_d,
   auto go = [&](auto kern, size_t smem) {
     cfg.dynamicSmemBytes = smem;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaLaunchKernelEx(&cfg, kern, L, (const float2*)src, (float2*)out, use_obs);
+    cudaLaunchKernelEx(&cfg, kern, L, (const float2*)src, (float2*)out, with_d ? (float2*)pnext : nullptr, use_obs);
   };
   const int g = c.zs_n;
   if (with_d) {

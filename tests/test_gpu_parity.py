@@ -278,14 +278,21 @@ def test_two_step_average_gpu():
         compare(gi, oi, FP64_J_TOL, FP64_RHO_TOL)
 
 
-@pytest.mark.parametrize("precision,n", [("fp64", 8), ("fp32", 8), ("fp32", 16), ("fp32_tc", 8), ("fp32_tc", 16)])
+@pytest.mark.parametrize("precision,n", [("fp64", 8), ("fp32", 8), ("fp32", 16), ("fp32", 32), ("fp32_tc", 8),
+                                         ("fp32_tc", 16)])
 def test_checkpoint_restart_bitwise(precision, n):
     """propagate(6) == propagate(3) + get_state/load_state + propagate(3), bit for bit
-    (8^3 and 16^3 grids: each shape's own stage and projection kernels; the
-    16^3 cell is 10 bohr wide so that dt E_max of the FD kinetic stays inside
-    the Taylor-4 stability range, about 2.8)."""
-    side = 6.0 if n == 8 else 10.0
-    cell = W.cell_tiny(atoms="pair", n=(n, n, n), a=(side, side, side), n_bands=4)
+    (8^3, 16^3 and 32 x 16 x 16 grids: each shape's own stage and projection
+    kernels; the 16^3 cell is 10 bohr wide so that dt E_max of the FD kinetic
+    stays inside the Taylor-4 stability range, about 2.8).  On the 32-point rows
+    (slab kernels) a continuing run starts each step from the projections that
+    the last observation left in P, a restarted one from a fresh projection
+    pass: the two must agree bit for bit."""
+    if n == 32:
+        cell = W.cell_tiny(atoms="pair", n=(32, 16, 16), a=(20.0, 10.0, 10.0), n_bands=4)
+    else:
+        side = 6.0 if n == 8 else 10.0
+        cell = W.cell_tiny(atoms="pair", n=(n, n, n), a=(side, side, side), n_bands=4)
     subs = [random_subsim(cell, (2, 1, 1), (0.5, 0.5, 0.5), 0.08, 6, W.Kick(k0=0.01), seed=6, tag=i) for i in range(2)]
     P1, g1 = gpu_run(cell, subs, precision=precision)
     P2, _ = gpu_run(cell, subs, precision=precision, steps=3)
