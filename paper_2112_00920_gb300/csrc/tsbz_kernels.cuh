@@ -31,10 +31,6 @@ template <typename V> __device__ __forceinline__ V csub(V a, V b) { return cmk<V
 template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
   return cmk<V>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
-// conj(a) * b
-template <typename V> __device__ __forceinline__ V cmulc(V a, V b) {
-  return cmk<V>(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
-}
 template <typename V, typename R> __device__ __forceinline__ V cscale(V a, R s) { return cmk<V>(a.x * s, a.y * s); }
 // acc += a * b
 template <typename V> __device__ __forceinline__ void cfma(V& acc, V a, V b) {
